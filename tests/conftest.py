@@ -1,0 +1,24 @@
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+
+
+def unit_links(volume):
+    U = np.zeros((volume, 4, 3, 3), dtype=np.complex128)
+    U[:] = np.eye(3)
+    return U
+
+
+@pytest.fixture
+def rng():
+    return np.random.default_rng(1234)
