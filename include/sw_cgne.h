@@ -1,0 +1,135 @@
+/*
+ * sw_cgne.h -- C ABI of the GB300 (sm_103a) staggered Wilson / Wilson CGNE library.
+ *
+ * The library computes the hot path of the cost comparison of arXiv:1312.3265
+ * (Adams, Nogradi, Petrashyk, Zielinski, "Computational efficiency of staggered
+ * Wilson fermions: A first look"): unpreconditioned conjugate gradient on the
+ * normal equations (D+m)^+(D+m) psi = (D+m)^+ chi (Eq. 2), for
+ *   - the 2-flavour staggered Wilson operator (Sec. 1-2):
+ *       D_SW + m = D_st + r (1 - Gamma55) + m,
+ *       (D_st psi)(x) = 1/2 sum_mu eta_mu(x) [U_mu(x) psi(x+mu) - U_mu(x-mu)^+ psi(x-mu)],
+ *       Gamma55 = eps(x) eta5(x) (C_0 C_1 C_2 C_3)_sym,  C_mu = (V_mu + V_mu^+)/2,
+ *       eta_mu(x) = (-1)^(x_0+..+x_{mu-1}),  eps(x) eta5(x) = (-1)^(x_1+x_3);
+ *     Gamma55 is applied as eps eta5 (1/16) sum_{s in {+-1}^4} W(x,s) psi(x+s), with
+ *     W(x,s) the average over the 24 orderings of the 4-link path x -> x+s
+ *     (the "8+16" neighbours of Sec. 3);
+ *   - the usual Wilson operator (the 1392 flop/site operator of Eq. 4):
+ *       (D_W + m) psi = (4r+m) psi - 1/2 sum_mu [(r - g_mu) U_mu(x) psi(x+mu)
+ *                                              + (r + g_mu) U_mu(x-mu)^+ psi(x-mu)],
+ *     gamma matrices in the DeGrand-Rossi basis (g5 = diag(1,1,-1,-1)).
+ * Adjoints: D_SW^+ flips the sign of D_st; D_W^+ flips the sign of every g_mu.
+ *
+ * Data (all DEVICE pointers unless stated; complex numbers as interleaved
+ * (re, im) doubles, 16-byte aligned; the caller owns every buffer it passes):
+ *   site index  n = x0 + L0*(x1 + L1*(x2 + L2*x3)),  x3 = time
+ *   U    [V][4][3][3]  complex128, U[n][mu][a][b] = U_mu(x)_ab
+ *   W    [V][8][3][3]  complex128, hypercube transports for the 8 displacements
+ *                      with s3 = +1; index k: s_mu = -1 iff bit mu of k is set
+ *                      (mu = 0,1,2).  W(x,s) for s3 = -1 is W(x+s,-s)^+.
+ *   staggered Wilson vectors [V][3]     complex128
+ *   Wilson spinors           [V][4][3]  complex128 (spin, colour)
+ * Boundary conditions: links periodic; fermion hops periodic, or antiperiodic
+ * across the time boundary when t_antiperiodic is set.
+ *
+ * Errors: every call returns SW_OK (0), SW_NOT_CONVERGED (> 0, cgne_solve only)
+ * or a negative SW_ERR_* code.  Arguments are checked before any launch
+ * (null, dims, alignment, buffer extent against its device allocation); on an
+ * error nothing is launched and no output is written.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Operator
+ * calls are asynchronous on it; cgne_solve returns after completion.
+ */
+#ifndef SW_CGNE_H
+#define SW_CGNE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int dims[4];        /* L0, L1, L2, L3 (time); each even and >= 2 */
+  int t_antiperiodic; /* 1: antiperiodic fermion boundary condition in time */
+} sw_lattice;
+
+enum {
+  SW_OK = 0,
+  SW_NOT_CONVERGED = 1,  /* cgne_solve: max_iter reached, best x returned */
+  SW_ERR_DIMS = -1,      /* bad lattice extents */
+  SW_ERR_NULL = -2,      /* null pointer argument */
+  SW_ERR_ALIGN = -3,     /* device pointer not 16-byte aligned */
+  SW_ERR_CUDA = -4,      /* CUDA runtime error (launch or execution) */
+  SW_ERR_NAN = -5,       /* non-finite residual or CG breakdown */
+  SW_ERR_OOM = -6,       /* workspace allocation failed */
+  SW_ERR_TIMEOUT = -7,   /* a bounded device wait gave up */
+  SW_ERR_ARG = -8        /* other bad argument (enum value, tolerance, buffer
+                            not device memory or smaller than required) */
+};
+
+enum { SW_OP_STAGGERED_WILSON = 0, SW_OP_WILSON = 1 };
+
+/* Arithmetic of the inner CG iterations.  SW_PREC_F64: every step in FP64.
+ * SW_PREC_F32_RELIABLE: matvecs and vector updates in FP32 on packed copies,
+ * with reliable updates (Sleijpen & van der Vorst 1996) that recompute the
+ * residual b - A x in FP64; dot products accumulate in FP64, and convergence
+ * is always decided on an FP64 residual.
+ * SW_PREC_F16_RELIABLE: as F32, with FP16 storage of links and vectors. */
+enum { SW_PREC_F64 = 0, SW_PREC_F32_RELIABLE = 1, SW_PREC_F16_RELIABLE = 2 };
+
+typedef struct {
+  int iters;               /* CG iterations (matvec pairs) performed */
+  int reliable_updates;    /* FP64 residual recomputations */
+  int status;              /* same value the call returns */
+  int precision;           /* SW_PREC_* used */
+  double true_rel_resid;   /* |b - A x| / |b| in FP64, A = (D+m)^+(D+m), b = (D+m)^+ chi */
+  double seconds;          /* wall time of the call */
+} sw_solve_info;
+
+/* Hypercube transports W(x,s) for the 8 stored displacements (Sec. 3, the 16
+ * hypercube neighbours; the other 8 follow by W(x,s) = W(x+s,-s)^+).
+ * U: [V][4][3][3] in, W: [V][8][3][3] out.  FP64. Asynchronous on `stream`. */
+int sw_hypercube_build(const sw_lattice* lat, const void* U, void* W, void* stream);
+
+/* out = (D_SW + m) in, or (D_SW + m)^+ in when dagger != 0.  FP64.
+ * in, out: [V][3]; in and out must not overlap.  W from sw_hypercube_build. */
+int sw_dslash_apply(const sw_lattice* lat, const void* U, const void* W,
+                    const void* in, void* out, double mass, double r, int dagger,
+                    void* stream);
+
+/* out = (D_W + m) in, or (D_W + m)^+ in when dagger != 0.  FP64.
+ * in, out: [V][4][3]; must not overlap. */
+int wilson_dslash_apply(const sw_lattice* lat, const void* U, const void* in, void* out,
+                        double mass, double r, int dagger, void* stream);
+
+/* Solve (D+m)^+(D+m) x = (D+m)^+ chi by unpreconditioned CG (Eq. 2).
+ * op: SW_OP_STAGGERED_WILSON (W required, vectors [V][3]) or SW_OP_WILSON
+ * (W ignored, spinors [V][4][3]).  x: on entry the initial guess (zeros for
+ * the paper's x0 = 0), on exit the solution.  Stops when the FP64 relative
+ * residual |b - A x|/|b| <= tol (tol > 0), or after max_iter iterations
+ * (returns SW_NOT_CONVERGED with the best x).  precision: SW_PREC_*.
+ * info (host pointer, may be NULL) receives the statistics.  Workspace is
+ * allocated and freed inside the call (stream-ordered).  Blocks until done. */
+int cgne_solve(const sw_lattice* lat, int op, const void* U, const void* W,
+               const void* chi, void* x, double mass, double r, double tol,
+               int max_iter, int precision, sw_solve_info* info, void* stream);
+
+/* Batched CGNE: nsys independent systems on the same gauge field (the
+ * multi-source / multi-mass batches of Sec. 3: 3 colour sources per mass for
+ * staggered Wilson, 12 spin-colour sources for Wilson), solved together so
+ * that every launch reads the links once for all systems in flight.
+ * chi, x: nsys vectors back to back ([nsys][V][3] or [nsys][V][4][3]).
+ * masses: HOST array [nsys] of bare masses.  infos: HOST array [nsys] or NULL.
+ * Each system follows exactly the iteration of cgne_solve with its own
+ * scalars and reductions, so its result does not depend on the other systems
+ * in the batch.  Returns SW_OK if every system converged, else the most
+ * severe status (negative codes before SW_NOT_CONVERGED).  Blocks until done. */
+int cgne_solve_batch(const sw_lattice* lat, int op, const void* U, const void* W, int nsys,
+                     const void* chi, void* x, const double* masses, double r, double tol,
+                     int max_iter, int precision, sw_solve_info* infos, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* sw_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SW_CGNE_H */

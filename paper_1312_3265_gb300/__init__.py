@@ -1,0 +1,19 @@
+"""GB300 (sm_103a) staggered Wilson / Wilson CGNE library.
+
+Thin Python binding over the C ABI in include/sw_cgne.h: it only marshals
+arguments (torch tensors -> device pointers, the current CUDA stream) and
+turns error codes into exceptions.  Every step of the computation runs in the
+library's CUDA kernels; there is no other implementation behind these names.
+
+Field layouts (complex128, canonical, site index n = x0 + L0*(x1 + L1*(x2 + L2*x3))):
+  U (V,4,3,3)   W (V,8,3,3)   staggered vectors (V,3)   Wilson spinors (V,4,3)
+"""
+from __future__ import annotations
+
+from ._binding import (  # noqa: F401
+    SWError, SolveInfo, lib, lib_path,
+    SW_OK, SW_NOT_CONVERGED, SW_OP_STAGGERED_WILSON, SW_OP_WILSON,
+    SW_PREC_F64, SW_PREC_F32_RELIABLE, SW_PREC_F16_RELIABLE,
+    sw_hypercube_build, sw_dslash_apply, wilson_dslash_apply, cgne_solve, cgne_solve_batch,
+    sw_status_string,
+)

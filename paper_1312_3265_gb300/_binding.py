@@ -1,0 +1,152 @@
+"""ctypes marshalling for the C ABI (include/sw_cgne.h)."""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from .build import lib_path as _lib_path
+
+SW_OK = 0
+SW_NOT_CONVERGED = 1
+SW_OP_STAGGERED_WILSON = 0
+SW_OP_WILSON = 1
+SW_PREC_F64 = 0
+SW_PREC_F32_RELIABLE = 1
+SW_PREC_F16_RELIABLE = 2
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("t_antiperiodic", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("status", ctypes.c_int),
+                ("precision", ctypes.c_int), ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+@dataclass
+class SolveInfo:
+    iters: int
+    reliable_updates: int
+    status: int
+    precision: int
+    true_rel_resid: float
+    seconds: float
+
+    @staticmethod
+    def from_c(c):
+        return SolveInfo(c.iters, c.reliable_updates, c.status, c.precision, c.true_rel_resid, c.seconds)
+
+
+class SWError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {sw_status_string(code)} (status {code})")
+
+
+def lib_path():
+    return _lib_path()
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        p = _lib_path()
+        if not os.path.exists(p):
+            raise ImportError(f"CUDA library {p} is missing: build it first with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(p)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        lat = ctypes.POINTER(Lattice)
+        L.sw_hypercube_build.argtypes = [lat, vp, vp, vp]
+        L.sw_dslash_apply.argtypes = [lat, vp, vp, vp, vp, d, d, i, vp]
+        L.wilson_dslash_apply.argtypes = [lat, vp, vp, vp, d, d, i, vp]
+        L.cgne_solve.argtypes = [lat, i, vp, vp, vp, vp, d, d, d, i, i, ctypes.POINTER(_Info), vp]
+        L.cgne_solve_batch.argtypes = [lat, i, vp, vp, i, vp, vp, ctypes.POINTER(ctypes.c_double), d, d, i, i,
+                                       ctypes.POINTER(_Info), vp]
+        L.sw_status_string.argtypes = [i]
+        L.sw_status_string.restype = ctypes.c_char_p
+        for f in ("sw_hypercube_build", "sw_dslash_apply", "wilson_dslash_apply", "cgne_solve", "cgne_solve_batch"):
+            getattr(L, f).restype = i
+        _lib = L
+    return _lib
+
+
+def sw_status_string(code):
+    return lib().sw_status_string(int(code)).decode()
+
+
+def _lat(dims, t_antiperiodic):
+    return ctypes.byref(Lattice((ctypes.c_int * 4)(*[int(v) for v in dims]), int(bool(t_antiperiodic))))
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or a raw integer address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(code, where):
+    if code < 0:
+        raise SWError(code, where)
+    return code
+
+
+def sw_hypercube_build(dims, U, W, t_antiperiodic=False, stream=None):
+    _check(lib().sw_hypercube_build(_lat(dims, t_antiperiodic), _ptr(U), _ptr(W), _stream(stream)),
+           "sw_hypercube_build")
+
+
+def sw_dslash_apply(dims, U, W, inp, out, mass, r=1.0, dagger=False, t_antiperiodic=False, stream=None):
+    _check(lib().sw_dslash_apply(_lat(dims, t_antiperiodic), _ptr(U), _ptr(W), _ptr(inp), _ptr(out),
+                                 float(mass), float(r), int(bool(dagger)), _stream(stream)), "sw_dslash_apply")
+
+
+def wilson_dslash_apply(dims, U, inp, out, mass, r=1.0, dagger=False, t_antiperiodic=False, stream=None):
+    _check(lib().wilson_dslash_apply(_lat(dims, t_antiperiodic), _ptr(U), _ptr(inp), _ptr(out),
+                                     float(mass), float(r), int(bool(dagger)), _stream(stream)),
+           "wilson_dslash_apply")
+
+
+def cgne_solve(dims, op, U, W, chi, x, mass, r=1.0, tol=1e-8, max_iter=100000, precision=SW_PREC_F64,
+               t_antiperiodic=False, stream=None):
+    """Solve (D+m)^+(D+m) x = (D+m)^+ chi; x holds the initial guess on entry.
+    Returns SolveInfo; raises SWError on negative status (not on SW_NOT_CONVERGED)."""
+    info = _Info()
+    rc = lib().cgne_solve(_lat(dims, t_antiperiodic), int(op), _ptr(U), _ptr(W), _ptr(chi), _ptr(x),
+                          float(mass), float(r), float(tol), int(max_iter), int(precision),
+                          ctypes.byref(info), _stream(stream))
+    _check(rc, "cgne_solve")
+    return SolveInfo.from_c(info)
+
+
+def cgne_solve_batch(dims, op, U, W, chi, x, masses, r=1.0, tol=1e-8, max_iter=100000, precision=SW_PREC_F64,
+                     t_antiperiodic=False, stream=None):
+    """Batched CGNE over nsys = len(masses) systems; chi and x hold the systems
+    back to back.  Returns (status, [SolveInfo]); raises SWError on negative status."""
+    n = len(masses)
+    m = (ctypes.c_double * n)(*[float(v) for v in masses])
+    infos = (_Info * n)()
+    rc = lib().cgne_solve_batch(_lat(dims, t_antiperiodic), int(op), _ptr(U), _ptr(W), n, _ptr(chi), _ptr(x), m,
+                                float(r), float(tol), int(max_iter), int(precision), infos, _stream(stream))
+    _check(rc, "cgne_solve_batch")
+    return rc, [SolveInfo.from_c(infos[i]) for i in range(n)]

@@ -1,0 +1,210 @@
+// C ABI entry points (include/sw_cgne.h): argument checks, then dispatch.
+#include <chrono>
+#include <cstdint>
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace swc {
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+static int make_geom(const sw_lattice* lat, Geom* g) {
+  if (!lat) return SW_ERR_NULL;
+  long long V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    const int L = lat->dims[mu];
+    if (L < 2 || (L & 1)) return SW_ERR_DIMS;
+    V *= L;
+    if (V > (1LL << 28)) return SW_ERR_DIMS;
+  }
+  for (int mu = 0; mu < 4; ++mu) g->L[mu] = lat->dims[mu];
+  g->stride[0] = 1;
+  for (int mu = 1; mu < 4; ++mu) g->stride[mu] = g->stride[mu - 1] * g->L[mu - 1];
+  g->V = (int)V;
+  g->apbc = lat->t_antiperiodic ? 1 : 0;
+  return SW_OK;
+}
+
+// Driver entry point for the allocation extent of a device pointer.
+typedef int (*AddrRangeFn)(unsigned long long*, size_t*, unsigned long long);
+static AddrRangeFn addr_range_fn() {
+  static std::once_flag once;
+  static AddrRangeFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<AddrRangeFn>(p);
+  });
+  return fn;
+}
+
+// The buffer must be device (or managed) memory, 16-byte aligned, and its
+// allocation must hold `bytes` from `p` on.
+static int check_buf(const void* p, size_t bytes) {
+  if (!p) return SW_ERR_NULL;
+  if (reinterpret_cast<uintptr_t>(p) & 15u) return SW_ERR_ALIGN;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return SW_ERR_ARG;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return SW_ERR_ARG;
+  if (AddrRangeFn fn = addr_range_fn()) {
+    unsigned long long base = 0;
+    size_t size = 0;
+    if (fn(&base, &size, reinterpret_cast<unsigned long long>(p)) != 0) return SW_ERR_ARG;
+    if (reinterpret_cast<unsigned long long>(p) + bytes > base + size) return SW_ERR_ARG;
+  }
+  return SW_OK;
+}
+
+static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
+}
+
+#define SW_TRY(expr)            \
+  do {                          \
+    const int _e = (expr);      \
+    if (_e != SW_OK) return _e; \
+  } while (0)
+
+}  // namespace swc
+
+using namespace swc;
+
+extern "C" {
+
+const char* sw_status_string(int s) {
+  switch (s) {
+    case SW_OK: return "ok";
+    case SW_NOT_CONVERGED: return "not converged (max_iter reached)";
+    case SW_ERR_DIMS: return "bad lattice extents (each must be even and >= 2)";
+    case SW_ERR_NULL: return "null pointer argument";
+    case SW_ERR_ALIGN: return "device pointer not 16-byte aligned";
+    case SW_ERR_CUDA: return "CUDA error";
+    case SW_ERR_NAN: return "non-finite residual or CG breakdown";
+    case SW_ERR_OOM: return "device workspace allocation failed";
+    case SW_ERR_TIMEOUT: return "bounded wait gave up";
+    case SW_ERR_ARG: return "bad argument";
+    default: return "unknown status";
+  }
+}
+
+int sw_hypercube_build(const sw_lattice* lat, const void* U, void* W, void* stream) {
+  Geom g;
+  SW_TRY(make_geom(lat, &g));
+  const size_t V = g.V;
+  SW_TRY(check_buf(U, V * 4 * 9 * 16));
+  SW_TRY(check_buf(W, V * 8 * 9 * 16));
+  if (overlap(U, V * 576, W, V * 1152)) return SW_ERR_ARG;
+  return hypercube_build_f64(g, static_cast<const double2*>(U), static_cast<double2*>(W),
+                             static_cast<cudaStream_t>(stream));
+}
+
+int sw_dslash_apply(const sw_lattice* lat, const void* U, const void* W, const void* in, void* out, double mass,
+                    double r, int dagger, void* stream) {
+  Geom g;
+  SW_TRY(make_geom(lat, &g));
+  const size_t V = g.V;
+  SW_TRY(check_buf(U, V * 576));
+  SW_TRY(check_buf(W, V * 1152));
+  SW_TRY(check_buf(in, V * 48));
+  SW_TRY(check_buf(out, V * 48));
+  if (overlap(in, V * 48, out, V * 48)) return SW_ERR_ARG;
+  return sw_apply_f64(g, static_cast<const double2*>(U), static_cast<const double2*>(W),
+                      static_cast<const double2*>(in), static_cast<double2*>(out), mass, r, dagger,
+                      static_cast<cudaStream_t>(stream));
+}
+
+int wilson_dslash_apply(const sw_lattice* lat, const void* U, const void* in, void* out, double mass, double r,
+                        int dagger, void* stream) {
+  Geom g;
+  SW_TRY(make_geom(lat, &g));
+  const size_t V = g.V;
+  SW_TRY(check_buf(U, V * 576));
+  SW_TRY(check_buf(in, V * 192));
+  SW_TRY(check_buf(out, V * 192));
+  if (overlap(in, V * 192, out, V * 192)) return SW_ERR_ARG;
+  return wilson_apply_f64(g, static_cast<const double2*>(U), static_cast<const double2*>(in),
+                          static_cast<double2*>(out), mass, r, dagger, static_cast<cudaStream_t>(stream));
+}
+
+int cgne_solve(const sw_lattice* lat, int op, const void* U, const void* W, const void* chi, void* x, double mass,
+               double r, double tol, int max_iter, int precision, sw_solve_info* info, void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (info) *info = sw_solve_info{};
+  Geom g;
+  SW_TRY(make_geom(lat, &g));
+  if (op != SW_OP_STAGGERED_WILSON && op != SW_OP_WILSON) return SW_ERR_ARG;
+  if (precision != SW_PREC_F64 && precision != SW_PREC_F32_RELIABLE) return SW_ERR_ARG;
+  if (!(tol > 0.0) || !(tol < 1.0) || max_iter < 1) return SW_ERR_ARG;
+  if (!(mass == mass) || !(r == r)) return SW_ERR_ARG;
+  const size_t V = g.V;
+  const size_t vb = V * (op == SW_OP_WILSON ? 192 : 48);
+  SW_TRY(check_buf(U, V * 576));
+  if (op == SW_OP_STAGGERED_WILSON) SW_TRY(check_buf(W, V * 1152));
+  SW_TRY(check_buf(chi, vb));
+  SW_TRY(check_buf(x, vb));
+  if (overlap(chi, vb, x, vb)) return SW_ERR_ARG;
+  SolveArgs a{static_cast<const double2*>(U), static_cast<const double2*>(W), static_cast<const double2*>(chi),
+              static_cast<double2*>(x), 1, &mass, r, tol, max_iter, precision, info,
+              static_cast<cudaStream_t>(stream)};
+  const int rc = (op == SW_OP_WILSON) ? wilson_cgne(g, a) : sw_cgne(g, a);
+  if (info) {
+    info->status = rc;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return rc;
+}
+
+int cgne_solve_batch(const sw_lattice* lat, int op, const void* U, const void* W, int nsys, const void* chi,
+                     void* x, const double* masses, double r, double tol, int max_iter, int precision,
+                     sw_solve_info* infos, void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (nsys < 1 || nsys > 65535) return SW_ERR_ARG;
+  if (!masses) return SW_ERR_NULL;
+  if (infos)
+    for (int i = 0; i < nsys; ++i) infos[i] = sw_solve_info{};
+  Geom g;
+  SW_TRY(make_geom(lat, &g));
+  if (op != SW_OP_STAGGERED_WILSON && op != SW_OP_WILSON) return SW_ERR_ARG;
+  if (precision != SW_PREC_F64 && precision != SW_PREC_F32_RELIABLE) return SW_ERR_ARG;
+  if (!(tol > 0.0) || !(tol < 1.0) || max_iter < 1) return SW_ERR_ARG;
+  for (int i = 0; i < nsys; ++i)
+    if (!(masses[i] == masses[i])) return SW_ERR_ARG;
+  if (!(r == r)) return SW_ERR_ARG;
+  const size_t V = g.V;
+  const size_t vb = V * (op == SW_OP_WILSON ? 192 : 48) * (size_t)nsys;
+  SW_TRY(check_buf(U, V * 576));
+  if (op == SW_OP_STAGGERED_WILSON) SW_TRY(check_buf(W, V * 1152));
+  SW_TRY(check_buf(chi, vb));
+  SW_TRY(check_buf(x, vb));
+  if (overlap(chi, vb, x, vb)) return SW_ERR_ARG;
+  SolveArgs a{static_cast<const double2*>(U), static_cast<const double2*>(W), static_cast<const double2*>(chi),
+              static_cast<double2*>(x), nsys, masses, r, tol, max_iter, precision, infos,
+              static_cast<cudaStream_t>(stream)};
+  const int rc = (op == SW_OP_WILSON) ? wilson_cgne(g, a) : sw_cgne(g, a);
+  if (infos) {
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int i = 0; i < nsys; ++i) infos[i].seconds = secs;
+  }
+  return rc;
+}
+
+}  // extern "C"

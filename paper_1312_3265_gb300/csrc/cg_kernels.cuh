@@ -1,0 +1,307 @@
+// CG kernels for CGNE (Eq. 2), generic over operator and storage.
+//
+// One iteration of textbook CG on A = (D+m)^+(D+m) takes three launches:
+//   k1  t = (D+m) p,  pAp = <p, A p> = |t|^2,  alpha = |r|^2 / pAp
+//   k2  Ap = (D+m)^+ t (never stored), x += alpha p, r -= alpha Ap,
+//       |r|^2, beta = |r_new|^2 / |r_old|^2, status decisions
+//   k3  p = r + beta p
+// Every launch covers a batch of independent systems (blockIdx.y = system)
+// that share the gauge field; blocks of a system whose status is not RUNNING
+// return at once, so converged systems cost nothing.  Scalars live in device
+// memory (SysState), so the host never waits inside an iteration.
+//
+// Reductions: sites are cut into fixed tiles of kTile consecutive sites.  A
+// tile's sum (each thread one site, promoted to FP64, warp shuffle + block
+// tree) is stored as one double per tile; the last block of the system
+// (atomic ticket) adds the tile sums in tile order.  The summation order thus
+// depends only on the lattice volume -- not on the grid size, nor on which
+// other systems share the launch -- so a system gives bit-identical results
+// alone and in any batch.
+#pragma once
+#include "common.cuh"
+#include "dslash.cuh"
+
+namespace swc {
+
+enum SysStatus : int {
+  ST_RUNNING = 0,
+  ST_NEED_RU = 1,       // host must recompute the FP64 residual
+  ST_CONVERGED = 2,
+  ST_FAILED = 3,        // NaN / breakdown
+  ST_MAXITER = 4,
+  ST_JUST_UPDATED = 5,  // residual replaced, p update pending
+  ST_IDLE = 6           // batch slot without a system
+};
+
+struct SysState {
+  double rr;       // |r|^2 of the iterated residual
+  double rr_old;   // previous |r|^2
+  double pAp;
+  double alpha;
+  double beta;
+  double b2;       // |b|^2
+  double tol2;     // tol^2 |b|^2
+  double rmax2;    // max |r|^2 since the last reliable update
+  double delta2;   // reliable-update trigger factor (0: only at convergence)
+  double rr_true;  // last FP64 residual norm^2
+  int iter;
+  int max_iter;
+  int status;
+  int n_ru;
+};
+
+constexpr int kTile = 128;  // sites per reduction tile == threads per stencil block
+
+struct RedBuf {
+  double* partials;   // [nsys][pstride] tile sums
+  unsigned* tickets;  // [nsys], zero between launches
+  int pstride;        // >= number of tiles
+};
+
+__device__ __forceinline__ void put_tile(const RedBuf& rb, int sys, int tile, double v) {
+  if (threadIdx.x == 0) rb.partials[(size_t)sys * rb.pstride + tile] = v;
+}
+
+// Sum the tile sums of system `sys` in a fixed order; valid in thread 0.
+__device__ __forceinline__ double finalize_sum(const RedBuf& rb, int sys, int ntiles, double* smem) {
+  const double* p = rb.partials + (size_t)sys * rb.pstride;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < ntiles; i += blockDim.x) v += __ldcg(p + i);
+  return block_sum(v, smem);
+}
+
+// Returns true in every thread of the block that is the last to finish for `sys`.
+__device__ __forceinline__ bool block_done(const RedBuf& rb, int sys, int* flag_smem) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(rb.tickets + sys, 1u);
+    *flag_smem = (t == gridDim.x - 1);
+    if (*flag_smem) rb.tickets[sys] = 0u;
+  }
+  __syncthreads();
+  const bool last = *flag_smem != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// ---------------------------------------------------------------- operator policies
+template <typename T, int N> struct CV { cx<T> c[N]; };
+
+template <typename T, typename G, typename Wt, template <int> class VA>
+struct SWOp {
+  static constexpr int NC = 3;
+  using Vec = VA<3>;
+  G U;
+  Wt W;
+  __device__ __forceinline__ CV<T, 3> apply(const Geom& g, int n, const Vec& in, T m, T r, bool dag) const {
+    const V3<T> o = sw_site<T>(g, n, U, W, in, m, r, dag);
+    CV<T, 3> v;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v.c[i] = o.c[i];
+    return v;
+  }
+};
+
+template <typename T, typename G, template <int> class VA, bool R1>
+struct WOp {
+  static constexpr int NC = 12;
+  using Vec = VA<12>;
+  G U;
+  __device__ __forceinline__ CV<T, 12> apply(const Geom& g, int n, const Vec& in, T m, T r, bool dag) const {
+    const Sp<T> o = wilson_site<T, R1>(g, n, U, in, m, r, dag);
+    CV<T, 12> v;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) v.c[3 * s + i] = o.s[s].c[i];
+    return v;
+  }
+};
+
+// Per-system view of a batched vector: system `sys` starts `sys * sstride`
+// complex numbers after the base pointer (layout inside a system unchanged).
+template <typename Vec> __device__ __forceinline__ Vec sys_view(Vec v, int sys, size_t sstride) {
+  v.p += sys * sstride;
+  return v;
+}
+
+struct BatchParams {
+  const double* mass;  // [nsys]
+  double r;
+  size_t sstride;      // complex numbers between systems, low-precision vectors
+  size_t sstride64;    // same for FP64 canonical vectors
+};
+
+// ---------------------------------------------------------------- plain apply (ABI)
+template <typename T, typename Op>
+__global__ void __launch_bounds__(kTile) apply_kernel(Geom g, Op op, typename Op::Vec in, typename Op::Vec out,
+                                                    double mass0, const double* mass, size_t sstride, double r,
+                                                    int dagger, const SysState* S, int only_status) {
+  const int sys = blockIdx.y;
+  if (S && S[sys].status != only_status) return;
+  in = sys_view(in, sys, sstride);
+  out = sys_view(out, sys, sstride);
+  const T m = (T)(mass ? mass[sys] : mass0);
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.V; n += gridDim.x * blockDim.x) {
+    const CV<T, Op::NC> v = op.apply(g, n, in, m, (T)r, dagger != 0);
+#pragma unroll
+    for (int c = 0; c < Op::NC; ++c) out.st(n, c, v.c[c]);
+  }
+}
+
+// ---------------------------------------------------------------- k1: t = D p, |t|^2
+template <typename T, typename Op>
+__global__ void __launch_bounds__(kTile) cg_k1(Geom g, Op op, typename Op::Vec p, typename Op::Vec t,
+                                             BatchParams bp, SysState* S, RedBuf rb) {
+  __shared__ double sm[32];
+  __shared__ int last;
+  const int sys = blockIdx.y;
+  if (S[sys].status != ST_RUNNING) return;
+  p = sys_view(p, sys, bp.sstride);
+  t = sys_view(t, sys, bp.sstride);
+  const T m = (T)bp.mass[sys];
+  const int ntiles = (g.V + kTile - 1) / kTile;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int n = tile * kTile + threadIdx.x;
+    T acc = T(0);
+    if (n < g.V) {
+      const CV<T, Op::NC> v = op.apply(g, n, p, m, (T)bp.r, false);
+#pragma unroll
+      for (int c = 0; c < Op::NC; ++c) {
+        t.st(n, c, v.c[c]);
+        acc += norm2(v.c[c]);
+      }
+    }
+    put_tile(rb, sys, tile, block_sum((double)acc, sm));
+  }
+  if (block_done(rb, sys, &last)) {
+    const double pAp = finalize_sum(rb, sys, ntiles, sm);
+    if (threadIdx.x == 0) {
+      SysState& s = S[sys];
+      s.pAp = pAp;
+      if (!(pAp > 0.0) || !isfinite(pAp)) {
+        s.status = ST_FAILED;
+      } else {
+        s.alpha = s.rr / pAp;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- k2: Ap = D^+ t; x, r update; |r|^2
+template <typename T, typename Op, typename XVec>
+__global__ void __launch_bounds__(kTile) cg_k2(Geom g, Op op, typename Op::Vec t, typename Op::Vec p,
+                                             typename Op::Vec r, XVec x, BatchParams bp, size_t xstride,
+                                             SysState* S, RedBuf rb) {
+  __shared__ double sm[32];
+  __shared__ int last;
+  const int sys = blockIdx.y;
+  if (S[sys].status != ST_RUNNING) return;
+  t = sys_view(t, sys, bp.sstride);
+  p = sys_view(p, sys, bp.sstride);
+  r = sys_view(r, sys, bp.sstride);
+  x = sys_view(x, sys, xstride);
+  const T m = (T)bp.mass[sys];
+  const T alpha = (T)S[sys].alpha;
+  const int ntiles = (g.V + kTile - 1) / kTile;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int n = tile * kTile + threadIdx.x;
+    T acc = T(0);
+    if (n < g.V) {
+      const CV<T, Op::NC> ap = op.apply(g, n, t, m, (T)bp.r, true);
+#pragma unroll
+      for (int c = 0; c < Op::NC; ++c) {
+        const cx<T> pc = p.ld(n, c);
+        const cx<T> xc = x.ld(n, c);
+        x.st(n, c, xc + alpha * pc);
+        const cx<T> rc = r.ld(n, c) - alpha * ap.c[c];
+        r.st(n, c, rc);
+        acc += norm2(rc);
+      }
+    }
+    put_tile(rb, sys, tile, block_sum((double)acc, sm));
+  }
+  if (block_done(rb, sys, &last)) {
+    const double rr = finalize_sum(rb, sys, ntiles, sm);
+    if (threadIdx.x == 0) {
+      SysState& s = S[sys];
+      s.iter += 1;
+      if (!isfinite(rr)) {
+        s.status = ST_FAILED;
+      } else {
+        s.rr_old = s.rr;
+        s.rr = rr;
+        s.beta = rr / s.rr_old;
+        if (rr > s.rmax2) s.rmax2 = rr;
+        if (rr <= s.tol2 || s.iter >= s.max_iter || rr < s.delta2 * s.rmax2) s.status = ST_NEED_RU;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- k3: p = r + beta p
+template <typename T, typename Vec, int NC>
+__global__ void __launch_bounds__(256) cg_k3(int V, Vec r, Vec p, size_t sstride, const SysState* S, int only_status) {
+  const int sys = blockIdx.y;
+  if (S[sys].status != only_status) return;
+  r = sys_view(r, sys, sstride);
+  p = sys_view(p, sys, sstride);
+  const T beta = (T)S[sys].beta;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < V; n += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) p.st(n, c, r.ld(n, c) + beta * p.ld(n, c));
+  }
+}
+
+// ---------------------------------------------------------------- FP64 residual (reliable update)
+// r64 = b - (D+m)^+ t64, |r64|^2, then the convergence decision.
+template <typename Op>
+__global__ void __launch_bounds__(kTile) residual64(Geom g, Op op, typename Op::Vec t, typename Op::Vec b,
+                                                  typename Op::Vec r, BatchParams bp, SysState* S, RedBuf rb) {
+  __shared__ double sm[32];
+  __shared__ int last;
+  const int sys = blockIdx.y;
+  if (S[sys].status != ST_NEED_RU) return;
+  t = sys_view(t, sys, bp.sstride64);
+  b = sys_view(b, sys, bp.sstride64);
+  r = sys_view(r, sys, bp.sstride64);
+  const double m = bp.mass[sys];
+  const int ntiles = (g.V + kTile - 1) / kTile;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int n = tile * kTile + threadIdx.x;
+    double acc = 0.0;
+    if (n < g.V) {
+      const CV<double, Op::NC> at = op.apply(g, n, t, m, bp.r, true);
+#pragma unroll
+      for (int c = 0; c < Op::NC; ++c) {
+        const cx<double> rc = b.ld(n, c) - at.c[c];
+        r.st(n, c, rc);
+        acc += norm2(rc);
+      }
+    }
+    put_tile(rb, sys, tile, block_sum(acc, sm));
+  }
+  if (block_done(rb, sys, &last)) {
+    const double rr = finalize_sum(rb, sys, ntiles, sm);
+    if (threadIdx.x == 0) {
+      SysState& s = S[sys];
+      s.rr_true = rr;
+      s.n_ru += 1;
+      if (!isfinite(rr)) {
+        s.status = ST_FAILED;
+      } else if (rr <= s.tol2) {
+        s.status = ST_CONVERGED;
+      } else if (s.iter >= s.max_iter) {
+        s.status = ST_MAXITER;
+      } else {
+        s.beta = (s.iter == 0) ? 0.0 : rr / s.rr_old;
+        s.rr = rr;
+        s.rmax2 = rr;
+        s.status = ST_JUST_UPDATED;
+      }
+    }
+  }
+}
+
+}  // namespace swc

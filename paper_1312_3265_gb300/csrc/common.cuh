@@ -1,0 +1,225 @@
+// Shared device helpers: complex and 3x3 colour algebra, lattice geometry,
+// and the field accessors that hide the storage layouts.
+//
+// Layouts
+//   canonical (the C ABI's, FP64): site-major arrays of complex128
+//     U[V][4][9], W[V][8][9], vectors [V][ncomp]
+//   planar (internal, FP32): component-major float2 planes, so that a warp
+//     reading one component of 32 consecutive sites touches 256 contiguous bytes
+//     U[4*9][V], W[8*9][V], vectors [ncomp][V]
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace swc {
+
+// ------------------------------------------------------------------ complex
+template <typename T> struct cx { T re, im; };
+
+template <typename T> __device__ __forceinline__ cx<T> mk(T r, T i) { return {r, i}; }
+template <typename T> __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// conj(a) * b
+template <typename T> __device__ __forceinline__ cx<T> cjmul(cx<T> a, cx<T> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+template <typename T> __device__ __forceinline__ cx<T> times_i(cx<T> a) { return {-a.im, a.re}; }
+template <typename T> __device__ __forceinline__ T norm2(cx<T> a) { return a.re * a.re + a.im * a.im; }
+
+template <typename T> struct V3 { cx<T> c[3]; };
+template <typename T> struct M3 { cx<T> e[3][3]; };
+
+template <typename T> __device__ __forceinline__ V3<T> zero3() {
+  V3<T> v;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v.c[i] = {T(0), T(0)};
+  return v;
+}
+
+// M v
+template <typename T> __device__ __forceinline__ V3<T> mv(const M3<T>& M, const V3<T>& v) {
+  V3<T> o;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cx<T> s = cmul(M.e[i][0], v.c[0]);
+    s = s + cmul(M.e[i][1], v.c[1]);
+    s = s + cmul(M.e[i][2], v.c[2]);
+    o.c[i] = s;
+  }
+  return o;
+}
+// M^+ v
+template <typename T> __device__ __forceinline__ V3<T> mdv(const M3<T>& M, const V3<T>& v) {
+  V3<T> o;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cx<T> s = cjmul(M.e[0][i], v.c[0]);
+    s = s + cjmul(M.e[1][i], v.c[1]);
+    s = s + cjmul(M.e[2][i], v.c[2]);
+    o.c[i] = s;
+  }
+  return o;
+}
+template <typename T> __device__ __forceinline__ void acc3(V3<T>& a, const V3<T>& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) a.c[i] = a.c[i] + b.c[i];
+}
+template <typename T> __device__ __forceinline__ void acc3s(V3<T>& a, T s, const V3<T>& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) a.c[i] = a.c[i] + s * b.c[i];
+}
+template <typename T> __device__ __forceinline__ M3<T> mm(const M3<T>& A, const M3<T>& B) {
+  M3<T> C;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<T> s = cmul(A.e[i][0], B.e[0][j]);
+      s = s + cmul(A.e[i][1], B.e[1][j]);
+      s = s + cmul(A.e[i][2], B.e[2][j]);
+      C.e[i][j] = s;
+    }
+  return C;
+}
+template <typename T> __device__ __forceinline__ M3<T> dag(const M3<T>& A) {
+  M3<T> C;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) C.e[i][j] = {A.e[j][i].re, -A.e[j][i].im};
+  return C;
+}
+template <typename T> __device__ __forceinline__ void madd(M3<T>& A, const M3<T>& B) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) A.e[i][j] = A.e[i][j] + B.e[i][j];
+}
+
+// ------------------------------------------------------------------ geometry
+struct Geom {
+  int L[4];
+  int stride[4];  // 1, L0, L0 L1, L0 L1 L2
+  int V;
+  int apbc;       // antiperiodic fermion BC in time
+};
+
+__device__ __forceinline__ void coords(const Geom& g, int n, int x[4]) {
+  x[0] = n % g.L[0];
+  int q = n / g.L[0];
+  x[1] = q % g.L[1];
+  q /= g.L[1];
+  x[2] = q % g.L[2];
+  x[3] = q / g.L[2];
+}
+
+// neighbour index of n (coordinates x) one step `s` (+1/-1) along mu
+__device__ __forceinline__ int hop(const Geom& g, int n, const int x[4], int mu, int s) {
+  if (s > 0) return (x[mu] == g.L[mu] - 1) ? n - (g.L[mu] - 1) * g.stride[mu] : n + g.stride[mu];
+  return (x[mu] == 0) ? n + (g.L[mu] - 1) * g.stride[mu] : n - g.stride[mu];
+}
+// fermion boundary sign of a time hop from x3 in direction s
+__device__ __forceinline__ bool bc_flip(const Geom& g, const int x[4], int s) {
+  return g.apbc && ((s > 0) ? (x[3] == g.L[3] - 1) : (x[3] == 0));
+}
+
+// ------------------------------------------------------------------ accessors
+// Canonical FP64 (the C ABI layout)
+struct GaugeC64 {
+  const double2* p;
+  __device__ __forceinline__ M3<double> link(int n, int mu) const {
+    const double2* q = p + ((size_t)n * 4 + mu) * 9;
+    M3<double> M;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) { double2 v = __ldg(q + i * 3 + j); M.e[i][j] = {v.x, v.y}; }
+    return M;
+  }
+};
+struct TransC64 {
+  const double2* p;
+  __device__ __forceinline__ M3<double> mat(int n, int k) const {
+    const double2* q = p + ((size_t)n * 8 + k) * 9;
+    M3<double> M;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) { double2 v = __ldg(q + i * 3 + j); M.e[i][j] = {v.x, v.y}; }
+    return M;
+  }
+};
+
+// Planar FP32: plane c of an object of `ncx` complex numbers per site at p[c*V + n]
+struct GaugeP32 {
+  const float2* p;
+  int V;
+  __device__ __forceinline__ M3<float> link(int n, int mu) const {
+    const float2* q = p + (size_t)mu * 9 * V + n;
+    M3<float> M;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) { float2 v = __ldg(q + (size_t)(i * 3 + j) * V); M.e[i][j] = {v.x, v.y}; }
+    return M;
+  }
+};
+struct TransP32 {
+  const float2* p;
+  int V;
+  __device__ __forceinline__ M3<float> mat(int n, int k) const {
+    const float2* q = p + (size_t)k * 9 * V + n;
+    M3<float> M;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) { float2 v = __ldg(q + (size_t)(i * 3 + j) * V); M.e[i][j] = {v.x, v.y}; }
+    return M;
+  }
+};
+
+// Vector fields: NC complex components per site.
+template <int NC> struct VecC64 {  // canonical [V][NC] complex128
+  double2* p;
+  __device__ __forceinline__ cx<double> ld(int n, int c) const { double2 v = __ldg(p + (size_t)n * NC + c); return {v.x, v.y}; }
+  __device__ __forceinline__ void st(int n, int c, cx<double> a) const { p[(size_t)n * NC + c] = make_double2(a.re, a.im); }
+};
+template <int NC> struct VecP32 {  // planar [NC][V] float2
+  float2* p;
+  int V;
+  __device__ __forceinline__ cx<float> ld(int n, int c) const { float2 v = __ldg(p + (size_t)c * V + n); return {v.x, v.y}; }
+  __device__ __forceinline__ void st(int n, int c, cx<float> a) const { p[(size_t)c * V + n] = make_float2(a.re, a.im); }
+};
+
+template <typename Acc, typename T> __device__ __forceinline__ V3<T> ld3(const Acc& a, int n, int off = 0) {
+  V3<T> v;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v.c[i] = a.ld(n, off + i);
+  return v;
+}
+
+// ------------------------------------------------------------------ reductions
+// Block-wide sum of one double per thread (result valid in thread 0).
+__device__ __forceinline__ double block_sum(double v, double* smem /* >= 32 */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) smem[w] = v;
+  __syncthreads();
+  v = 0.0;
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (lane < nw) ? smem[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+}  // namespace swc

@@ -1,0 +1,198 @@
+// Per-site operator application for both Dirac operators, generic over the
+// storage layout (accessors from common.cuh) and the arithmetic type.
+//
+// Staggered Wilson (Sec. 1-2; operator of Adams, PLB 699 (2011) 394):
+//   (D_SW + m) psi(x) = sgn/2 sum_mu eta_mu(x) [U_mu(x) psi(x+mu) - U_mu(x-mu)^+ psi(x-mu)]
+//                       + (r + m) psi(x)
+//                       - r eps(x) eta5(x) / 16 sum_{s in {+-1}^4} W(x,s) psi(x+s)
+//   sgn = +1, or -1 for the adjoint (D_st anti-Hermitian, Gamma55 Hermitian).
+//   The 16 hypercube corners use the 8 stored transports: W(x,s) for s3 = +1,
+//   and W(x,s) = W(x+s,-s)^+ (stored at the corner site) for s3 = -1.
+//
+// Wilson (Eq. 4's 1392 flop/site operator):
+//   (D_W + m) psi(x) = (4r+m) psi(x) - 1/2 sum_mu [(r - c g_mu) U_mu(x) psi(x+mu)
+//                                                 + (r + c g_mu) U_mu(x-mu)^+ psi(x-mu)]
+//   c = +1, or -1 for the adjoint.  At r = 1 the factors (1 -+ g_mu) have rank 2
+//   and the hop is done on projected 2-spinors ("8x2" of Sec. 3); other r use
+//   the full 4-spinor.  DeGrand-Rossi basis: g_mu = [[0, A_mu], [A_mu^+, 0]].
+#pragma once
+#include "common.cuh"
+
+namespace swc {
+
+// eps(x) eta5(x) = (-1)^(x1 + x3)
+__device__ __forceinline__ bool eps_eta5_neg(const int x[4]) { return ((x[1] + x[3]) & 1) != 0; }
+
+template <typename T> __device__ __forceinline__ void neg3(V3<T>& v) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v.c[i] = T(-1) * v.c[i];
+}
+
+// Hypercube corner of n displaced by s = (s0, s1, s2, s3), each +-1.
+__device__ __forceinline__ int corner(const Geom& g, int n, const int x[4], int s0, int s1, int s2, int s3) {
+  n = hop(g, n, x, 0, s0);
+  n = hop(g, n, x, 1, s1);
+  n = hop(g, n, x, 2, s2);
+  return hop(g, n, x, 3, s3);
+}
+
+template <typename T, typename G, typename Wt, typename In>
+__device__ __forceinline__ V3<T> sw_site(const Geom& g, int n, const G& U, const Wt& W, const In& in,
+                                         T mass, T r, bool dagger) {
+  int x[4];
+  coords(g, n, x);
+  V3<T> st = zero3<T>();
+  int par = 0;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int nf = hop(g, n, x, mu, +1), nb = hop(g, n, x, mu, -1);
+    V3<T> f = mv(U.link(n, mu), ld3<In, T>(in, nf));
+    V3<T> b = mdv(U.link(nb, mu), ld3<In, T>(in, nb));
+    if (mu == 3) {
+      if (bc_flip(g, x, +1)) neg3(f);
+      if (bc_flip(g, x, -1)) neg3(b);
+    }
+    const T eta = (par & 1) ? T(-1) : T(1);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) st.c[i] = st.c[i] + eta * (f.c[i] - b.c[i]);
+    par += x[mu];
+  }
+  V3<T> h = zero3<T>();
+  const bool fflip = bc_flip(g, x, +1), bflip = bc_flip(g, x, -1);
+#pragma unroll 2
+  for (int k = 0; k < 8; ++k) {
+    const int s0 = (k & 1) ? -1 : 1, s1 = (k & 2) ? -1 : 1, s2 = (k & 4) ? -1 : 1;
+    const int yf = corner(g, n, x, s0, s1, s2, +1);
+    const int yb = corner(g, n, x, -s0, -s1, -s2, -1);
+    V3<T> a = mv(W.mat(n, k), ld3<In, T>(in, yf));
+    V3<T> b = mdv(W.mat(yb, k), ld3<In, T>(in, yb));
+    if (fflip) neg3(a);
+    if (bflip) neg3(b);
+    acc3(h, a);
+    acc3(h, b);
+  }
+  const T hs = (eps_eta5_neg(x) ? r : -r) * T(0.0625);
+  const T ss = dagger ? T(-0.5) : T(0.5);
+  const V3<T> self = ld3<In, T>(in, n);
+  V3<T> o;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) o.c[i] = ss * st.c[i] + (r + mass) * self.c[i] + hs * h.c[i];
+  return o;
+}
+
+template <typename T> struct Sp { V3<T> s[4]; };
+
+template <typename In, typename T> __device__ __forceinline__ Sp<T> ld_sp(const In& in, int n) {
+  Sp<T> p;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) p.s[s] = ld3<In, T>(in, n, 3 * s);
+  return p;
+}
+
+// h = (psi_u - c A_mu psi_d): the two independent spin rows of (1 - c g_mu) psi
+template <typename T>
+__device__ __forceinline__ void wproject(int mu, T c, const Sp<T>& p, V3<T>& h0, V3<T>& h1) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const cx<T> a0 = p.s[0].c[i], a1 = p.s[1].c[i], a2 = p.s[2].c[i], a3 = p.s[3].c[i];
+    switch (mu) {
+      case 0: h0.c[i] = a0 - c * times_i(a3); h1.c[i] = a1 - c * times_i(a2); break;
+      case 1: h0.c[i] = a0 + c * a3;          h1.c[i] = a1 - c * a2;          break;
+      case 2: h0.c[i] = a0 - c * times_i(a2); h1.c[i] = a1 + c * times_i(a3); break;
+      default: h0.c[i] = a0 - c * a2;         h1.c[i] = a1 - c * a3;          break;
+    }
+  }
+}
+// acc += (1 - c g_mu) reconstructed from the transported rows h0, h1
+template <typename T>
+__device__ __forceinline__ void wreconstruct(int mu, T c, const V3<T>& h0, const V3<T>& h1, Sp<T>& acc) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const cx<T> b0 = h0.c[i], b1 = h1.c[i];
+    acc.s[0].c[i] = acc.s[0].c[i] + b0;
+    acc.s[1].c[i] = acc.s[1].c[i] + b1;
+    switch (mu) {
+      case 0: acc.s[2].c[i] = acc.s[2].c[i] + c * times_i(b1); acc.s[3].c[i] = acc.s[3].c[i] + c * times_i(b0); break;
+      case 1: acc.s[2].c[i] = acc.s[2].c[i] - c * b1;          acc.s[3].c[i] = acc.s[3].c[i] + c * b0;          break;
+      case 2: acc.s[2].c[i] = acc.s[2].c[i] + c * times_i(b0); acc.s[3].c[i] = acc.s[3].c[i] - c * times_i(b1); break;
+      default: acc.s[2].c[i] = acc.s[2].c[i] - c * b0;         acc.s[3].c[i] = acc.s[3].c[i] - c * b1;          break;
+    }
+  }
+}
+// acc += (r - c g_mu) f for a full transported 4-spinor f
+template <typename T>
+__device__ __forceinline__ void wgeneral(int mu, T c, T r, const Sp<T>& f, Sp<T>& acc) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const cx<T> f0 = f.s[0].c[i], f1 = f.s[1].c[i], f2 = f.s[2].c[i], f3 = f.s[3].c[i];
+    cx<T> g0, g1, g2, g3;  // g_mu f
+    switch (mu) {
+      case 0: g0 = times_i(f3); g1 = times_i(f2); g2 = T(-1) * times_i(f1); g3 = T(-1) * times_i(f0); break;
+      case 1: g0 = T(-1) * f3;  g1 = f2;          g2 = f1;                   g3 = T(-1) * f0;          break;
+      case 2: g0 = times_i(f2); g1 = T(-1) * times_i(f3); g2 = T(-1) * times_i(f0); g3 = times_i(f1); break;
+      default: g0 = f2;         g1 = f3;          g2 = f0;                   g3 = f1;                  break;
+    }
+    acc.s[0].c[i] = acc.s[0].c[i] + r * f0 - c * g0;
+    acc.s[1].c[i] = acc.s[1].c[i] + r * f1 - c * g1;
+    acc.s[2].c[i] = acc.s[2].c[i] + r * f2 - c * g2;
+    acc.s[3].c[i] = acc.s[3].c[i] + r * f3 - c * g3;
+  }
+}
+
+template <typename T, bool R1, typename G, typename In>
+__device__ __forceinline__ Sp<T> wilson_site(const Geom& g, int n, const G& U, const In& in,
+                                             T mass, T r, bool dagger) {
+  int x[4];
+  coords(g, n, x);
+  Sp<T> acc;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) acc.s[s] = zero3<T>();
+  const T sg = dagger ? T(-1) : T(1);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int nf = hop(g, n, x, mu, +1), nb = hop(g, n, x, mu, -1);
+    T bf = T(1), bb = T(1);
+    if (mu == 3) {
+      if (bc_flip(g, x, +1)) bf = T(-1);
+      if (bc_flip(g, x, -1)) bb = T(-1);
+    }
+    const M3<T> Uf = U.link(n, mu);
+    const M3<T> Ub = U.link(nb, mu);
+    if (R1) {
+      V3<T> h0, h1;
+      const Sp<T> pf = ld_sp<In, T>(in, nf);
+      wproject(mu, sg, pf, h0, h1);
+      V3<T> u0 = mv(Uf, h0), u1 = mv(Uf, h1);
+      if (bf < T(0)) { neg3(u0); neg3(u1); }
+      wreconstruct(mu, sg, u0, u1, acc);
+      const Sp<T> pb = ld_sp<In, T>(in, nb);
+      wproject(mu, -sg, pb, h0, h1);
+      u0 = mdv(Ub, h0);
+      u1 = mdv(Ub, h1);
+      if (bb < T(0)) { neg3(u0); neg3(u1); }
+      wreconstruct(mu, -sg, u0, u1, acc);
+    } else {
+      const Sp<T> pf = ld_sp<In, T>(in, nf), pb = ld_sp<In, T>(in, nb);
+      Sp<T> f, b;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        f.s[s] = mv(Uf, pf.s[s]);
+        b.s[s] = mdv(Ub, pb.s[s]);
+        if (bf < T(0)) neg3(f.s[s]);
+        if (bb < T(0)) neg3(b.s[s]);
+      }
+      wgeneral(mu, sg, r, f, acc);
+      wgeneral(mu, -sg, r, b, acc);
+    }
+  }
+  const Sp<T> self = ld_sp<In, T>(in, n);
+  const T diag = T(4) * r + mass;
+  Sp<T> o;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o.s[s].c[i] = diag * self.s[s].c[i] - T(0.5) * acc.s[s].c[i];
+  return o;
+}
+
+}  // namespace swc

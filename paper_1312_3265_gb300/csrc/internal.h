@@ -1,0 +1,38 @@
+// Internal C++ entry points behind the C ABI (one translation unit per operator).
+#pragma once
+#include <cuda_runtime.h>
+#include "../../include/sw_cgne.h"
+
+namespace swc {
+
+struct Geom;
+
+// Common arguments of a batched CGNE call.  chi, x: nsys systems back to back
+// in the canonical layout.  masses: host array [nsys].  infos: host [nsys].
+struct SolveArgs {
+  const double2* U;
+  const double2* W;  // staggered Wilson only
+  const double2* chi;
+  double2* x;
+  int nsys;
+  const double* masses;
+  double r;
+  double tol;
+  int max_iter;
+  int precision;
+  sw_solve_info* infos;
+  cudaStream_t stream;
+};
+
+int hypercube_build_f64(const Geom& g, const double2* U, double2* W, cudaStream_t st);
+int sw_apply_f64(const Geom& g, const double2* U, const double2* W, const double2* in, double2* out,
+                 double mass, double r, int dagger, cudaStream_t st);
+int wilson_apply_f64(const Geom& g, const double2* U, const double2* in, double2* out,
+                     double mass, double r, int dagger, cudaStream_t st);
+int sw_cgne(const Geom& g, const SolveArgs& a);
+int wilson_cgne(const Geom& g, const SolveArgs& a);
+
+// Device properties cached per device.
+int sm_count();
+
+}  // namespace swc

@@ -1,0 +1,36 @@
+// Staggered Wilson operator: FP64 apply (C ABI) and batched CGNE.
+#include "driver.cuh"
+
+namespace swc {
+
+using SW64 = SWOp<double, GaugeC64, TransC64, VecC64>;
+using SW32 = SWOp<float, GaugeP32, TransP32, VecP32>;
+
+int sw_apply_f64(const Geom& g, const double2* U, const double2* W, const double2* in, double2* out,
+                 double mass, double r, int dagger, cudaStream_t st) {
+  const SW64 op{GaugeC64{U}, TransC64{W}};
+  const int gx = (g.V + 127) / 128;
+  apply_kernel<double, SW64><<<dim3(gx, 1), 128, 0, st>>>(g, op, VecC64<3>{const_cast<double2*>(in)},
+                                                          VecC64<3>{out}, mass, nullptr, 0, r, dagger,
+                                                          nullptr, 0);
+  return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
+int sw_cgne(const Geom& g, const SolveArgs& a) {
+  const SW64 opd{GaugeC64{a.U}, TransC64{a.W}};
+  if (a.precision == SW_PREC_F64) return run_cgne<SW64, SW64, false>(g, opd, opd, a);
+  if (a.precision == SW_PREC_F32_RELIABLE) {
+    DevMem mu, mw;
+    if (!mu.alloc(sizeof(float2) * 36 * (size_t)g.V, a.stream) ||
+        !mw.alloc(sizeof(float2) * 72 * (size_t)g.V, a.stream))
+      return SW_ERR_OOM;
+    const int gp = sm_count() * 8;
+    pack_mats_p32<<<gp, 256, 0, a.stream>>>(g.V, 4, a.U, mu.as<float2>());
+    pack_mats_p32<<<gp, 256, 0, a.stream>>>(g.V, 8, a.W, mw.as<float2>());
+    const SW32 opf{GaugeP32{mu.as<float2>(), g.V}, TransP32{mw.as<float2>(), g.V}};
+    return run_cgne<SW64, SW32, true>(g, opd, opf, a);
+  }
+  return SW_ERR_ARG;
+}
+
+}  // namespace swc

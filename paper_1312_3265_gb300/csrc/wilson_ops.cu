@@ -1,0 +1,45 @@
+// Wilson operator: FP64 apply (C ABI) and batched CGNE.  r = 1 uses the
+// spin-projected hop, other r the full 4-spinor hop.
+#include "driver.cuh"
+
+namespace swc {
+
+template <bool R1> using W64 = WOp<double, GaugeC64, VecC64, R1>;
+template <bool R1> using W32 = WOp<float, GaugeP32, VecP32, R1>;
+
+template <bool R1>
+static int apply_impl(const Geom& g, const double2* U, const double2* in, double2* out, double mass, double r,
+                      int dagger, cudaStream_t st) {
+  const W64<R1> op{GaugeC64{U}};
+  const int gx = (g.V + 127) / 128;
+  apply_kernel<double, W64<R1>><<<dim3(gx, 1), 128, 0, st>>>(g, op, VecC64<12>{const_cast<double2*>(in)},
+                                                             VecC64<12>{out}, mass, nullptr, 0, r, dagger,
+                                                             nullptr, 0);
+  return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
+int wilson_apply_f64(const Geom& g, const double2* U, const double2* in, double2* out, double mass, double r,
+                     int dagger, cudaStream_t st) {
+  return (r == 1.0) ? apply_impl<true>(g, U, in, out, mass, r, dagger, st)
+                    : apply_impl<false>(g, U, in, out, mass, r, dagger, st);
+}
+
+template <bool R1>
+static int cgne_impl(const Geom& g, const SolveArgs& a) {
+  const W64<R1> opd{GaugeC64{a.U}};
+  if (a.precision == SW_PREC_F64) return run_cgne<W64<R1>, W64<R1>, false>(g, opd, opd, a);
+  if (a.precision == SW_PREC_F32_RELIABLE) {
+    DevMem mu;
+    if (!mu.alloc(sizeof(float2) * 36 * (size_t)g.V, a.stream)) return SW_ERR_OOM;
+    pack_mats_p32<<<sm_count() * 8, 256, 0, a.stream>>>(g.V, 4, a.U, mu.as<float2>());
+    const W32<R1> opf{GaugeP32{mu.as<float2>(), g.V}};
+    return run_cgne<W64<R1>, W32<R1>, true>(g, opd, opf, a);
+  }
+  return SW_ERR_ARG;
+}
+
+int wilson_cgne(const Geom& g, const SolveArgs& a) {
+  return (a.r == 1.0) ? cgne_impl<true>(g, a) : cgne_impl<false>(g, a);
+}
+
+}  // namespace swc

@@ -1,0 +1,159 @@
+"""GPU CGNE (Eq. 2) against the oracle, through the C ABI.
+
+Bar: FP64 true relative residual |b - A x|/|b| <= tol (1e-8, recomputed by the
+oracle's operator on the GPU's x), solution within 1e-6 relative of the
+oracle's CG solution (solved to 1e-12), FP64 iteration counts within 2% (or 2
+iterations) of the oracle's at the same tolerance.
+"""
+import numpy as np
+import pytest
+
+import lattice_synth as ls
+from oracle import Lattice, operators as ops
+from oracle.cg import cgne
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1312_3265_gb300 as m
+    m.lib()
+    return m
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+class Problem:
+    def __init__(self, sw, dims, op, seed, eps, mass, apbc=False, r=1.0):
+        import torch
+        self.dims, self.op, self.mass, self.apbc, self.r = dims, op, mass, apbc, r
+        self.lat = Lattice(dims, apbc)
+        self.Uh = ls.su3_links(dims, seed, eps)
+        self.U = dev(self.Uh)
+        self.U4 = self.lat.links(self.Uh)
+        self.nc = 3 if op == sw.SW_OP_STAGGERED_WILSON else 12
+        self.internal = (3,) if self.nc == 3 else (4, 3)
+        self.W = None
+        if self.nc == 3:
+            self.W = torch.empty((self.lat.volume, 8, 3, 3), dtype=torch.complex128, device="cuda")
+            sw.sw_hypercube_build(dims, self.U, self.W)
+
+    def D(self, v, dag=False):
+        if self.nc == 3:
+            return ops.sw_dslash(self.lat, self.U4, v, self.mass, self.r, dag)
+        return ops.wilson_dslash(self.lat, self.U4, v, self.mass, self.r, dag)
+
+    def field(self, flat):
+        return self.lat.field(flat.reshape((-1,) + self.internal), self.internal)
+
+    def oracle(self, chi_flat, tol):
+        x, info = cgne(lambda v: self.D(v), lambda v: self.D(v, True), self.field(chi_flat), tol, 100000)
+        return x.reshape(-1), info
+
+    def true_resid(self, chi_flat, x_flat):
+        b = self.D(self.field(chi_flat), True)
+        r = b - self.D(self.D(self.field(x_flat)), True)
+        return np.linalg.norm(r) / np.linalg.norm(b)
+
+    def solve(self, sw, chi_flat, tol, prec, max_iter=100000, x0=None):
+        import torch
+        chi = dev(chi_flat.reshape((-1,) + self.internal))
+        x = torch.zeros_like(chi) if x0 is None else dev(x0.reshape((-1,) + self.internal))
+        info = sw.cgne_solve(self.dims, self.op, self.U, self.W, chi, x, self.mass, self.r, tol, max_iter, prec,
+                             self.apbc)
+        torch.cuda.synchronize()
+        return x.cpu().numpy().reshape(-1), info
+
+
+def check(sw, P, chi, prec, tol=1e-8):
+    x, info = P.solve(sw, chi, tol, prec)
+    assert info.status == sw.SW_OK
+    assert info.true_rel_resid <= tol
+    assert P.true_resid(chi, x) <= tol * 1.01
+    ref, _ = P.oracle(chi, 1e-12)
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-6
+    return x, info
+
+
+def test_small_workload_sw(sw):
+    """4^4 staggered Wilson: eps = 0.3 links from seed 0, r = 1, m = 0.05, point
+    source at the origin, colour 0, tol 1e-8."""
+    P = Problem(sw, (4, 4, 4, 4), sw.SW_OP_STAGGERED_WILSON, 0, ls.LINK_EPS_SMALL, 0.05)
+    chi = ls.point_source(P.dims, 3, 0).reshape(-1)
+    _, info = check(sw, P, chi, sw.SW_PREC_F64)
+    _, oinfo = P.oracle(chi, 1e-8)
+    assert abs(info.iters - oinfo["iters"]) <= max(2, 0.02 * oinfo["iters"])
+    check(sw, P, chi, sw.SW_PREC_F32_RELIABLE)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("alpha", [0, 7])
+def test_small_workload_wilson(sw, prec, alpha):
+    P = Problem(sw, (4, 4, 4, 4), sw.SW_OP_WILSON, 0, ls.LINK_EPS_SMALL, 0.05)
+    chi = ls.point_source(P.dims, 12, alpha).reshape(-1)
+    _, info = check(sw, P, chi, prec)
+    if prec == sw.SW_PREC_F64:
+        _, oinfo = P.oracle(chi, 1e-8)
+        assert abs(info.iters - oinfo["iters"]) <= max(2, 0.02 * oinfo["iters"])
+
+
+@pytest.mark.parametrize("op", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ragged_antiperiodic(sw, op, prec):
+    P = Problem(sw, (6, 6, 4, 6), op, 2, ls.PLAQ_EPS, 0.1, apbc=True)
+    chi = ls.gaussian_source(P.dims, P.nc, 3).reshape(-1)
+    check(sw, P, chi, prec)
+
+
+def test_wilson_general_r(sw):
+    P = Problem(sw, (4, 4, 2, 4), sw.SW_OP_WILSON, 5, 0.4, 0.1, r=0.75)
+    chi = ls.gaussian_source(P.dims, 12, 1).reshape(-1)
+    check(sw, P, chi, sw.SW_PREC_F64)
+    check(sw, P, chi, sw.SW_PREC_F32_RELIABLE)
+
+
+def test_edge_cases(sw):
+    P = Problem(sw, (2, 2, 2, 2), sw.SW_OP_STAGGERED_WILSON, 1, 0.3, 0.1)
+    # zero source: x = 0 exactly, even from a non-zero guess
+    zero = np.zeros(P.lat.volume * 3, dtype=np.complex128)
+    x, info = P.solve(sw, zero, 1e-8, 0, x0=np.ones_like(zero))
+    assert info.status == sw.SW_OK and np.all(x == 0)
+    # max_iter reached: status SW_NOT_CONVERGED, true residual reported
+    P4 = Problem(sw, (4, 4, 4, 4), sw.SW_OP_WILSON, 0, 0.3, 0.01)
+    chi = ls.point_source(P4.dims, 12, 0).reshape(-1)
+    x, info = P4.solve(sw, chi, 1e-10, 0, max_iter=3)
+    assert info.status == sw.SW_NOT_CONVERGED and info.iters == 3
+    assert abs(info.true_rel_resid - P4.true_resid(chi, x)) < 1e-6
+    # the guess is used: starting from the solution needs no iteration
+    xs, _ = P4.solve(sw, chi, 1e-9, 0)
+    _, info = P4.solve(sw, chi, 1e-8, 0, x0=xs)
+    assert info.status == sw.SW_OK and info.iters == 0
+    # a NaN source is reported, not iterated on
+    bad = chi.copy()
+    bad[5] = np.nan
+    with pytest.raises(sw.SWError) as e:
+        P4.solve(sw, bad, 1e-8, 1)
+    assert e.value.code == -5
+    # free field on 2^4: CG ends in at most 2 iterations (2 distinct eigenvalues)
+    F = Problem(sw, (2, 2, 2, 2), sw.SW_OP_STAGGERED_WILSON, 1, 0.0, 0.1)
+    chi = ls.gaussian_source(F.dims, 3, 4).reshape(-1)
+    _, info = F.solve(sw, chi, 1e-12, 0)
+    assert info.status == sw.SW_OK and info.iters <= 2
+
+
+def test_full_size_solve(sw):
+    """16^3x32, mean plaquette 0.59 links: mixed-precision solves of both operators
+    meet the FP64 true residual checked by the oracle's operator."""
+    for op in (sw.SW_OP_STAGGERED_WILSON, sw.SW_OP_WILSON):
+        P = Problem(sw, (16, 16, 16, 32), op, 0, ls.PLAQ_EPS, 0.1)
+        chi = ls.point_source(P.dims, P.nc, 0).reshape(-1)
+        x, info = P.solve(sw, chi, 1e-8, sw.SW_PREC_F32_RELIABLE)
+        assert info.status == sw.SW_OK and info.true_rel_resid <= 1e-8
+        assert P.true_resid(chi, x) <= 1.01e-8
