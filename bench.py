@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""CGNE throughput on the paper-shaped workload (Sec. 3 of arXiv:1312.3265).
+
+Workload (one "step" = one gauge configuration, every row of the hot path):
+  16^3x32 lattice, SU(3) links exp(i eps H) with eps tuned to mean plaquette
+  0.59 (stand-in for the paper's quenched beta = 6 ensemble, which is not
+  available), configuration seed = step index mod 10;
+  hypercube transports built on the device for that configuration;
+  staggered Wilson (r = 1): 4 bare masses x 3 colour point sources = 12 solves;
+  Wilson (r = 1):           4 bare masses x 12 spin-colour point sources = 48 solves;
+  unpreconditioned CGNE (Eq. 2) to an FP64 true relative residual of 1e-8,
+  FP32 inner iterations with FP64 reliable updates, one batched call per
+  operator.
+value = solves per second (device-resident inputs); e2e = the same through
+the public API with inputs copied from pinned host memory and solutions
+copied back inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CG solves/sec to 1e-8 residual and Dslash GB/s vs HBM roofline; p50/p99 latency"
+DIMS = (16, 16, 16, 32)
+MASSES = (0.02, 0.05, 0.1, 0.2)
+TOL = 1e-8
+R_WILSON = 1.0
+N_SEEDS = 10
+WORKLOAD = "16^3x32 paper-shaped CGNE: staggered Wilson 4 masses x 3 colour sources + Wilson 4 masses x 12 spin-colour sources per configuration"
+
+# Mean CG iterations per (operator, mass) of the workload above, used only to
+# turn the CPU oracle's seconds per iteration into solves/s in the reference
+# arm (which cannot afford full solves).  Measured with this bench's
+# reliable-update solves on configurations 3-5.
+ITERS_TABLE = {"sw": {0.02: 41.0, 0.05: 39.0, 0.1: 36.9, 0.2: 32.0},
+               "wilson": {0.02: 118.0, 0.05: 113.6, 0.1: 107.0, 0.2: 94.9}}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "f64"], default="mixed")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def seed_for(step, rank, world):
+    return (step * world + rank) % N_SEEDS
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        busy = [v for v in sm if v > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(busy) if busy else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ workload inputs
+def host_inputs(seeds):
+    import lattice_synth as ls
+    V = ls.volume(DIMS)
+    U = {s: ls.su3_links(DIMS, s, ls.PLAQ_EPS) for s in seeds}
+    chi_sw = np.zeros((len(MASSES) * 3, V, 3), dtype=np.complex128)
+    m_sw = []
+    for i, m in enumerate(MASSES):
+        for a in range(3):
+            chi_sw[3 * i + a] = ls.point_source(DIMS, 3, a)
+            m_sw.append(m)
+    chi_w = np.zeros((len(MASSES) * 12, V, 4, 3), dtype=np.complex128)
+    m_w = []
+    for i, m in enumerate(MASSES):
+        for a in range(12):
+            chi_w[12 * i + a] = ls.point_source(DIMS, 12, a).reshape(V, 4, 3)
+            m_w.append(m)
+    return U, chi_sw, m_sw, chi_w, m_w
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import paper_1312_3265_gb300 as sw
+
+    rank, world, local = dist_env()
+    use_dist = world > 1
+    if use_dist:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if use_dist else 0)
+    torch.cuda.set_device(dev)
+    sw.lib()
+    prec = sw.SW_PREC_F32_RELIABLE if args.precision == "mixed" else sw.SW_PREC_F64
+    K, Wm = args.steps, args.warmup
+    seeds = sorted({seed_for(s, rank, world) for s in range(K + Wm)})
+    Uh, chi_sw_h, m_sw, chi_w_h, m_w = host_inputs(seeds)
+    V = int(np.prod(DIMS))
+
+    U = {s: torch.from_numpy(Uh[s]).to(dev) for s in seeds}
+    W = torch.empty((V, 8, 3, 3), dtype=torch.complex128, device=dev)
+    chi_sw = torch.from_numpy(chi_sw_h).to(dev)
+    chi_w = torch.from_numpy(chi_w_h).to(dev)
+    x_sw = torch.empty_like(chi_sw)
+    x_w = torch.empty_like(chi_w)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(seed, Ud, csw, cw, xsw, xw):
+        sw.sw_hypercube_build(DIMS, Ud, W, stream=stream)
+        xsw.zero_()
+        rc1, inf_sw = sw.cgne_solve_batch(DIMS, sw.SW_OP_STAGGERED_WILSON, Ud, W, csw, xsw, m_sw, 1.0, TOL,
+                                          100000, prec, stream=stream)
+        xw.zero_()
+        rc2, inf_w = sw.cgne_solve_batch(DIMS, sw.SW_OP_WILSON, Ud, None, cw, xw, m_w, R_WILSON, TOL, 100000,
+                                         prec, stream=stream)
+        for inf in inf_sw + inf_w:
+            if inf.status != sw.SW_OK or not (inf.true_rel_resid <= TOL):
+                raise RuntimeError(f"solve failed: {inf}")
+        return inf_sw, inf_w
+
+    for s in range(Wm):
+        step(seed_for(s, rank, world), U[seed_for(s, rank, world)], chi_sw, chi_w, x_sw, x_w)
+
+    # ---- timed region: device-resident inputs
+    clocks = ClockSampler(dev.index)
+    sw.sw_profile_reset()
+    sw.sw_profile_enable(True)
+    launches0 = sw.sw_kernel_launches()
+    if use_dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for s in range(Wm, Wm + K):
+        sd = seed_for(s, rank, world)
+        infos.append(step(sd, U[sd], chi_sw, chi_w, x_sw, x_w))
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = sw.sw_kernel_launches() - launches0
+    sw.sw_profile_enable(False)
+    prof = sw.sw_profile_read()
+    if use_dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+
+    n_solves = (len(m_sw) + len(m_w)) * K * world
+    value = n_solves / (ms / 1e3)
+
+    # ---- end to end through the public API, host buffers in pinned memory
+    e2e = None
+    if not args.no_e2e:
+        U_pin = {s: torch.from_numpy(Uh[s]).pin_memory() for s in seeds}
+        csw_pin = torch.from_numpy(chi_sw_h).pin_memory()
+        cw_pin = torch.from_numpy(chi_w_h).pin_memory()
+        xsw_pin = torch.empty(chi_sw_h.shape, dtype=torch.complex128).pin_memory()
+        xw_pin = torch.empty(chi_w_h.shape, dtype=torch.complex128).pin_memory()
+        Ud = torch.empty_like(U[seeds[0]])
+        csw_d, cw_d = torch.empty_like(chi_sw), torch.empty_like(chi_w)
+        if use_dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for s in range(Wm, Wm + K):
+            sd = seed_for(s, rank, world)
+            Ud.copy_(U_pin[sd], non_blocking=True)
+            csw_d.copy_(csw_pin, non_blocking=True)
+            cw_d.copy_(cw_pin, non_blocking=True)
+            step(sd, Ud, csw_d, cw_d, x_sw, x_w)
+            xsw_pin.copy_(x_sw, non_blocking=True)
+            xw_pin.copy_(x_w, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ems = f0.elapsed_time(f1)
+        if use_dist:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        h2d = Uh[seeds[0]].nbytes + chi_sw_h.nbytes + chi_w_h.nbytes
+        d2h = chi_sw_h.nbytes + chi_w_h.nbytes
+        e2e = {"value": n_solves / (ems / 1e3), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": ems / K}
+
+    # ---- per-operator statistics
+    it_sw = [i.iters for st in infos for i in st[0]]
+    it_w = [i.iters for st in infos for i in st[1]]
+    by_mass = {"sw": {}, "wilson": {}}
+    for st in infos:
+        for m, i in zip(m_sw, st[0]):
+            by_mass["sw"].setdefault(m, []).append(i.iters)
+        for m, i in zip(m_w, st[1]):
+            by_mass["wilson"].setdefault(m, []).append(i.iters)
+    lat_sw = [st[0][0].seconds * 1e3 for st in infos]
+    lat_w = [st[1][0].seconds * 1e3 for st in infos]
+    lats = sorted([v for v in lat_sw for _ in m_sw] + [v for v in lat_w for _ in m_w])
+
+    peak, peak_kind = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
+    roof = None
+    if dom:
+        name, d = dom
+        ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_launch": d["bytes"] / d["launches"], "launch_ms": d["ms"] / d["launches"]}
+    kernels = {k: {"launches": v["launches"], "ms_per_launch": round(v["ms"] / v["launches"], 4),
+                   "GB/s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1),
+                   "frac_hbm": round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / peak, 4)}
+               for k, v in prof.items()}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": K,
+        "warmup": Wm, "ms_per_step": round(ms / K, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == sw.SW_PREC_F32_RELIABLE else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "masses": list(MASSES),
+                   "solves_per_step": len(m_sw) + len(m_w), "tol": TOL, "r": 1.0,
+                   "precision": args.precision, "configurations": "seeds 0-9, mean plaquette 0.59",
+                   "l2": "inputs larger than L2: a step touches ~10 GB and each step uses a new configuration",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": ck, "gpu_launches": int(launches), "roofline": roof, "kernels": kernels,
+        "latency_ms": {"p50": round(float(np.percentile(lats, 50)), 2),
+                       "p99": round(float(np.percentile(lats, 99)), 2),
+                       "note": "time to solution of each solve's batch"},
+        "operators": {
+            "sw": {"solves": len(m_sw), "iters_mean": float(np.mean(it_sw)),
+                   "batch_ms_mean": float(np.mean(lat_sw)),
+                   "iters_by_mass": {str(m): float(np.mean(v)) for m, v in by_mass["sw"].items()}},
+            "wilson": {"solves": len(m_w), "iters_mean": float(np.mean(it_w)),
+                       "batch_ms_mean": float(np.mean(lat_w)),
+                       "iters_by_mass": {str(m): float(np.mean(v)) for m, v in by_mass["wilson"].items()}},
+            "iters_ratio_w_over_sw": float(np.mean(it_w) / np.mean(it_sw)),
+            "paper_context": "Sec. 3: iteration ratio W/SW almost 2 on thermalised beta=6 fields "
+                             "(not comparable: synthetic links)"},
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(Uh[seeds[0]], by_mass)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if use_dist:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_iteration_seconds(Uflat, k_sw=2, k_w=3):
+    """Seconds per CG iteration of the oracle (numpy FP64) on the 16^3x32
+    systems at m = 0.1: cg() run for k iterations, minus its final true-residual
+    recomputation (two A applications, timed separately)."""
+    import lattice_synth as ls
+    from oracle import Lattice, operators as ops
+    from oracle.cg import cg
+    lat = Lattice(DIMS)
+    U4 = lat.links(Uflat)
+    out = {}
+    for name, k, nc in (("sw", k_sw, 3), ("wilson", k_w, 12)):
+        internal = (3,) if nc == 3 else (4, 3)
+        if nc == 3:
+            A = lambda v: ops.sw_dslash(lat, U4, ops.sw_dslash(lat, U4, v, 0.1), 0.1, dagger=True)
+        else:
+            A = lambda v: ops.wilson_dslash(lat, U4, ops.wilson_dslash(lat, U4, v, 0.1), 0.1, dagger=True)
+        b = lat.field(ls.point_source(DIMS, nc, 0).reshape((-1,) + internal), internal)
+        t0 = time.perf_counter()
+        A(b)
+        tA = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        cg(A, b, 0.0, k)
+        tk = time.perf_counter() - t0
+        out[name] = {"s_per_iter": (tk - 2 * tA) / k, "s_per_A": tA, "iters_sampled": k}
+    return out
+
+
+def cpu_solves_per_s(per_iter, iters_by_mass):
+    """Solves/s of the oracle on one configuration's 60 solves: per solve, its
+    iteration count times the seconds per iteration, plus b = (D+m)^+ chi and the
+    final residual (about 1.5 A applications)."""
+    total, n = 0.0, 0
+    for op, nsrc in (("sw", 3), ("wilson", 12)):
+        for m, its in iters_by_mass[op].items():
+            mean_it = float(np.mean(its)) if isinstance(its, (list, tuple)) else float(its)
+            total += nsrc * (mean_it * per_iter[op]["s_per_iter"] + 1.5 * per_iter[op]["s_per_A"])
+            n += nsrc
+    return n / total
+
+
+def cpu_baseline(Uflat, iters_by_mass):
+    t0 = time.perf_counter()
+    per = oracle_iteration_seconds(Uflat)
+    spent = time.perf_counter() - t0
+    return {"value": round(cpu_solves_per_s(per, iters_by_mass), 6), "unit": "solves/s", "cores": 1,
+            "kind": "oracle",
+            "sample": (f"oracle (numpy FP64, single thread) CG on 16^3x32 seed-0 links, m=0.1: "
+                       f"{per['sw']['iters_sampled']} staggered Wilson + {per['wilson']['iters_sampled']} "
+                       f"Wilson iterations timed ({spent:.1f} s); s/iter SW {per['sw']['s_per_iter']:.2f}, "
+                       f"W {per['wilson']['s_per_iter']:.2f}; scaled to the workload's 60 solves with "
+                       f"this run's mean iteration counts per operator and mass")}
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import lattice_synth as ls
+    if not all(ITERS_TABLE[op][m] > 0 for op in ITERS_TABLE for m in MASSES):
+        print(json.dumps({"impl": "reference", "unavailable": "iteration table not filled"}))
+        return
+    vals = []
+    for s in range(args.warmup + args.steps):
+        Uflat = ls.su3_links(DIMS, s % N_SEEDS, ls.PLAQ_EPS)
+        t0 = time.perf_counter()
+        per = oracle_iteration_seconds(Uflat, 1, 1)
+        v = cpu_solves_per_s(per, ITERS_TABLE)
+        if s >= args.warmup:
+            vals.append((v, time.perf_counter() - t0))
+    value = float(np.mean([v for v, _ in vals]))
+    ms = float(np.mean([t for _, t in vals])) * 1e3
+    sample = ("per step: 1 staggered Wilson + 1 Wilson CG iteration of the oracle (numpy FP64, single "
+              "thread) on that step's 16^3x32 configuration at m=0.1, scaled to the 60 solves with the "
+              "mean iteration counts per operator and mass of the workload")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "masses": list(MASSES),
+                   "tol": TOL, "parallelism": "cpu oracle, rank 0 only"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

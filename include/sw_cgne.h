@@ -125,6 +125,26 @@ int cgne_solve_batch(const sw_lattice* lat, int op, const void* U, const void* W
                      const void* chi, void* x, const double* masses, double r, double tol,
                      int max_iter, int precision, sw_solve_info* infos, void* stream);
 
+/* Kernel timing.  Instrumentation with no counterpart in the paper.  While
+ * enabled, the first iteration of every chunk of CG iterations has its two
+ * stencil launches (k1: t = (D+m) p with |t|^2; k2: (D+m)^+ t with the x, r
+ * updates and |r|^2) bracketed by CUDA events on the solve's stream.  After
+ * each solve completes, the per-class totals grow by: launches, event time
+ * (ms), and the algorithmic bytes of those launches (links and transports
+ * once per launch, plus each running system's vectors read and written).
+ * Classes are named "<operator>.<kernel>.<precision>", e.g. "sw.k1.f32".
+ * Process-wide and thread-safe; disabled by default. */
+int sw_profile_enable(int on);
+/* Total kernel launches this library has issued in the process (always on). */
+long long sw_kernel_launches(void);
+int sw_profile_reset(void);
+/* Number of classes recorded so far. */
+int sw_profile_count(void);
+/* Class i (0 <= i < count): name into name[name_len], totals into the other
+ * HOST pointers (each may be NULL).  Returns SW_ERR_ARG for a bad index. */
+int sw_profile_entry(int i, char* name, int name_len, long long* launches, double* total_ms,
+                     double* total_bytes);
+
 /* Human-readable name of a status code (static string). */
 const char* sw_status_string(int status);
 

@@ -69,6 +69,15 @@ def lib():
         L.cgne_solve.argtypes = [lat, i, vp, vp, vp, vp, d, d, d, i, i, ctypes.POINTER(_Info), vp]
         L.cgne_solve_batch.argtypes = [lat, i, vp, vp, i, vp, vp, ctypes.POINTER(ctypes.c_double), d, d, i, i,
                                        ctypes.POINTER(_Info), vp]
+        L.sw_kernel_launches.argtypes = []
+        L.sw_kernel_launches.restype = ctypes.c_longlong
+        L.sw_profile_enable.argtypes = [i]
+        L.sw_profile_reset.argtypes = []
+        L.sw_profile_count.argtypes = []
+        L.sw_profile_entry.argtypes = [i, ctypes.c_char_p, i, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(d), ctypes.POINTER(d)]
+        for f in ("sw_profile_enable", "sw_profile_reset", "sw_profile_count", "sw_profile_entry"):
+            getattr(L, f).restype = i
         L.sw_status_string.argtypes = [i]
         L.sw_status_string.restype = ctypes.c_char_p
         for f in ("sw_hypercube_build", "sw_dslash_apply", "wilson_dslash_apply", "cgne_solve", "cgne_solve_batch"):
@@ -150,3 +159,28 @@ def cgne_solve_batch(dims, op, U, W, chi, x, masses, r=1.0, tol=1e-8, max_iter=1
                                 float(r), float(tol), int(max_iter), int(precision), infos, _stream(stream))
     _check(rc, "cgne_solve_batch")
     return rc, [SolveInfo.from_c(infos[i]) for i in range(n)]
+
+
+def sw_profile_enable(on=True):
+    lib().sw_profile_enable(int(bool(on)))
+
+
+def sw_profile_reset():
+    lib().sw_profile_reset()
+
+
+def sw_profile_read():
+    """{class: {"launches", "ms", "bytes"}} accumulated since the last reset."""
+    out = {}
+    L = lib()
+    for i in range(L.sw_profile_count()):
+        name = ctypes.create_string_buffer(64)
+        n, ms, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        _check(L.sw_profile_entry(i, name, 64, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)),
+               "sw_profile_entry")
+        out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "bytes": by.value}
+    return out
+
+
+def sw_kernel_launches():
+    return int(lib().sw_kernel_launches())

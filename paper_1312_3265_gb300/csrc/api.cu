@@ -1,7 +1,12 @@
 // C ABI entry points (include/sw_cgne.h): argument checks, then dispatch.
+#include <atomic>
 #include <chrono>
 #include <cstdint>
+#include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -19,6 +24,70 @@ int sm_count() {
     cached[dev] = n;
   }
   return cached[dev];
+}
+
+// ---------------------------------------------------------------- profiler
+namespace {
+struct ProfStat {
+  long long launches = 0;
+  double ms = 0.0;
+  double bytes = 0.0;
+};
+struct Pending {
+  std::string cls;
+  cudaEvent_t a, b;
+  double bytes;
+};
+std::mutex g_prof_mu;
+std::atomic<long long> g_launches{0};
+bool g_prof_on = false;
+std::map<std::string, ProfStat> g_prof;
+std::vector<cudaEvent_t> g_pool;
+thread_local std::vector<Pending> t_pending;
+thread_local std::vector<cudaEvent_t> t_used;
+}  // namespace
+
+void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+bool prof_enabled() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  return g_prof_on;
+}
+
+cudaEvent_t prof_event() {
+  cudaEvent_t e = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_pool.empty()) {
+      e = g_pool.back();
+      g_pool.pop_back();
+    }
+  }
+  if (!e) cudaEventCreate(&e);
+  t_used.push_back(e);
+  return e;
+}
+
+void prof_push(const char* cls, cudaEvent_t a, cudaEvent_t b, double bytes) {
+  t_pending.push_back(Pending{cls, a, b, bytes});
+}
+
+void prof_flush() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (const Pending& p : t_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      ProfStat& s = g_prof[p.cls];
+      s.launches += 1;
+      s.ms += ms;
+      s.bytes += p.bytes;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  t_pending.clear();
+  for (cudaEvent_t e : t_used) g_pool.push_back(e);
+  t_used.clear();
 }
 
 static int make_geom(const sw_lattice* lat, Geom* g) {
@@ -104,6 +173,41 @@ const char* sw_status_string(int s) {
     case SW_ERR_ARG: return "bad argument";
     default: return "unknown status";
   }
+}
+
+long long sw_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int sw_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+  return SW_OK;
+}
+
+int sw_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.clear();
+  return SW_OK;
+}
+
+int sw_profile_count(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  return (int)g_prof.size();
+}
+
+int sw_profile_entry(int i, char* name, int name_len, long long* launches, double* total_ms,
+                     double* total_bytes) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (i < 0 || i >= (int)g_prof.size()) return SW_ERR_ARG;
+  auto it = g_prof.begin();
+  std::advance(it, i);
+  if (name && name_len > 0) {
+    std::strncpy(name, it->first.c_str(), name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (launches) *launches = it->second.launches;
+  if (total_ms) *total_ms = it->second.ms;
+  if (total_bytes) *total_bytes = it->second.bytes;
+  return SW_OK;
 }
 
 int sw_hypercube_build(const sw_lattice* lat, const void* U, void* W, void* stream) {

@@ -91,6 +91,8 @@ template <typename T, int N> struct CV { cx<T> c[N]; };
 template <typename T, typename G, typename Wt, template <int> class VA>
 struct SWOp {
   static constexpr int NC = 3;
+  static constexpr int kMats = 12;  // 4 links + 8 stored hypercube transports per site
+  static constexpr const char* kName = "sw";
   using Vec = VA<3>;
   G U;
   Wt W;
@@ -106,6 +108,8 @@ struct SWOp {
 template <typename T, typename G, template <int> class VA, bool R1>
 struct WOp {
   static constexpr int NC = 12;
+  static constexpr int kMats = 4;   // 4 links per site
+  static constexpr const char* kName = "wilson";
   using Vec = VA<12>;
   G U;
   __device__ __forceinline__ CV<T, 12> apply(const Geom& g, int n, const Vec& in, T m, T r, bool dag) const {

@@ -17,6 +17,7 @@
 #pragma once
 #include <chrono>
 #include <mutex>
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -91,10 +92,64 @@ inline int status_to_code(int st) {
   }
 }
 
+// Device workspace of one batched solve, carved from a single block.
+struct Workspace {
+  double2 *b64, *r64, *t64, *p64;   // FP64 canonical; p64 only in F64 mode
+  float2 *r32, *p32, *t32, *x32;    // FP32 planar; MIXED mode only
+  SysState* S;
+  double* partials;
+  unsigned* tickets;
+  double* mass;
+};
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Bytes of workspace for nsys systems of NC complex components per site.
+inline size_t workspace_bytes(int V, int NC, int nsys, bool mixed) {
+  const size_t n = (size_t)V * NC * nsys;
+  const size_t ntiles = (size_t)(V + kTile - 1) / kTile;
+  size_t b = 3 * align_up(sizeof(double2) * n);
+  b += mixed ? 4 * align_up(sizeof(float2) * n) : align_up(sizeof(double2) * n);
+  b += align_up(sizeof(SysState) * nsys) + align_up(sizeof(double) * ntiles * nsys) +
+       align_up(sizeof(unsigned) * nsys) + align_up(sizeof(double) * nsys);
+  return b;
+}
+
+inline Workspace carve_workspace(void* base, int V, int NC, int nsys, bool mixed) {
+  const size_t n = (size_t)V * NC * nsys;
+  const size_t ntiles = (size_t)(V + kTile - 1) / kTile;
+  char* c = static_cast<char*>(base);
+  auto take = [&](size_t bytes) {
+    void* p = c;
+    c += align_up(bytes);
+    return p;
+  };
+  Workspace w{};
+  w.b64 = (double2*)take(sizeof(double2) * n);
+  w.r64 = (double2*)take(sizeof(double2) * n);
+  w.t64 = (double2*)take(sizeof(double2) * n);
+  if (mixed) {
+    w.r32 = (float2*)take(sizeof(float2) * n);
+    w.p32 = (float2*)take(sizeof(float2) * n);
+    w.t32 = (float2*)take(sizeof(float2) * n);
+    w.x32 = (float2*)take(sizeof(float2) * n);
+  } else {
+    w.p64 = (double2*)take(sizeof(double2) * n);
+  }
+  w.S = (SysState*)take(sizeof(SysState) * nsys);
+  w.partials = (double*)take(sizeof(double) * ntiles * nsys);
+  w.tickets = (unsigned*)take(sizeof(unsigned) * nsys);
+  w.mass = (double*)take(sizeof(double) * nsys);
+  return w;
+}
+
 // OpD: FP64 operator on canonical storage.  OpF: the inner-iteration operator
-// (FP32 planar when MIXED, else the same as OpD).
+// (FP32 planar when MIXED, else the same as OpD).  ws: device workspace from
+// carve_workspace; hs: host array [nsys] for the status words.
 template <class OpD, class OpF, bool MIXED>
-int run_cgne(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a) {
+int run_cgne_ws(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a, const Workspace& ws,
+                SysState* hs) {
   using namespace std::chrono;
   const auto t0 = steady_clock::now();
   constexpr int NC = OpD::NC;
@@ -107,27 +162,13 @@ int run_cgne(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a) 
   cudaStream_t st = a.stream;
   const int pstride = (V + kTile - 1) / kTile;  // one partial per reduction tile
 
-  DevMem mb64, mr64, mt64, mp64, mr32, mp32, mt32, mx32, mS, mpart, mtick, mmass;
-  bool ok = mb64.alloc(sizeof(double2) * n * nsys, st) && mr64.alloc(sizeof(double2) * n * nsys, st) &&
-            mt64.alloc(sizeof(double2) * n * nsys, st) && mS.alloc(sizeof(SysState) * nsys, st) &&
-            mpart.alloc(sizeof(double) * pstride * nsys, st) && mtick.alloc(sizeof(unsigned) * nsys, st) &&
-            mmass.alloc(sizeof(double) * nsys, st);
-  if (MIXED)
-    ok = ok && mr32.alloc(sizeof(float2) * n * nsys, st) && mp32.alloc(sizeof(float2) * n * nsys, st) &&
-         mt32.alloc(sizeof(float2) * n * nsys, st) && mx32.alloc(sizeof(float2) * n * nsys, st);
-  else
-    ok = ok && mp64.alloc(sizeof(double2) * n * nsys, st);
-  if (!ok) return SW_ERR_OOM;
+  double2* b64 = ws.b64;
+  double2* r64 = ws.r64;
+  double2* t64 = ws.t64;
+  SysState* S = ws.S;
+  RedBuf rb{ws.partials, ws.tickets, pstride};
+  double* mass_d = ws.mass;
 
-  double2* b64 = mb64.as<double2>();
-  double2* r64 = mr64.as<double2>();
-  double2* t64 = mt64.as<double2>();
-  SysState* S = mS.as<SysState>();
-  RedBuf rb{mpart.as<double>(), mtick.as<unsigned>(), pstride};
-  double* mass_d = mmass.as<double>();
-
-  SysState* hs = nullptr;
-  if (int e = pinned_states(nsys, &hs)) return e;
   for (int i = 0; i < nsys; ++i) {
     SysState s{};
     s.tol2 = a.tol * a.tol;
@@ -153,21 +194,22 @@ int run_cgne(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a) 
   // b = (D+m)^+ chi, |b|^2
   apply_kernel<double, OpD><<<dim3(gA, nsys), kTile, 0, st>>>(g, opd, chi, vb, 0.0, mass_d, n, a.r, 1, nullptr, 0);
   norm_b<NC><<<dim3(gN, nsys), kTile, 0, st>>>(V, b64, n, S, rb);
+  note_launches(2);
 
   VF fr, fp, ft, fx;
   if constexpr (MIXED) {
-    fr = VF{mr32.as<float2>(), V};
-    fp = VF{mp32.as<float2>(), V};
-    ft = VF{mt32.as<float2>(), V};
-    fx = VF{mx32.as<float2>(), V};
-    cudaMemsetAsync(mp32.p, 0, sizeof(float2) * n * nsys, st);
-    cudaMemsetAsync(mx32.p, 0, sizeof(float2) * n * nsys, st);
+    fr = VF{ws.r32, V};
+    fp = VF{ws.p32, V};
+    ft = VF{ws.t32, V};
+    fx = VF{ws.x32, V};
+    cudaMemsetAsync(ws.p32, 0, sizeof(float2) * n * nsys, st);
+    cudaMemsetAsync(ws.x32, 0, sizeof(float2) * n * nsys, st);
   } else {
     fr = vr;
-    fp = VF{mp64.as<double2>()};
+    fp = VF{ws.p64};
     ft = vt;
     fx = vx;
-    cudaMemsetAsync(mp64.p, 0, sizeof(double2) * n * nsys, st);
+    cudaMemsetAsync(ws.p64, 0, sizeof(double2) * n * nsys, st);
   }
 
   // |b| = 0: the solution is x = 0
@@ -191,11 +233,35 @@ int run_cgne(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a) 
     if constexpr (MIXED) demote_r<NC><<<dim3(gV, nsys), 256, 0, st>>>(V, r64, fr.p, n, n, S);
     cg_k3<TF, VF, NC><<<dim3(gV, nsys), 256, 0, st>>>(V, fr, fp, n, S, ST_JUST_UPDATED);
     commit_status<<<(nsys + 127) / 128, 128, 0, st>>>(nsys, S);
+    note_launches(MIXED ? 6 : 4);
   };
-  auto iterate = [&]() {
+  // Algorithmic bytes of one stencil launch (every stored element touched
+  // once): the links (and transports) once per launch, plus per running
+  // system the vectors the kernel reads and writes (k1: p, t; k2: t, p, x and
+  // r read and written).
+  constexpr double kCx = 2.0 * sizeof(TF);
+  const double gauge_bytes = (double)V * OpF::kMats * 9 * kCx;
+  const double vec_bytes = (double)V * NC * kCx;
+  static const std::string cls1 = std::string(OpF::kName) + (MIXED ? ".k1.f32" : ".k1.f64");
+  static const std::string cls2 = std::string(OpF::kName) + (MIXED ? ".k2.f32" : ".k2.f64");
+  auto iterate = [&](int nrun) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    if (nrun > 0) {
+      e0 = prof_event();
+      e1 = prof_event();
+      e2 = prof_event();
+      cudaEventRecord(e0, st);
+    }
     cg_k1<TF, OpF><<<dim3(g1, nsys), kTile, 0, st>>>(g, opf, fp, ft, bp, S, rb);
+    if (nrun > 0) cudaEventRecord(e1, st);
     cg_k2<TF, OpF, VF><<<dim3(g2, nsys), kTile, 0, st>>>(g, opf, ft, fp, fr, fx, bp, n, S, rb);
+    if (nrun > 0) {
+      cudaEventRecord(e2, st);
+      prof_push(cls1.c_str(), e0, e1, gauge_bytes + nrun * 2.0 * vec_bytes);
+      prof_push(cls2.c_str(), e1, e2, gauge_bytes + nrun * 6.0 * vec_bytes);
+    }
     cg_k3<TF, VF, NC><<<dim3(gV, nsys), 256, 0, st>>>(V, fr, fp, n, S, ST_RUNNING);
+    note_launches(3);
   };
 
   // initial residual r = b - A x0 (all systems start in NEED_RU)
@@ -206,10 +272,12 @@ int run_cgne(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a) 
     cudaMemcpyAsync(hs, S, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
     bool need_ru = false, active = false;
+    int nrun = 0;
     for (int i = 0; i < nsys; ++i) {
       const int s = hs[i].status;
       need_ru |= (s == ST_NEED_RU);
       active |= (s == ST_RUNNING || s == ST_NEED_RU || s == ST_JUST_UPDATED);
+      nrun += (s == ST_RUNNING);
     }
     if (!active) break;
     if (round > max_rounds) {
@@ -220,10 +288,12 @@ int run_cgne(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a) 
       reliable_update();
       continue;
     }
-    for (int i = 0; i < kChunk; ++i) iterate();
+    const bool prof = prof_enabled();
+    for (int i = 0; i < kChunk; ++i) iterate((prof && i == 0) ? nrun : 0);
     if (cudaPeekAtLastError() != cudaSuccess) return SW_ERR_CUDA;
   }
   if (cudaGetLastError() != cudaSuccess) return SW_ERR_CUDA;
+  prof_flush();
 
   const double secs = duration<double>(steady_clock::now() - t0).count();
   int worst = SW_OK;
@@ -242,6 +312,18 @@ int run_cgne(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a) 
     if (code > 0 && worst == SW_OK) worst = code;
   }
   return worst;
+}
+
+// Allocating entry: one stream-ordered block of workspace for the call and a
+// pinned host buffer for the status words.
+template <class OpD, class OpF, bool MIXED>
+int run_cgne(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a) {
+  DevMem mem;
+  if (!mem.alloc(workspace_bytes(g.V, OpD::NC, a.nsys, MIXED), a.stream)) return SW_ERR_OOM;
+  SysState* hs = nullptr;
+  if (int e = pinned_states(a.nsys, &hs)) return e;
+  const Workspace ws = carve_workspace(mem.p, g.V, OpD::NC, a.nsys, MIXED);
+  return run_cgne_ws<OpD, OpF, MIXED>(g, opd, opf, a, ws, hs);
 }
 
 }  // namespace swc

@@ -35,4 +35,15 @@ int wilson_cgne(const Geom& g, const SolveArgs& a);
 // Device properties cached per device.
 int sm_count();
 
+// Kernel timing (instrumentation, off by default).  The driver brackets
+// sampled launches with events from a pool; once the solve has synchronised,
+// prof_flush() turns them into per-class launch counts, times and the
+// algorithmic bytes those launches moved.
+bool prof_enabled();
+cudaEvent_t prof_event();
+void prof_push(const char* cls, cudaEvent_t a, cudaEvent_t b, double bytes);
+void prof_flush();
+// Kernel launches issued by the library (all entry points), for the caller's accounting.
+void note_launches(int k);
+
 }  // namespace swc

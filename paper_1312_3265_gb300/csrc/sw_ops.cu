@@ -13,6 +13,7 @@ int sw_apply_f64(const Geom& g, const double2* U, const double2* W, const double
   apply_kernel<double, SW64><<<dim3(gx, 1), 128, 0, st>>>(g, op, VecC64<3>{const_cast<double2*>(in)},
                                                           VecC64<3>{out}, mass, nullptr, 0, r, dagger,
                                                           nullptr, 0);
+  note_launches(1);
   return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
 }
 
@@ -27,6 +28,7 @@ int sw_cgne(const Geom& g, const SolveArgs& a) {
     const int gp = sm_count() * 8;
     pack_mats_p32<<<gp, 256, 0, a.stream>>>(g.V, 4, a.U, mu.as<float2>());
     pack_mats_p32<<<gp, 256, 0, a.stream>>>(g.V, 8, a.W, mw.as<float2>());
+    note_launches(2);
     const SW32 opf{GaugeP32{mu.as<float2>(), g.V}, TransP32{mw.as<float2>(), g.V}};
     return run_cgne<SW64, SW32, true>(g, opd, opf, a);
   }

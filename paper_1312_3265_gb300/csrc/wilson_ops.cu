@@ -15,6 +15,7 @@ static int apply_impl(const Geom& g, const double2* U, const double2* in, double
   apply_kernel<double, W64<R1>><<<dim3(gx, 1), 128, 0, st>>>(g, op, VecC64<12>{const_cast<double2*>(in)},
                                                              VecC64<12>{out}, mass, nullptr, 0, r, dagger,
                                                              nullptr, 0);
+  note_launches(1);
   return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
 }
 
@@ -32,6 +33,7 @@ static int cgne_impl(const Geom& g, const SolveArgs& a) {
     DevMem mu;
     if (!mu.alloc(sizeof(float2) * 36 * (size_t)g.V, a.stream)) return SW_ERR_OOM;
     pack_mats_p32<<<sm_count() * 8, 256, 0, a.stream>>>(g.V, 4, a.U, mu.as<float2>());
+    note_launches(1);
     const W32<R1> opf{GaugeP32{mu.as<float2>(), g.V}};
     return run_cgne<W64<R1>, W32<R1>, true>(g, opd, opf, a);
   }
