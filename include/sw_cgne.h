@@ -125,6 +125,28 @@ int cgne_solve_batch(const sw_lattice* lat, int op, const void* U, const void* W
                      const void* chi, void* x, const double* masses, double r, double tol,
                      int max_iter, int precision, sw_solve_info* infos, void* stream);
 
+/* FP64 CGNE exactly as cgne_solve with SW_PREC_F64, but allocating nothing:
+ * its device workspace is a static array of SW_NOALLOC_SCRATCH_BYTES inside the
+ * library.  The paper has no counterpart; this is for callers that cannot
+ * call cudaMalloc while they run -- code executing during CUDA graph capture,
+ * runtimes whose device memory belongs to another allocator, allocation-free
+ * latency loops.  They pass U, W, chi and x as for cgne_solve.
+ * Limit: the workspace is 4 FP64 vectors of the lattice plus a few KB
+ * (192 B per site for staggered Wilson, 768 B per site for Wilson), so at
+ * most ~174k sites (16^3x32) for staggered Wilson and ~43k (12^3x24) for
+ * Wilson; larger lattices return SW_ERR_ARG before anything is launched.
+ * The array is loaded with the library and every GPU that loads it keeps it
+ * until exit.  The first call on a device looks up the array's address with
+ * cudaGetSymbolAddress (that device must be current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (the solve initialises everything it reads); calls whose
+ * GPU work overlaps race on it and must be serialised by the caller.
+ * Blocks until done, like cgne_solve. */
+#define SW_NOALLOC_SCRATCH_BYTES (32u << 20)
+int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, const void* W,
+                       const void* chi, void* x, double mass, double r, double tol,
+                       int max_iter, sw_solve_info* info, void* stream);
+
 /* Kernel timing.  Instrumentation with no counterpart in the paper.  While
  * enabled, the first iteration of every chunk of CG iterations has its two
  * stencil launches (k1: t = (D+m) p with |t|^2; k2: (D+m)^+ t with the x, r

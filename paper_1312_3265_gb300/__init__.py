@@ -16,5 +16,5 @@ from ._binding import (  # noqa: F401
     SW_PREC_F64, SW_PREC_F32_RELIABLE, SW_PREC_F16_RELIABLE,
     sw_hypercube_build, sw_dslash_apply, wilson_dslash_apply, cgne_solve, cgne_solve_batch,
     sw_status_string, sw_profile_enable, sw_profile_reset, sw_profile_read,
-    sw_kernel_launches,
+    sw_kernel_launches, cgne_solve_noalloc,
 )

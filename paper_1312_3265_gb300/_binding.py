@@ -69,6 +69,8 @@ def lib():
         L.cgne_solve.argtypes = [lat, i, vp, vp, vp, vp, d, d, d, i, i, ctypes.POINTER(_Info), vp]
         L.cgne_solve_batch.argtypes = [lat, i, vp, vp, i, vp, vp, ctypes.POINTER(ctypes.c_double), d, d, i, i,
                                        ctypes.POINTER(_Info), vp]
+        L.cgne_solve_noalloc.argtypes = [lat, i, vp, vp, vp, vp, d, d, d, i, ctypes.POINTER(_Info), vp]
+        L.cgne_solve_noalloc.restype = i
         L.sw_kernel_launches.argtypes = []
         L.sw_kernel_launches.restype = ctypes.c_longlong
         L.sw_profile_enable.argtypes = [i]
@@ -184,3 +186,14 @@ def sw_profile_read():
 
 def sw_kernel_launches():
     return int(lib().sw_kernel_launches())
+
+
+def cgne_solve_noalloc(dims, op, U, W, chi, x, mass, r=1.0, tol=1e-8, max_iter=100000, t_antiperiodic=False,
+                       stream=None):
+    """FP64 CGNE with the library's static device scratch (no allocation)."""
+    info = _Info()
+    rc = lib().cgne_solve_noalloc(_lat(dims, t_antiperiodic), int(op), _ptr(U), _ptr(W), _ptr(chi), _ptr(x),
+                                  float(mass), float(r), float(tol), int(max_iter), ctypes.byref(info),
+                                  _stream(stream))
+    _check(rc, "cgne_solve_noalloc")
+    return SolveInfo.from_c(info)

@@ -90,7 +90,7 @@ void prof_flush() {
   t_used.clear();
 }
 
-static int make_geom(const sw_lattice* lat, Geom* g) {
+int make_geom(const sw_lattice* lat, Geom* g) {
   if (!lat) return SW_ERR_NULL;
   long long V = 1;
   for (int mu = 0; mu < 4; ++mu) {
@@ -124,7 +124,7 @@ static AddrRangeFn addr_range_fn() {
 
 // The buffer must be device (or managed) memory, 16-byte aligned, and its
 // allocation must hold `bytes` from `p` on.
-static int check_buf(const void* p, size_t bytes) {
+int check_buf(const void* p, size_t bytes) {
   if (!p) return SW_ERR_NULL;
   if (reinterpret_cast<uintptr_t>(p) & 15u) return SW_ERR_ALIGN;
   cudaPointerAttributes at;
@@ -142,7 +142,7 @@ static int check_buf(const void* p, size_t bytes) {
   return SW_OK;
 }
 
-static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
   const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
   return x < y + nb && y < x + na;
 }

@@ -32,6 +32,11 @@ int wilson_apply_f64(const Geom& g, const double2* U, const double2* in, double2
 int sw_cgne(const Geom& g, const SolveArgs& a);
 int wilson_cgne(const Geom& g, const SolveArgs& a);
 
+// Argument checks shared by the entry points (api.cu).
+int make_geom(const sw_lattice* lat, Geom* g);
+int check_buf(const void* p, size_t bytes);
+bool overlap(const void* a, size_t na, const void* b, size_t nb);
+
 // Device properties cached per device.
 int sm_count();
 
