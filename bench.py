@@ -58,6 +58,16 @@ def parse():
     ap.add_argument("--precision", choices=["mixed", "f64"], default="mixed")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--delta", type=float, default=None, help="reliable-update delta (library default if unset)")
+    ap.add_argument("--chunk", type=int, default=None, help="CG iterations between status reads")
+    ap.add_argument("--ns-sw", type=int, default=None, help="systems per thread, staggered Wilson FP32 stencils")
+    ap.add_argument("--ns-wilson", type=int, default=None, help="systems per thread, Wilson FP32 stencils")
+    ap.add_argument("--serving-requests", type=int, default=400,
+                    help="requests in the Poisson serving phase (0: skip)")
+    ap.add_argument("--serving-lattices", default="8x8x8x8,12x12x12x24,16x16x16x32,24x24x24x48")
+    ap.add_argument("--no-f64", action="store_true", help="skip the plain-FP64 comparison step")
+    ap.add_argument("--masses", default=None, help="comma-separated bare masses (default: the workload's four)")
+    ap.add_argument("--w-sources", type=int, default=12, help="Wilson spin-colour sources per mass (<= 12)")
     return ap.parse_args()
 
 
@@ -70,7 +80,20 @@ def dist_env():
 
 
 def seed_for(step, rank, world):
+    """Configuration of a replica's step: ranks take disjoint configurations in
+    each step (weak scaling: every rank solves a full configuration)."""
     return (step * world + rank) % N_SEEDS
+
+
+def max_over_ranks(ms, device=None):
+    """Slowest rank's time (the job's time) when running under torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([float(ms)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ------------------------------------------------------------------ clocks
@@ -126,21 +149,21 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ workload inputs
-def host_inputs(seeds):
+def host_inputs(seeds, masses=MASSES, w_sources=12):
     import lattice_synth as ls
     V = ls.volume(DIMS)
     U = {s: ls.su3_links(DIMS, s, ls.PLAQ_EPS) for s in seeds}
-    chi_sw = np.zeros((len(MASSES) * 3, V, 3), dtype=np.complex128)
+    chi_sw = np.zeros((len(masses) * 3, V, 3), dtype=np.complex128)
     m_sw = []
-    for i, m in enumerate(MASSES):
+    for i, m in enumerate(masses):
         for a in range(3):
             chi_sw[3 * i + a] = ls.point_source(DIMS, 3, a)
             m_sw.append(m)
-    chi_w = np.zeros((len(MASSES) * 12, V, 4, 3), dtype=np.complex128)
+    chi_w = np.zeros((len(masses) * w_sources, V, 4, 3), dtype=np.complex128)
     m_w = []
-    for i, m in enumerate(MASSES):
-        for a in range(12):
-            chi_w[12 * i + a] = ls.point_source(DIMS, 12, a).reshape(V, 4, 3)
+    for i, m in enumerate(masses):
+        for a in range(w_sources):
+            chi_w[w_sources * i + a] = ls.point_source(DIMS, 12, a).reshape(V, 4, 3)
             m_w.append(m)
     return U, chi_sw, m_sw, chi_w, m_w
 
@@ -160,9 +183,18 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     sw.lib()
     prec = sw.SW_PREC_F32_RELIABLE if args.precision == "mixed" else sw.SW_PREC_F64
+    if args.delta is not None:
+        sw.sw_set_param(sw.SW_PARAM_RELIABLE_DELTA, args.delta)
+    if args.chunk is not None:
+        sw.sw_set_param(sw.SW_PARAM_CHUNK, args.chunk)
+    if args.ns_sw is not None:
+        sw.sw_set_param(sw.SW_PARAM_NS_SW, args.ns_sw)
+    if args.ns_wilson is not None:
+        sw.sw_set_param(sw.SW_PARAM_NS_WILSON, args.ns_wilson)
     K, Wm = args.steps, args.warmup
     seeds = sorted({seed_for(s, rank, world) for s in range(K + Wm)})
-    Uh, chi_sw_h, m_sw, chi_w_h, m_w = host_inputs(seeds)
+    masses = MASSES if args.masses is None else tuple(float(v) for v in args.masses.split(","))
+    Uh, chi_sw_h, m_sw, chi_w_h, m_w = host_inputs(seeds, masses, args.w_sources)
     V = int(np.prod(DIMS))
 
     U = {s: torch.from_numpy(Uh[s]).to(dev) for s in seeds}
@@ -173,14 +205,15 @@ def run_ours(args):
     x_w = torch.empty_like(chi_w)
     stream = torch.cuda.current_stream(dev)
 
-    def step(seed, Ud, csw, cw, xsw, xw):
+    def step(seed, Ud, csw, cw, xsw, xw, precision=None):
+        pr = prec if precision is None else precision
         sw.sw_hypercube_build(DIMS, Ud, W, stream=stream)
         xsw.zero_()
         rc1, inf_sw = sw.cgne_solve_batch(DIMS, sw.SW_OP_STAGGERED_WILSON, Ud, W, csw, xsw, m_sw, 1.0, TOL,
-                                          100000, prec, stream=stream)
+                                          100000, pr, stream=stream)
         xw.zero_()
         rc2, inf_w = sw.cgne_solve_batch(DIMS, sw.SW_OP_WILSON, Ud, None, cw, xw, m_w, R_WILSON, TOL, 100000,
-                                         prec, stream=stream)
+                                         pr, stream=stream)
         for inf in inf_sw + inf_w:
             if inf.status != sw.SW_OK or not (inf.true_rel_resid <= TOL):
                 raise RuntimeError(f"solve failed: {inf}")
@@ -211,10 +244,8 @@ def run_ours(args):
     launches = sw.sw_kernel_launches() - launches0
     sw.sw_profile_enable(False)
     prof = sw.sw_profile_read()
+    ms = max_over_ranks(ms, dev)
     if use_dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
 
     n_solves = (len(m_sw) + len(m_w)) * K * world
@@ -246,14 +277,29 @@ def run_ours(args):
         f1.record(stream)
         torch.cuda.synchronize(dev)
         ems = f0.elapsed_time(f1)
-        if use_dist:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(ems, dev)
         h2d = Uh[seeds[0]].nbytes + chi_sw_h.nbytes + chi_w_h.nbytes
         d2h = chi_sw_h.nbytes + chi_w_h.nbytes
         e2e = {"value": n_solves / (ems / 1e3), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": ems / K}
+
+    # ---- plain FP64 CG on one configuration of the same workload (comparison)
+    f64 = None
+    if not args.no_f64 and prec != sw.SW_PREC_F64:
+        torch.cuda.synchronize(dev)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sd = seed_for(Wm, rank, world)
+        g0.record(stream)
+        step(sd, U[sd], chi_sw, chi_w, x_sw, x_w, precision=sw.SW_PREC_F64)
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+        fms = g0.elapsed_time(g1)
+        f64 = {"value": round((len(m_sw) + len(m_w)) / (fms / 1e3), 3), "unit": "solves/s",
+               "ms_per_step": round(fms, 1), "note": "same workload, one configuration, FP64 inner iterations"}
+
+    serving = None
+    if args.serving_requests > 0 and world == 1:
+        serving = run_serving(sw, torch, dev, args)
 
     # ---- per-operator statistics
     it_sw = [i.iters for st in infos for i in st[0]]
@@ -287,9 +333,13 @@ def run_ours(args):
         "warmup": Wm, "ms_per_step": round(ms / K, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == sw.SW_PREC_F32_RELIABLE else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "masses": list(MASSES),
+        "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "masses": list(masses),
                    "solves_per_step": len(m_sw) + len(m_w), "tol": TOL, "r": 1.0,
                    "precision": args.precision, "configurations": "seeds 0-9, mean plaquette 0.59",
+                   "reliable_delta": sw.sw_get_param(sw.SW_PARAM_RELIABLE_DELTA),
+                   "chunk": int(sw.sw_get_param(sw.SW_PARAM_CHUNK)),
+                   "systems_per_thread": {"sw": int(sw.sw_get_param(sw.SW_PARAM_NS_SW)),
+                                          "wilson": int(sw.sw_get_param(sw.SW_PARAM_NS_WILSON))},
                    "l2": "inputs larger than L2: a step touches ~10 GB and each step uses a new configuration",
                    "parallelism": f"replicas x{world}"},
         "clocks": ck, "gpu_launches": int(launches), "roofline": roof, "kernels": kernels,
@@ -309,12 +359,110 @@ def run_ours(args):
     }
     if e2e:
         line["e2e"] = e2e
+    if f64:
+        line["f64_baseline"] = f64
+    if serving:
+        line["serving"] = serving
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(Uh[seeds[0]], by_mass)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if use_dist:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ serving phase
+def run_serving(sw, torch, dev, args, seed=0, slots=8):
+    """Poisson stream of solve requests through the continuous-batching server:
+    lattices drawn uniformly from --serving-lattices, operator uniform
+    (staggered Wilson or Wilson), bare mass uniform in [0.02, 0.2], complex
+    Gaussian sources, FP32 inner / FP64 reliable updates, tol 1e-8.  The rate is
+    80% of the capacity measured by a burst of requests first."""
+    import lattice_synth as ls
+    lats = [tuple(int(v) for v in t.split("x")) for t in args.serving_lattices.split(",")]
+    rng = np.random.default_rng(seed)
+    srv = sw.Server(200 << 30)
+    engines, pools = [], []
+    for li, dims in enumerate(lats):
+        Ud = torch.from_numpy(ls.su3_links(dims, 100 + li, ls.PLAQ_EPS)).to(dev)
+        for op in (sw.SW_OP_STAGGERED_WILSON, sw.SW_OP_WILSON):
+            nc = 3 if op == sw.SW_OP_STAGGERED_WILSON else 12
+            engines.append((dims, op, srv.add_engine(dims, op, Ud, 1.0, sw.SW_PREC_F32_RELIABLE, slots)))
+            V = ls.volume(dims)
+            srcs = []
+            for j in range(2):
+                c = torch.empty((V, nc), dtype=torch.complex128).pin_memory().numpy()
+                c[:] = ls.gaussian_source(dims, nc, 1000 * li + 10 * op + j)
+                srcs.append(c)
+            outs = [torch.empty((V, nc), dtype=torch.complex128).pin_memory().numpy() for _ in range(3 * slots)]
+            pools.append({"src": srcs, "free": list(range(len(outs))), "out": outs})
+        del Ud
+    pending = {}
+
+    def submit(k):
+        pool = pools[k]
+        if not pool["free"]:
+            return False
+        o = pool["free"].pop()
+        rid = srv.submit(engines[k][2], pool["src"][int(rng.integers(0, 2))], pool["out"][o],
+                         float(rng.uniform(0.02, 0.2)), TOL)
+        pending[rid] = (k, o)
+        return True
+
+    def collect(res):
+        for rid, info in srv.poll(4096):
+            k, o = pending.pop(rid)
+            pools[k]["free"].append(o)
+            res.append((k, info))
+
+    # capacity: a burst of requests with every engine busy
+    burst = []
+    t0 = time.perf_counter()
+    nb = 0
+    for _ in range(3):
+        for k in range(len(engines)):
+            nb += submit(k)
+    while pending:
+        collect(burst)
+        time.sleep(0.0005)
+    cap = nb / (time.perf_counter() - t0)
+    rate = 0.8 * cap
+    # Poisson stream at 80% of capacity
+    n = args.serving_requests
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    picks = rng.integers(0, len(engines), size=n)
+    res, waited = [], 0
+    t0 = time.perf_counter()
+    for a, k in zip(arrivals, picks):
+        while time.perf_counter() - t0 < a:
+            collect(res)
+            time.sleep(0.0002)
+        while not submit(int(k)):  # this engine's output buffers are all in flight
+            collect(res)
+            waited += 1
+            time.sleep(0.0002)
+    while pending:
+        collect(res)
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    srv.close()
+    bad = [i for _, i in res if i.status != sw.SW_OK or not i.true_rel_resid <= TOL]
+    if bad:
+        raise RuntimeError(f"serving: {len(bad)} requests failed, e.g. {bad[0]}")
+    lat = np.array([i.seconds * 1e3 for _, i in res])
+    per = {}
+    for k, i in res:
+        d, op, _ = engines[k]
+        key = "x".join(map(str, d)) + ("/sw" if op == sw.SW_OP_STAGGERED_WILSON else "/wilson")
+        per.setdefault(key, []).append(i.seconds * 1e3)
+    return {"requests": n, "solves_per_s": round(n / wall, 2), "capacity_burst_solves_per_s": round(cap, 2),
+            "offered_rate_per_s": round(rate, 2),
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 2),
+                           "p99": round(float(np.percentile(lat, 99)), 2)},
+            "latency_p50_ms_by_engine": {k: round(float(np.median(v)), 2) for k, v in sorted(per.items())},
+            "slots_per_engine": slots, "engines": len(engines),
+            "workload": "Poisson arrivals at 80% of burst capacity; lattices " + args.serving_lattices +
+                        "; operator uniform; mass U[0.02,0.2]; Gaussian sources; tol 1e-8; FP32 inner + FP64"}
 
 
 # ------------------------------------------------------------------ CPU oracle sample
@@ -397,7 +545,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "masses": list(MASSES),
+        "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "masses": list(masses),
                    "tol": TOL, "parallelism": "cpu oracle, rank 0 only"},
         "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
                          "sample": sample},

@@ -41,6 +41,8 @@
 #ifndef SW_CGNE_H
 #define SW_CGNE_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -81,6 +83,10 @@ typedef struct {
   int precision;           /* SW_PREC_* used */
   double true_rel_resid;   /* |b - A x| / |b| in FP64, A = (D+m)^+(D+m), b = (D+m)^+ chi */
   double seconds;          /* wall time of the call */
+  double lambda_min;       /* Ritz estimates of the extreme eigenvalues of A from the */
+  double lambda_max;       /* Lanczos tridiagonal of CG's coefficients (first 4096 iterations);
+                              lambda_max/lambda_min estimates the condition number kappa of
+                              Sec. 3 from below.  0 if no iteration was taken. */
 } sw_solve_info;
 
 /* Hypercube transports W(x,s) for the 8 stored displacements (Sec. 3, the 16
@@ -131,7 +137,7 @@ int cgne_solve_batch(const sw_lattice* lat, int op, const void* U, const void* W
  * call cudaMalloc while they run -- code executing during CUDA graph capture,
  * runtimes whose device memory belongs to another allocator, allocation-free
  * latency loops.  They pass U, W, chi and x as for cgne_solve.
- * Limit: the workspace is 4 FP64 vectors of the lattice plus a few KB
+ * Limit: the workspace is 4 FP64 vectors of the lattice plus about 0.1 MB
  * (192 B per site for staggered Wilson, 768 B per site for Wilson), so at
  * most ~174k sites (16^3x32) for staggered Wilson and ~43k (12^3x24) for
  * Wilson; larger lattices return SW_ERR_ARG before anything is launched.
@@ -147,13 +153,34 @@ int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, const void*
                        const void* chi, void* x, double mass, double r, double tol,
                        int max_iter, sw_solve_info* info, void* stream);
 
+/* Solver tunables (process-wide, read at the start of each solve).
+ * SW_PARAM_CHUNK: CG iterations launched between two reads of the per-system
+ *   status words (1..4096, default 16).  Larger chunks mean fewer host
+ *   synchronisations; converged systems idle for at most one chunk.
+ * SW_PARAM_RELIABLE_DELTA: mixed precision only; the FP32 correction is
+ *   folded into the FP64 solution and r = b - A x recomputed in FP64 when the
+ *   iterated |r| falls below delta times its maximum since the last such
+ *   update (Sleijpen & van der Vorst 1996); (0, 1), default 0.001.
+ * SW_PARAM_NS_SW, SW_PARAM_NS_WILSON: mixed precision only; systems each
+ *   thread of the FP32 stencil kernels computes, sharing every link and
+ *   transport load (1, 2 or 4; defaults 2 for staggered Wilson, 1 for Wilson).
+ *   Fixed per operator, so a system's arithmetic never depends on the batch.
+ * None of these changes what a solve converges to: convergence is always
+ * decided on an FP64 residual.  Returns SW_ERR_ARG for an unknown key or a
+ * value out of range. */
+enum { SW_PARAM_CHUNK = 0, SW_PARAM_RELIABLE_DELTA = 1, SW_PARAM_NS_SW = 2, SW_PARAM_NS_WILSON = 3 };
+int sw_set_param(int key, double value);
+int sw_get_param(int key, double* value);
+
 /* Kernel timing.  Instrumentation with no counterpart in the paper.  While
- * enabled, the first iteration of every chunk of CG iterations has its two
+ * enabled, the second iteration of every chunk of CG iterations has its two
  * stencil launches (k1: t = (D+m) p with |t|^2; k2: (D+m)^+ t with the x, r
  * updates and |r|^2) bracketed by CUDA events on the solve's stream.  After
  * each solve completes, the per-class totals grow by: launches, event time
  * (ms), and the algorithmic bytes of those launches (links and transports
  * once per launch, plus each running system's vectors read and written).
+ * The stencil kernels of a sampled iteration count the systems they compute
+ * on the device, so the byte count matches the work done.
  * Classes are named "<operator>.<kernel>.<precision>", e.g. "sw.k1.f32".
  * Process-wide and thread-safe; disabled by default. */
 int sw_profile_enable(int on);
@@ -166,6 +193,49 @@ int sw_profile_count(void);
  * HOST pointers (each may be NULL).  Returns SW_ERR_ARG for a bad index. */
 int sw_profile_entry(int i, char* name, int name_len, long long* launches, double* total_ms,
                      double* total_bytes);
+
+/* ---- Continuous-batching solve server -------------------------------------
+ * Serving counterpart of the batched solve: gauge fields stay resident on the
+ * device (one engine per field, with its own stream and a fixed number of
+ * system slots), requests are queued per engine, and a scheduler thread
+ * admits them into slots as slots free up while the other slots keep
+ * iterating.  A request's result does not depend on what else is running
+ * (per-slot scalars and fixed-order reductions): it is bit-identical to the
+ * same request served alone.
+ * The paper has no serving layer; each request is one CGNE solve of Eq. 2. */
+typedef struct sw_server_s* sw_server;
+
+/* New server on the current device; engines may hold at most hbm_budget_bytes
+ * of device memory in total. */
+int sw_server_create(size_t hbm_budget_bytes, sw_server* out);
+
+/* Add an engine before the first submit: the links U ([V][4][3][3] complex128,
+ * device; copied, the caller may free U afterwards), operator, r, precision
+ * (SW_PREC_F64 or SW_PREC_F32_RELIABLE) and slot count.  Its memory (links,
+ * hypercube transports, packed FP32 copies, per-slot vectors and workspace) is
+ * charged against the budget; SW_ERR_OOM if it does not fit. */
+int sw_server_add_engine(sw_server srv, const sw_lattice* lat, int op, const void* U, double r,
+                         int precision, int slots, int* engine);
+
+/* Queue one solve on an engine.  chi_host: the source ([V][3] or [V][4][3]
+ * complex128, HOST memory, pinned for asynchronous copies); x_host: HOST
+ * buffer of the same size that receives the solution (initial guess 0).
+ * Both must stay valid until the request is reported by sw_server_poll.
+ * Returns at once with the request id. */
+int sw_server_submit(sw_server srv, int engine, const void* chi_host, void* x_host, double mass,
+                     double tol, int max_iter, long long* request);
+
+/* Up to max finished requests (ids and infos; info.seconds is the latency from
+ * submit to the solution landing in x_host).  *n_done receives the count.
+ * Returns the server's error status (SW_OK while healthy). */
+int sw_server_poll(sw_server srv, int max, long long* requests, sw_solve_info* infos, int* n_done);
+
+/* Wait until every submitted request has finished (SW_ERR_TIMEOUT after
+ * timeout_s seconds). */
+int sw_server_drain(sw_server srv, double timeout_s);
+
+/* Stop the scheduler, wait for the device and free everything. */
+int sw_server_destroy(sw_server srv);
 
 /* Human-readable name of a status code (static string). */
 const char* sw_status_string(int status);

@@ -14,6 +14,10 @@ SW_OP_WILSON = 1
 SW_PREC_F64 = 0
 SW_PREC_F32_RELIABLE = 1
 SW_PREC_F16_RELIABLE = 2
+SW_PARAM_CHUNK = 0
+SW_PARAM_RELIABLE_DELTA = 1
+SW_PARAM_NS_SW = 2
+SW_PARAM_NS_WILSON = 3
 
 
 class Lattice(ctypes.Structure):
@@ -22,7 +26,8 @@ class Lattice(ctypes.Structure):
 
 class _Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("status", ctypes.c_int),
-                ("precision", ctypes.c_int), ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("precision", ctypes.c_int), ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("lambda_min", ctypes.c_double), ("lambda_max", ctypes.c_double)]
 
 
 @dataclass
@@ -33,10 +38,17 @@ class SolveInfo:
     precision: int
     true_rel_resid: float
     seconds: float
+    lambda_min: float = 0.0
+    lambda_max: float = 0.0
+
+    @property
+    def kappa(self):
+        return self.lambda_max / self.lambda_min if self.lambda_min > 0 else float("nan")
 
     @staticmethod
     def from_c(c):
-        return SolveInfo(c.iters, c.reliable_updates, c.status, c.precision, c.true_rel_resid, c.seconds)
+        return SolveInfo(c.iters, c.reliable_updates, c.status, c.precision, c.true_rel_resid, c.seconds,
+                         c.lambda_min, c.lambda_max)
 
 
 class SWError(RuntimeError):
@@ -71,6 +83,21 @@ def lib():
                                        ctypes.POINTER(_Info), vp]
         L.cgne_solve_noalloc.argtypes = [lat, i, vp, vp, vp, vp, d, d, d, i, ctypes.POINTER(_Info), vp]
         L.cgne_solve_noalloc.restype = i
+        srv = ctypes.c_void_p
+        L.sw_server_create.argtypes = [ctypes.c_size_t, ctypes.POINTER(srv)]
+        L.sw_server_add_engine.argtypes = [srv, lat, i, vp, d, i, i, ctypes.POINTER(i)]
+        L.sw_server_submit.argtypes = [srv, i, vp, vp, d, d, i, ctypes.POINTER(ctypes.c_longlong)]
+        L.sw_server_poll.argtypes = [srv, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_Info),
+                                     ctypes.POINTER(i)]
+        L.sw_server_drain.argtypes = [srv, d]
+        L.sw_server_destroy.argtypes = [srv]
+        for f in ("sw_server_create", "sw_server_add_engine", "sw_server_submit", "sw_server_poll",
+                  "sw_server_drain", "sw_server_destroy"):
+            getattr(L, f).restype = i
+        L.sw_set_param.argtypes = [i, d]
+        L.sw_get_param.argtypes = [i, ctypes.POINTER(d)]
+        L.sw_set_param.restype = i
+        L.sw_get_param.restype = i
         L.sw_kernel_launches.argtypes = []
         L.sw_kernel_launches.restype = ctypes.c_longlong
         L.sw_profile_enable.argtypes = [i]
@@ -197,3 +224,75 @@ def cgne_solve_noalloc(dims, op, U, W, chi, x, mass, r=1.0, tol=1e-8, max_iter=1
                                   _stream(stream))
     _check(rc, "cgne_solve_noalloc")
     return SolveInfo.from_c(info)
+
+
+def sw_set_param(key, value):
+    _check(lib().sw_set_param(int(key), float(value)), "sw_set_param")
+
+
+def sw_get_param(key):
+    v = ctypes.c_double()
+    _check(lib().sw_get_param(int(key), ctypes.byref(v)), "sw_get_param")
+    return v.value
+
+
+def _host_ptr(a):
+    """Address of a host buffer: a numpy array or a CPU torch tensor (contiguous)."""
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffer must be contiguous")
+        return a.ctypes.data
+    if a.is_cuda or not a.is_contiguous():
+        raise ValueError("host buffer must be a contiguous CPU tensor")
+    return a.data_ptr()
+
+
+class Server:
+    """Continuous-batching solve server (see sw_server_* in include/sw_cgne.h).
+
+    Host buffers handed to submit() are kept referenced here until their
+    request is returned by poll()."""
+
+    def __init__(self, hbm_budget_bytes):
+        self._h = ctypes.c_void_p()
+        _check(lib().sw_server_create(int(hbm_budget_bytes), ctypes.byref(self._h)), "sw_server_create")
+        self._keep = {}
+
+    def add_engine(self, dims, op, U, r=1.0, precision=SW_PREC_F32_RELIABLE, slots=8, t_antiperiodic=False):
+        eng = ctypes.c_int()
+        _check(lib().sw_server_add_engine(self._h, _lat(dims, t_antiperiodic), int(op), _ptr(U), float(r),
+                                          int(precision), int(slots), ctypes.byref(eng)), "sw_server_add_engine")
+        return eng.value
+
+    def submit(self, engine, chi_host, x_host, mass, tol=1e-8, max_iter=100000):
+        rid = ctypes.c_longlong()
+        _check(lib().sw_server_submit(self._h, int(engine), _host_ptr(chi_host), _host_ptr(x_host), float(mass),
+                                      float(tol), int(max_iter), ctypes.byref(rid)), "sw_server_submit")
+        self._keep[rid.value] = (chi_host, x_host)
+        return rid.value
+
+    def poll(self, max_n=1024):
+        ids = (ctypes.c_longlong * max_n)()
+        infos = (_Info * max_n)()
+        n = ctypes.c_int()
+        _check(lib().sw_server_poll(self._h, max_n, ids, infos, ctypes.byref(n)), "sw_server_poll")
+        out = []
+        for k in range(n.value):
+            self._keep.pop(ids[k], None)
+            out.append((ids[k], SolveInfo.from_c(infos[k])))
+        return out
+
+    def drain(self, timeout_s=600.0):
+        _check(lib().sw_server_drain(self._h, float(timeout_s)), "sw_server_drain")
+
+    def close(self):
+        if self._h:
+            lib().sw_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

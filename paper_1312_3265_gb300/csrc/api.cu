@@ -44,6 +44,11 @@ bool g_prof_on = false;
 std::map<std::string, ProfStat> g_prof;
 std::vector<cudaEvent_t> g_pool;
 thread_local std::vector<Pending> t_pending;
+thread_local std::vector<Pending> t_staged;
+std::atomic<int> g_param_chunk{16};
+std::atomic<double> g_param_delta{0.001};
+std::atomic<int> g_param_ns_sw{2};
+std::atomic<int> g_param_ns_wilson{1};
 thread_local std::vector<cudaEvent_t> t_used;
 }  // namespace
 
@@ -69,8 +74,17 @@ cudaEvent_t prof_event() {
 }
 
 void prof_push(const char* cls, cudaEvent_t a, cudaEvent_t b, double bytes) {
-  t_pending.push_back(Pending{cls, a, b, bytes});
+  t_staged.push_back(Pending{cls, a, b, bytes});
 }
+
+void prof_commit(bool keep) {
+  if (keep) t_pending.insert(t_pending.end(), t_staged.begin(), t_staged.end());
+  t_staged.clear();
+}
+
+int param_chunk() { return g_param_chunk.load(); }
+double param_delta() { return g_param_delta.load(); }
+int param_ns(int nc) { return nc == 3 ? g_param_ns_sw.load() : g_param_ns_wilson.load(); }
 
 void prof_flush() {
   std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -86,6 +100,7 @@ void prof_flush() {
     }
   }
   t_pending.clear();
+  t_staged.clear();
   for (cudaEvent_t e : t_used) g_pool.push_back(e);
   t_used.clear();
 }
@@ -172,6 +187,37 @@ const char* sw_status_string(int s) {
     case SW_ERR_TIMEOUT: return "bounded wait gave up";
     case SW_ERR_ARG: return "bad argument";
     default: return "unknown status";
+  }
+}
+
+int sw_set_param(int key, double value) {
+  switch (key) {
+    case SW_PARAM_CHUNK:
+      if (!(value >= 1 && value <= 4096)) return SW_ERR_ARG;
+      g_param_chunk.store((int)value);
+      return SW_OK;
+    case SW_PARAM_RELIABLE_DELTA:
+      if (!(value > 0 && value < 1)) return SW_ERR_ARG;
+      g_param_delta.store(value);
+      return SW_OK;
+    case SW_PARAM_NS_SW:
+    case SW_PARAM_NS_WILSON:
+      if (!(value == 1 || value == 2 || value == 4)) return SW_ERR_ARG;
+      (key == SW_PARAM_NS_SW ? g_param_ns_sw : g_param_ns_wilson).store((int)value);
+      return SW_OK;
+    default:
+      return SW_ERR_ARG;
+  }
+}
+
+int sw_get_param(int key, double* value) {
+  if (!value) return SW_ERR_NULL;
+  switch (key) {
+    case SW_PARAM_CHUNK: *value = g_param_chunk.load(); return SW_OK;
+    case SW_PARAM_RELIABLE_DELTA: *value = g_param_delta.load(); return SW_OK;
+    case SW_PARAM_NS_SW: *value = g_param_ns_sw.load(); return SW_OK;
+    case SW_PARAM_NS_WILSON: *value = g_param_ns_wilson.load(); return SW_OK;
+    default: return SW_ERR_ARG;
   }
 }
 

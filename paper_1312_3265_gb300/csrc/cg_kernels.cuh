@@ -30,7 +30,10 @@ enum SysStatus : int {
   ST_FAILED = 3,        // NaN / breakdown
   ST_MAXITER = 4,
   ST_JUST_UPDATED = 5,  // residual replaced, p update pending
-  ST_IDLE = 6           // batch slot without a system
+  ST_IDLE = 6,          // slot without a system
+  ST_ADMIT = 7,         // slot being set up: b = (D+m)^+ chi, norms
+  ST_ZERO_B = 8,        // admitted with b = 0: solution x = 0
+  ST_ZERO_GUESS = 9     // admitted with x0 = 0: r = b, no matvec needed
 };
 
 struct SysState {
@@ -44,6 +47,8 @@ struct SysState {
   double rmax2;    // max |r|^2 since the last reliable update
   double delta2;   // reliable-update trigger factor (0: only at convergence)
   double rr_true;  // last FP64 residual norm^2
+  double x02;      // |x0|^2 of the initial guess
+  double mass;     // bare mass of this system
   int iter;
   int max_iter;
   int status;
@@ -56,7 +61,14 @@ struct RedBuf {
   double* partials;   // [nsys][pstride] tile sums
   unsigned* tickets;  // [nsys], zero between launches
   int pstride;        // >= number of tiles
+  double* hist;       // [nsys][kHist][2]: (alpha_k, beta_k) of every iteration, for Ritz values
 };
+
+constexpr int kHist = 4096;  // CG coefficients kept per system (Lanczos tridiagonal size cap)
+
+__device__ __forceinline__ void record(const RedBuf& rb, int sys, int k, int which, double v) {
+  if (rb.hist && k >= 0 && k < kHist) rb.hist[((size_t)sys * kHist + k) * 2 + which] = v;
+}
 
 __device__ __forceinline__ void put_tile(const RedBuf& rb, int sys, int tile, double v) {
   if (threadIdx.x == 0) rb.partials[(size_t)sys * rb.pstride + tile] = v;
@@ -93,6 +105,9 @@ struct SWOp {
   static constexpr int NC = 3;
   static constexpr int kMats = 12;  // 4 links + 8 stored hypercube transports per site
   static constexpr const char* kName = "sw";
+  // default systems per thread in the CG kernels (FP32 shares each matrix load
+  // over several systems; FP64 is ALU-bound and gains nothing from it)
+  static constexpr int kNS = sizeof(T) == 4 ? 4 : 1;
   using Vec = VA<3>;
   G U;
   Wt W;
@@ -103,6 +118,16 @@ struct SWOp {
     for (int i = 0; i < 3; ++i) v.c[i] = o.c[i];
     return v;
   }
+  template <int NS>
+  __device__ __forceinline__ void apply_multi(const Geom& g, int n, const Vec& in, size_t stride, unsigned act,
+                                              const T* m, T r, bool dag, CV<T, 3>* out) const {
+    V3<T> o[NS];
+    sw_site_multi<T, NS>(g, n, U, W, in, stride, act, m, r, dag, o);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) out[s].c[i] = o[s].c[i];
+  }
 };
 
 template <typename T, typename G, template <int> class VA, bool R1>
@@ -110,6 +135,7 @@ struct WOp {
   static constexpr int NC = 12;
   static constexpr int kMats = 4;   // 4 links per site
   static constexpr const char* kName = "wilson";
+  static constexpr int kNS = 1;
   using Vec = VA<12>;
   G U;
   __device__ __forceinline__ CV<T, 12> apply(const Geom& g, int n, const Vec& in, T m, T r, bool dag) const {
@@ -121,6 +147,18 @@ struct WOp {
       for (int i = 0; i < 3; ++i) v.c[3 * s + i] = o.s[s].c[i];
     return v;
   }
+  template <int NS>
+  __device__ __forceinline__ void apply_multi(const Geom& g, int n, const Vec& in, size_t stride, unsigned act,
+                                              const T* m, T r, bool dag, CV<T, 12>* out) const {
+    Sp<T> o[NS];
+    wilson_site_multi<T, R1, NS>(g, n, U, in, stride, act, m, r, dag, o);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) out[s].c[3 * k + i] = o[s].s[k].c[i];
+  }
 };
 
 // Per-system view of a batched vector: system `sys` starts `sys * sstride`
@@ -131,7 +169,6 @@ template <typename Vec> __device__ __forceinline__ Vec sys_view(Vec v, int sys, 
 }
 
 struct BatchParams {
-  const double* mass;  // [nsys]
   double r;
   size_t sstride;      // complex numbers between systems, low-precision vectors
   size_t sstride64;    // same for FP64 canonical vectors
@@ -140,13 +177,14 @@ struct BatchParams {
 // ---------------------------------------------------------------- plain apply (ABI)
 template <typename T, typename Op>
 __global__ void __launch_bounds__(kTile) apply_kernel(Geom g, Op op, typename Op::Vec in, typename Op::Vec out,
-                                                    double mass0, const double* mass, size_t sstride, double r,
-                                                    int dagger, const SysState* S, int only_status) {
+                                                    double mass0, size_t sstride, double r, int dagger,
+                                                    const SysState* S, int only_status) {
+  // mass: mass0, or each system's own mass when the launch is filtered by status
   const int sys = blockIdx.y;
   if (S && S[sys].status != only_status) return;
   in = sys_view(in, sys, sstride);
   out = sys_view(out, sys, sstride);
-  const T m = (T)(mass ? mass[sys] : mass0);
+  const T m = (T)(S ? S[sys].mass : mass0);
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.V; n += gridDim.x * blockDim.x) {
     const CV<T, Op::NC> v = op.apply(g, n, in, m, (T)r, dagger != 0);
 #pragma unroll
@@ -154,91 +192,174 @@ __global__ void __launch_bounds__(kTile) apply_kernel(Geom g, Op op, typename Op
   }
 }
 
+// Block-wide sums of NS doubles per thread (results valid in thread 0).
+template <int NS> __device__ __forceinline__ void block_sum_multi(double* v, double* smem /* NS*32 */) {
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[s] += __shfl_down_sync(0xffffffffu, v[s], o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) smem[s * 32 + w] = v[s];
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      v[s] = (lane < nw) ? smem[s * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[s] += __shfl_down_sync(0xffffffffu, v[s], o);
+    }
+  }
+}
+
+// Systems of group blockIdx.y that are RUNNING, as a bit mask, and their masses.
+template <typename T, int NS>
+__device__ __forceinline__ unsigned running_mask(const SysState* S, int sys0, int nsys, T* m) {
+  unsigned act = 0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int sys = sys0 + s;
+    m[s] = T(0);
+    if (sys < nsys) {
+      m[s] = (T)S[sys].mass;
+      if (S[sys].status == ST_RUNNING) act |= 1u << s;
+    }
+  }
+  return act;
+}
+
 // ---------------------------------------------------------------- k1: t = D p, |t|^2
-template <typename T, typename Op>
+// blockIdx.y = group of NS consecutive systems; tickets are per group.
+// nact (instrumentation, may be null): the systems this launch computes are
+// added to *nact, once per group.
+template <typename T, typename Op, int NS>
 __global__ void __launch_bounds__(kTile) cg_k1(Geom g, Op op, typename Op::Vec p, typename Op::Vec t,
-                                             BatchParams bp, SysState* S, RedBuf rb) {
-  __shared__ double sm[32];
+                                               BatchParams bp, int nsys, SysState* S, RedBuf rb, int* nact) {
+  __shared__ double sm[NS * 32];
   __shared__ int last;
-  const int sys = blockIdx.y;
-  if (S[sys].status != ST_RUNNING) return;
-  p = sys_view(p, sys, bp.sstride);
-  t = sys_view(t, sys, bp.sstride);
-  const T m = (T)bp.mass[sys];
+  const int sys0 = blockIdx.y * NS;
+  T m[NS];
+  const unsigned act = running_mask<T, NS>(S, sys0, nsys, m);
+  if (!act) return;
+  if (nact && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nact, __popc(act));
+  p = sys_view(p, sys0, bp.sstride);
+  t = sys_view(t, sys0, bp.sstride);
   const int ntiles = (g.V + kTile - 1) / kTile;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int n = tile * kTile + threadIdx.x;
-    T acc = T(0);
-    if (n < g.V) {
-      const CV<T, Op::NC> v = op.apply(g, n, p, m, (T)bp.r, false);
+    double acc[NS];
 #pragma unroll
-      for (int c = 0; c < Op::NC; ++c) {
-        t.st(n, c, v.c[c]);
-        acc += norm2(v.c[c]);
+    for (int s = 0; s < NS; ++s) acc[s] = 0.0;
+    if (n < g.V) {
+      CV<T, Op::NC> v[NS];
+      op.template apply_multi<NS>(g, n, p, bp.sstride, act, m, (T)bp.r, false, v);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if (!(act & (1u << s))) continue;
+        const typename Op::Vec ts = sys_at(t, s, bp.sstride);
+        T a = T(0);
+#pragma unroll
+        for (int c = 0; c < Op::NC; ++c) {
+          ts.st(n, c, v[s].c[c]);
+          a += norm2(v[s].c[c]);
+        }
+        acc[s] = (double)a;
       }
     }
-    put_tile(rb, sys, tile, block_sum((double)acc, sm));
+    block_sum_multi<NS>(acc, sm);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (act & (1u << s)) put_tile(rb, sys0 + s, tile, acc[s]);
   }
-  if (block_done(rb, sys, &last)) {
-    const double pAp = finalize_sum(rb, sys, ntiles, sm);
-    if (threadIdx.x == 0) {
-      SysState& s = S[sys];
-      s.pAp = pAp;
-      if (!(pAp > 0.0) || !isfinite(pAp)) {
-        s.status = ST_FAILED;
-      } else {
-        s.alpha = s.rr / pAp;
+  if (block_done(rb, blockIdx.y, &last)) {
+#pragma unroll 1
+    for (int s = 0; s < NS; ++s) {
+      if (!(act & (1u << s))) continue;
+      const double pAp = finalize_sum(rb, sys0 + s, ntiles, sm);
+      if (threadIdx.x == 0) {
+        SysState& st = S[sys0 + s];
+        st.pAp = pAp;
+        if (!(pAp > 0.0) || !isfinite(pAp)) {
+          st.status = ST_FAILED;
+        } else {
+          st.alpha = st.rr / pAp;
+          record(rb, sys0 + s, st.iter, 0, st.alpha);
+        }
       }
     }
   }
 }
 
 // ---------------------------------------------------------------- k2: Ap = D^+ t; x, r update; |r|^2
-template <typename T, typename Op, typename XVec>
+template <typename T, typename Op, int NS>
 __global__ void __launch_bounds__(kTile) cg_k2(Geom g, Op op, typename Op::Vec t, typename Op::Vec p,
-                                             typename Op::Vec r, XVec x, BatchParams bp, size_t xstride,
-                                             SysState* S, RedBuf rb) {
-  __shared__ double sm[32];
+                                               typename Op::Vec r, typename Op::Vec x, BatchParams bp, int nsys,
+                                               SysState* S, RedBuf rb, int* nact) {
+  __shared__ double sm[NS * 32];
   __shared__ int last;
-  const int sys = blockIdx.y;
-  if (S[sys].status != ST_RUNNING) return;
-  t = sys_view(t, sys, bp.sstride);
-  p = sys_view(p, sys, bp.sstride);
-  r = sys_view(r, sys, bp.sstride);
-  x = sys_view(x, sys, xstride);
-  const T m = (T)bp.mass[sys];
-  const T alpha = (T)S[sys].alpha;
+  const int sys0 = blockIdx.y * NS;
+  T m[NS];
+  const unsigned act = running_mask<T, NS>(S, sys0, nsys, m);
+  if (!act) return;
+  if (nact && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nact, __popc(act));
+  T alpha[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) alpha[s] = (act & (1u << s)) ? (T)S[sys0 + s].alpha : T(0);
+  t = sys_view(t, sys0, bp.sstride);
+  p = sys_view(p, sys0, bp.sstride);
+  r = sys_view(r, sys0, bp.sstride);
+  x = sys_view(x, sys0, bp.sstride);
   const int ntiles = (g.V + kTile - 1) / kTile;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int n = tile * kTile + threadIdx.x;
-    T acc = T(0);
-    if (n < g.V) {
-      const CV<T, Op::NC> ap = op.apply(g, n, t, m, (T)bp.r, true);
+    double acc[NS];
 #pragma unroll
-      for (int c = 0; c < Op::NC; ++c) {
-        const cx<T> pc = p.ld(n, c);
-        const cx<T> xc = x.ld(n, c);
-        x.st(n, c, xc + alpha * pc);
-        const cx<T> rc = r.ld(n, c) - alpha * ap.c[c];
-        r.st(n, c, rc);
-        acc += norm2(rc);
+    for (int s = 0; s < NS; ++s) acc[s] = 0.0;
+    if (n < g.V) {
+      CV<T, Op::NC> ap[NS];
+      op.template apply_multi<NS>(g, n, t, bp.sstride, act, m, (T)bp.r, true, ap);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if (!(act & (1u << s))) continue;
+        const typename Op::Vec ps = sys_at(p, s, bp.sstride), rs = sys_at(r, s, bp.sstride),
+                               xs = sys_at(x, s, bp.sstride);
+        T a = T(0);
+#pragma unroll
+        for (int c = 0; c < Op::NC; ++c) {
+          xs.st(n, c, xs.ld(n, c) + alpha[s] * ps.ld(n, c));
+          const cx<T> rc = rs.ld(n, c) - alpha[s] * ap[s].c[c];
+          rs.st(n, c, rc);
+          a += norm2(rc);
+        }
+        acc[s] = (double)a;
       }
     }
-    put_tile(rb, sys, tile, block_sum((double)acc, sm));
+    block_sum_multi<NS>(acc, sm);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (act & (1u << s)) put_tile(rb, sys0 + s, tile, acc[s]);
   }
-  if (block_done(rb, sys, &last)) {
-    const double rr = finalize_sum(rb, sys, ntiles, sm);
-    if (threadIdx.x == 0) {
-      SysState& s = S[sys];
-      s.iter += 1;
-      if (!isfinite(rr)) {
-        s.status = ST_FAILED;
-      } else {
-        s.rr_old = s.rr;
-        s.rr = rr;
-        s.beta = rr / s.rr_old;
-        if (rr > s.rmax2) s.rmax2 = rr;
-        if (rr <= s.tol2 || s.iter >= s.max_iter || rr < s.delta2 * s.rmax2) s.status = ST_NEED_RU;
+  if (block_done(rb, blockIdx.y, &last)) {
+#pragma unroll 1
+    for (int s = 0; s < NS; ++s) {
+      if (!(act & (1u << s))) continue;
+      const double rr = finalize_sum(rb, sys0 + s, ntiles, sm);
+      if (threadIdx.x == 0) {
+        SysState& st = S[sys0 + s];
+        st.iter += 1;
+        if (!isfinite(rr)) {
+          st.status = ST_FAILED;
+        } else {
+          st.rr_old = st.rr;
+          st.rr = rr;
+          st.beta = rr / st.rr_old;
+          record(rb, sys0 + s, st.iter - 1, 1, st.beta);
+          if (rr > st.rmax2) st.rmax2 = rr;
+          if (rr <= st.tol2 || st.iter >= st.max_iter || rr < st.delta2 * st.rmax2) st.status = ST_NEED_RU;
+        }
       }
     }
   }
@@ -270,7 +391,7 @@ __global__ void __launch_bounds__(kTile) residual64(Geom g, Op op, typename Op::
   t = sys_view(t, sys, bp.sstride64);
   b = sys_view(b, sys, bp.sstride64);
   r = sys_view(r, sys, bp.sstride64);
-  const double m = bp.mass[sys];
+  const double m = S[sys].mass;
   const int ntiles = (g.V + kTile - 1) / kTile;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int n = tile * kTile + threadIdx.x;
@@ -300,6 +421,7 @@ __global__ void __launch_bounds__(kTile) residual64(Geom g, Op op, typename Op::
         s.status = ST_MAXITER;
       } else {
         s.beta = (s.iter == 0) ? 0.0 : rr / s.rr_old;
+        record(rb, sys, s.iter - 1, 1, s.beta);
         s.rr = rr;
         s.rmax2 = rr;
         s.status = ST_JUST_UPDATED;

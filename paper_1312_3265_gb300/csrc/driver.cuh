@@ -15,6 +15,7 @@
 // words between chunks; iterations of systems that have stopped return at
 // once on the device.
 #pragma once
+#include <algorithm>
 #include <chrono>
 #include <mutex>
 #include <string>
@@ -26,8 +27,11 @@
 
 namespace swc {
 
-constexpr int kChunk = 16;
-constexpr double kReliableDelta = 0.1;
+// Tunables (sw_set_param): iterations launched between status reads, and
+// the reliable-update trigger delta (update when |r| < delta max|r|).
+int param_chunk();
+double param_delta();
+int param_ns(int nc);  // systems per thread of the FP32 stencils (1, 2 or 4) for NC components
 
 inline int grid_for(const void* kernel, int block, int V, int nsys, int cap) {
   static std::mutex mu;
@@ -100,7 +104,11 @@ struct Workspace {
   double* partials;
   unsigned* tickets;
   double* mass;
+  double* hist;  // CG coefficients, [nsys][kHist][2]
+  int* pcount;   // systems computed per sampled launch, [kProfSlots][2]
 };
+
+constexpr int kProfSlots = 1024;  // sampled iterations per solve
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -111,8 +119,9 @@ inline size_t workspace_bytes(int V, int NC, int nsys, bool mixed) {
   const size_t ntiles = (size_t)(V + kTile - 1) / kTile;
   size_t b = 3 * align_up(sizeof(double2) * n);
   b += mixed ? 4 * align_up(sizeof(float2) * n) : align_up(sizeof(double2) * n);
-  b += align_up(sizeof(SysState) * nsys) + align_up(sizeof(double) * ntiles * nsys) +
-       align_up(sizeof(unsigned) * nsys) + align_up(sizeof(double) * nsys);
+  b += align_up(sizeof(SysState) * nsys) + align_up(sizeof(double) * 2 * ntiles * nsys) +
+       align_up(sizeof(unsigned) * nsys) + align_up(sizeof(double) * nsys) +
+       align_up(sizeof(double) * 2 * kHist * nsys) + align_up(sizeof(int) * 2 * kProfSlots);
   return b;
 }
 
@@ -138,178 +147,398 @@ inline Workspace carve_workspace(void* base, int V, int NC, int nsys, bool mixed
     w.p64 = (double2*)take(sizeof(double2) * n);
   }
   w.S = (SysState*)take(sizeof(SysState) * nsys);
-  w.partials = (double*)take(sizeof(double) * ntiles * nsys);
+  w.partials = (double*)take(sizeof(double) * 2 * ntiles * nsys);  // 2nd half: norm_b's |x0|^2
   w.tickets = (unsigned*)take(sizeof(unsigned) * nsys);
   w.mass = (double*)take(sizeof(double) * nsys);
+  w.hist = (double*)take(sizeof(double) * 2 * kHist * nsys);
+  w.pcount = (int*)take(sizeof(int) * 2 * kProfSlots);
   return w;
 }
 
+// Extreme eigenvalues of the k x k Lanczos tridiagonal built from CG's
+// (alpha_j, beta_j) (Golub & Van Loan, Sec. 10.2): diagonal
+// 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal sqrt(beta_j)/alpha_j.
+// Its eigenvalues (Ritz values) lie inside the spectrum of A and the extremes
+// converge first, so lambda_max/lambda_min estimates the condition number
+// kappa of (D+m)^+(D+m) (Sec. 3) from below.  Sturm-sequence bisection.
+inline void ritz_extremes(const double* h, int k, double* lmin, double* lmax) {
+  *lmin = *lmax = 0.0;
+  if (k < 1) return;
+  std::vector<double> d(k), e2(k, 0.0);
+  for (int j = 0; j < k; ++j) {
+    const double a = h[2 * j];
+    if (!(a > 0.0)) return;
+    d[j] = 1.0 / a + (j > 0 ? h[2 * (j - 1) + 1] / h[2 * (j - 1)] : 0.0);
+    if (j + 1 < k) e2[j] = h[2 * j + 1] / (a * a);
+  }
+  double lo = d[0], hi = d[0];
+  for (int j = 0; j < k; ++j) {
+    const double r = (j > 0 ? sqrt(e2[j - 1]) : 0.0) + (j + 1 < k ? sqrt(e2[j]) : 0.0);
+    lo = fmin(lo, d[j] - r);
+    hi = fmax(hi, d[j] + r);
+  }
+  auto count_below = [&](double x) {  // eigenvalues < x
+    int c = 0;
+    double q = 1.0;
+    for (int j = 0; j < k; ++j) {
+      q = d[j] - x - (j > 0 ? e2[j - 1] / q : 0.0);
+      if (q == 0.0) q = -1e-300;
+      c += (q < 0.0);
+    }
+    return c;
+  };
+  auto kth = [&](int want) {  // smallest x with count_below(x) >= want
+    double a = lo, b = hi;
+    for (int it = 0; it < 200 && b - a > 1e-15 * fmax(fabs(a), fabs(b)); ++it) {
+      const double m = 0.5 * (a + b);
+      if (count_below(m) >= want) b = m; else a = m;
+    }
+    return 0.5 * (a + b);
+  };
+  *lmin = kth(1);
+  *lmax = kth(k);
+}
+
+// A CGNE engine: `cap` system slots on one gauge field, advanced together.
+//
+// Each slot carries its own scalars, mass and status word (SysState) and the
+// kernels compute only the slots in the state they act on, so systems can be
+// admitted, iterate, take reliable updates and finish independently.  One
+// round = (admission of staged slots) + (reliable updates the last status read
+// asked for) + a chunk of CG iterations + an asynchronous copy of the status
+// words.  The host never waits inside a round; complete() reads the copy.
+//
+// Admission runs on the device: p (and the FP32 correction) cleared,
+// b = (D+m)^+ chi, |b|^2 and |x0|^2, then b = 0 -> x = 0 (converged),
+// x0 = 0 -> r = b exactly, otherwise an FP64 residual b - A x0.
+//
 // OpD: FP64 operator on canonical storage.  OpF: the inner-iteration operator
-// (FP32 planar when MIXED, else the same as OpD).  ws: device workspace from
-// carve_workspace; hs: host array [nsys] for the status words.
+// (FP32 planar when MIXED, else the same as OpD).
+template <class OpD, class OpF, bool MIXED>
+class Engine {
+ public:
+  static constexpr int NC = OpD::NC;
+  using V64 = typename OpD::Vec;
+  using VF = typename OpF::Vec;
+  using TF = typename std::conditional<MIXED, float, double>::type;
+
+  // chi, x: cap slots in the canonical layout (x: initial guess in, solution
+  // out).  hs_read / hs_stage: host arrays [cap] (pinned for overlap).
+  // ev: event marking the status copy (nullptr: complete() syncs the stream).
+  Engine(const Geom& g, const OpD& opd, const OpF& opf, double r, int cap, double2* chi, double2* x,
+         const Workspace& ws, SysState* hs_read, SysState* hs_stage, cudaStream_t st, cudaEvent_t ev)
+      : g_(g), opd_(opd), opf_(opf), r_(r), cap_(cap), chi_(chi), x_(x), ws_(ws), hr_(hs_read), hst_(hs_stage),
+        st_(st), ev_(ev), n_((size_t)g.V * NC) {
+    pstride_ = (g.V + kTile - 1) / kTile;
+    rb_ = RedBuf{ws.partials, ws.tickets, pstride_, ws.hist};
+    bp_ = BatchParams{r, n_, n_};
+    ns_ = MIXED ? param_ns(NC) : 1;
+    ngrp_ = (cap + ns_ - 1) / ns_;
+    gA_ = grid_for((const void*)apply_kernel<double, OpD>, kTile, g.V, cap, pstride_);
+    gR_ = grid_for((const void*)residual64<OpD>, kTile, g.V, cap, pstride_);
+    gV_ = grid_for((const void*)cg_k3<TF, VF, NC>, 256, g.V, cap, pstride_);
+    gN_ = grid_for((const void*)norm_b<NC>, kTile, g.V, cap, pstride_);
+    g1_ = grid_for(k1_ptr(), kTile, g.V, ngrp_, pstride_);
+    g2_ = grid_for(k2_ptr(), kTile, g.V, ngrp_, pstride_);
+    if constexpr (MIXED) {
+      fr_ = VF{ws.r32, g.V};
+      fp_ = VF{ws.p32, g.V};
+      ft_ = VF{ws.t32, g.V};
+      fx_ = VF{ws.x32, g.V};
+    } else {
+      fr_ = VF{ws.r64};
+      fp_ = VF{ws.p64};
+      ft_ = VF{ws.t64};
+      fx_ = VF{x};
+    }
+    reported_.assign(cap, 1);
+    for (int i = 0; i < cap; ++i) {
+      SysState z{};
+      z.status = ST_IDLE;
+      hr_[i] = z;
+    }
+    cudaMemsetAsync(ws.tickets, 0, sizeof(unsigned) * cap, st);
+    cudaMemsetAsync(ws.pcount, 0, sizeof(int) * 2 * kProfSlots, st);
+    cudaMemcpyAsync(ws.S, hr_, sizeof(SysState) * cap, cudaMemcpyHostToDevice, st);
+    chunk_ = param_chunk();
+    delta_ = param_delta();
+  }
+
+  // Turn the sampled launches into profiler records (after the stream is idle).
+  void flush_profile() {
+    if (samples_.empty()) return;
+    std::vector<int> cnt(2 * samples_.size());
+    if (cudaMemcpy(cnt.data(), ws_.pcount, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    constexpr double kCx = 2.0 * sizeof(TF);
+    const double gauge = (double)g_.V * OpF::kMats * 9 * kCx, vec = (double)n_ * kCx;
+    static const std::string c1 = std::string(OpF::kName) + (MIXED ? ".k1.f32" : ".k1.f64");
+    static const std::string c2 = std::string(OpF::kName) + (MIXED ? ".k2.f32" : ".k2.f64");
+    for (size_t k = 0; k < samples_.size(); ++k) {
+      prof_push(c1.c_str(), samples_[k].e0, samples_[k].e1, gauge + cnt[2 * k] * 2.0 * vec);
+      prof_push(c2.c_str(), samples_[k].e1, samples_[k].e2, gauge + cnt[2 * k + 1] * 6.0 * vec);
+    }
+    prof_commit(true);
+    samples_.clear();
+    cudaMemset(ws_.pcount, 0, sizeof(int) * 2 * kProfSlots);
+  }
+
+  int cap() const { return cap_; }
+  size_t slot_elems() const { return n_; }
+  double2* chi_slot(int i) const { return chi_ + (size_t)i * n_; }
+  double2* x_slot(int i) const { return x_ + (size_t)i * n_; }
+  const SysState& state(int i) const { return hr_[i]; }
+  const double* hist() const { return ws_.hist; }
+  cudaStream_t stream() const { return st_; }
+
+  // Host: put slot i up for admission in the next round.  Its chi and initial
+  // guess must be in the slot's buffers (in stream order) before issue().
+  void stage(int i, double mass, double tol, int max_iter) {
+    SysState s{};
+    s.tol2 = tol * tol;
+    s.delta2 = MIXED ? delta_ * delta_ : 0.0;
+    s.max_iter = max_iter;
+    s.mass = mass;
+    s.status = ST_ADMIT;
+    hst_[i] = s;
+    hr_[i].status = ST_ADMIT;
+    reported_[i] = 0;
+    staged_.push_back(i);
+  }
+
+  // Launch one round on the stream (see the class comment).
+  void issue() {
+    SysState* S = ws_.S;
+    bool ru = need_ru_;
+    if (!staged_.empty()) {
+      upload_staged();
+      if constexpr (MIXED)
+        admit_clear<NC, float2><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, ws_.p32, ws_.x32, n_, S);
+      else
+        admit_clear<NC, double2><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, ws_.p64, nullptr, n_, S);
+      apply_kernel<double, OpD><<<dim3(gA_, cap_), kTile, 0, st_>>>(g_, opd_, V64{chi_}, V64{ws_.b64}, 0.0, n_,
+                                                                    r_, 1, S, ST_ADMIT);
+      norm_b<NC><<<dim3(gN_, cap_), kTile, 0, st_>>>(g_.V, ws_.b64, x_, n_, S, rb_);
+      admit_vectors<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, ws_.b64, n_, S);
+      admit_states<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S);
+      note_launches(5);
+      ru = true;
+    }
+    if (ru) reliable_update();
+    // After reliable updates with nothing known to be running, read the
+    // statuses first rather than launch a chunk that may find nothing to do.
+    if (!ru || nrun_ > 0) {
+      // time the second iteration of the chunk: by then the queue is full, so
+      // the events time the kernels rather than the host's launch latency
+      const bool prof = prof_enabled() && chunk_ > 1 && samples_.size() < (size_t)kProfSlots;
+      for (int i = 0; i < chunk_; ++i) iterate(prof && i == 1);
+    }
+    cudaMemcpyAsync(hr_, S, sizeof(SysState) * cap_, cudaMemcpyDeviceToHost, st_);
+    if (ev_) cudaEventRecord(ev_, st_);
+  }
+
+  // The round's status copy has landed (non-blocking check).
+  bool ready() const { return ev_ ? cudaEventQuery(ev_) != cudaErrorNotReady : true; }
+
+  // Wait for the round and scan the status words.  Returns the number of
+  // slots still in flight, or a negative SW_ERR_* code.
+  int complete() {
+    const cudaError_t e = ev_ ? cudaEventSynchronize(ev_) : cudaStreamSynchronize(st_);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return SW_ERR_CUDA;
+    int active = 0, nrun = 0;
+    need_ru_ = false;
+    for (int i = 0; i < cap_; ++i) {
+      const int s = hr_[i].status;
+      need_ru_ |= (s == ST_NEED_RU);
+      nrun += (s == ST_RUNNING);
+      active += (s == ST_RUNNING || s == ST_NEED_RU || s == ST_JUST_UPDATED || s == ST_ADMIT ||
+                 s == ST_ZERO_B || s == ST_ZERO_GUESS);
+    }
+    nrun_ = nrun;
+    ++rounds_;
+    return active;
+  }
+
+  // Slots that reached a final state since the last call (each reported once).
+  void finished(std::vector<int>& out) {
+    for (int i = 0; i < cap_; ++i) {
+      const int s = hr_[i].status;
+      if (!reported_[i] && (s == ST_CONVERGED || s == ST_MAXITER || s == ST_FAILED)) {
+        reported_[i] = 1;
+        out.push_back(i);
+      }
+    }
+  }
+
+  long long rounds() const { return rounds_; }
+
+ private:
+  void upload_staged() {
+    std::sort(staged_.begin(), staged_.end());
+    size_t a = 0;
+    while (a < staged_.size()) {  // one copy per run of consecutive slots
+      size_t b = a + 1;
+      while (b < staged_.size() && staged_[b] == staged_[b - 1] + 1) ++b;
+      cudaMemcpyAsync(ws_.S + staged_[a], hst_ + staged_[a], sizeof(SysState) * (b - a), cudaMemcpyHostToDevice,
+                      st_);
+      a = b;
+    }
+    staged_.clear();
+  }
+
+  void reliable_update() {
+    SysState* S = ws_.S;
+    if constexpr (MIXED) accum_x<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, x_, ws_.x32, n_, n_, S);
+    apply_kernel<double, OpD><<<dim3(gA_, cap_), kTile, 0, st_>>>(g_, opd_, V64{x_}, V64{ws_.t64}, 0.0, n_, r_, 0,
+                                                                  S, ST_NEED_RU);
+    residual64<OpD><<<dim3(gR_, cap_), kTile, 0, st_>>>(g_, opd_, V64{ws_.t64}, V64{ws_.b64}, V64{ws_.r64}, bp_, S,
+                                                        rb_);
+    if constexpr (MIXED) demote_r<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, ws_.r64, ws_.r32, n_, n_, S);
+    cg_k3<TF, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, S, ST_JUST_UPDATED);
+    commit_status<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S);
+    note_launches(MIXED ? 6 : 4);
+  }
+
+  const void* k1_ptr() const {
+    switch (ns_) {
+      case 2: return (const void*)cg_k1<TF, OpF, 2>;
+      case 4: return (const void*)cg_k1<TF, OpF, 4>;
+      default: return (const void*)cg_k1<TF, OpF, 1>;
+    }
+  }
+  const void* k2_ptr() const {
+    switch (ns_) {
+      case 2: return (const void*)cg_k2<TF, OpF, 2>;
+      case 4: return (const void*)cg_k2<TF, OpF, 4>;
+      default: return (const void*)cg_k2<TF, OpF, 1>;
+    }
+  }
+  template <int NS> void launch_k12(int* c) {
+    SysState* S = ws_.S;
+    cg_k1<TF, OpF, NS><<<dim3(g1_, ngrp_), kTile, 0, st_>>>(g_, opf_, fp_, ft_, bp_, cap_, S, rb_, c);
+    if (c) cudaEventRecord(samples_.back().e1, st_);
+    cg_k2<TF, OpF, NS><<<dim3(g2_, ngrp_), kTile, 0, st_>>>(g_, opf_, ft_, fp_, fr_, fx_, bp_, cap_, S, rb_,
+                                                             c ? c + 1 : nullptr);
+  }
+
+  // One CG iteration (k1, k2, k3).  A sampled iteration is bracketed by
+  // events, and its stencil kernels count the systems they compute; the
+  // algorithmic bytes of a launch (every stored element touched once) are the
+  // links (and transports) once plus, per computed system, the vectors read
+  // and written: k1 p, t; k2 t, p and x, r read and written.
+  void iterate(bool sample) {
+    SysState* S = ws_.S;
+    int* c = nullptr;
+    if (sample) {
+      samples_.push_back(Sample{prof_event(), prof_event(), prof_event()});
+      c = ws_.pcount + 2 * (samples_.size() - 1);
+      cudaEventRecord(samples_.back().e0, st_);
+    }
+    switch (ns_) {
+      case 2: launch_k12<2>(c); break;
+      case 4: launch_k12<4>(c); break;
+      default: launch_k12<1>(c); break;
+    }
+    if (sample) cudaEventRecord(samples_.back().e2, st_);
+    cg_k3<TF, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, S, ST_RUNNING);
+    note_launches(3);
+  }
+
+  struct Sample {
+    cudaEvent_t e0, e1, e2;
+  };
+  Geom g_;
+  OpD opd_;
+  OpF opf_;
+  double r_;
+  int cap_;
+  double2* chi_;
+  double2* x_;
+  Workspace ws_;
+  SysState* hr_;
+  SysState* hst_;
+  cudaStream_t st_;
+  cudaEvent_t ev_;
+  size_t n_;
+  int pstride_ = 0, ngrp_ = 0, gA_ = 0, gR_ = 0, gV_ = 0, gN_ = 0, g1_ = 0, g2_ = 0;
+  RedBuf rb_{};
+  BatchParams bp_{};
+  VF fr_{}, fp_{}, ft_{}, fx_{};
+  int chunk_ = 16;
+  double delta_ = 0.1;
+  bool need_ru_ = false;
+  int nrun_ = 0, ns_ = 1;
+  std::vector<Sample> samples_;
+  long long rounds_ = 0;
+  std::vector<int> staged_;
+  std::vector<char> reported_;
+};
+
+// Fill sw_solve_info for slot i of an engine from its final status word and
+// its CG coefficients (hh: host copy of the slot's [kHist][2] history).
+inline int fill_info(const SysState& s, const double* hh, int precision, double secs, sw_solve_info* inf) {
+  const int code = status_to_code(s.status);
+  if (inf) {
+    inf->iters = s.iter;
+    inf->reliable_updates = s.n_ru;
+    inf->status = code;
+    inf->precision = precision;
+    inf->true_rel_resid = s.b2 > 0 ? sqrt(s.rr_true / s.b2) : 0.0;
+    inf->seconds = secs;
+    ritz_extremes(hh, s.iter < kHist ? s.iter : kHist, &inf->lambda_min, &inf->lambda_max);
+  }
+  return code;
+}
+
+inline int worst_code(int worst, int code) {
+  if (code < 0 && (worst >= 0 || code < worst)) return code;
+  if (code > 0 && worst == SW_OK) return code;
+  return worst;
+}
+
+// Batched solve on caller-provided workspace: every system admitted at once,
+// rounds until none is in flight.  hs: host array [2 nsys] (status reads and
+// staging).
 template <class OpD, class OpF, bool MIXED>
 int run_cgne_ws(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a, const Workspace& ws,
                 SysState* hs) {
   using namespace std::chrono;
   const auto t0 = steady_clock::now();
-  constexpr int NC = OpD::NC;
-  using V64 = typename OpD::Vec;
-  using VF = typename OpF::Vec;
-  using TF = typename std::conditional<MIXED, float, double>::type;
-  const int nsys = a.nsys;
-  const int V = g.V;
-  const size_t n = (size_t)V * NC;
-  cudaStream_t st = a.stream;
-  const int pstride = (V + kTile - 1) / kTile;  // one partial per reduction tile
-
-  double2* b64 = ws.b64;
-  double2* r64 = ws.r64;
-  double2* t64 = ws.t64;
-  SysState* S = ws.S;
-  RedBuf rb{ws.partials, ws.tickets, pstride};
-  double* mass_d = ws.mass;
-
-  for (int i = 0; i < nsys; ++i) {
-    SysState s{};
-    s.tol2 = a.tol * a.tol;
-    s.delta2 = MIXED ? kReliableDelta * kReliableDelta : 0.0;
-    s.max_iter = a.max_iter;
-    s.status = ST_NEED_RU;
-    hs[i] = s;
-  }
-  cudaMemcpyAsync(S, hs, sizeof(SysState) * nsys, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(mass_d, a.masses, sizeof(double) * nsys, cudaMemcpyHostToDevice, st);
-  cudaMemsetAsync(rb.tickets, 0, sizeof(unsigned) * nsys, st);
-
-  V64 chi{const_cast<double2*>(a.chi)}, vb{b64}, vr{r64}, vt{t64}, vx{a.x};
-  BatchParams bp{mass_d, a.r, n, n};
-
-  const int gA = grid_for((const void*)apply_kernel<double, OpD>, kTile, V, nsys, pstride);
-  const int gR = grid_for((const void*)residual64<OpD>, kTile, V, nsys, pstride);
-  const int gV = grid_for((const void*)cg_k3<TF, VF, NC>, 256, V, nsys, pstride);
-  const int gN = grid_for((const void*)norm_b<NC>, kTile, V, nsys, pstride);
-  const int g1 = grid_for((const void*)cg_k1<TF, OpF>, kTile, V, nsys, pstride);
-  const int g2 = grid_for((const void*)cg_k2<TF, OpF, VF>, kTile, V, nsys, pstride);
-
-  // b = (D+m)^+ chi, |b|^2
-  apply_kernel<double, OpD><<<dim3(gA, nsys), kTile, 0, st>>>(g, opd, chi, vb, 0.0, mass_d, n, a.r, 1, nullptr, 0);
-  norm_b<NC><<<dim3(gN, nsys), kTile, 0, st>>>(V, b64, n, S, rb);
-  note_launches(2);
-
-  VF fr, fp, ft, fx;
-  if constexpr (MIXED) {
-    fr = VF{ws.r32, V};
-    fp = VF{ws.p32, V};
-    ft = VF{ws.t32, V};
-    fx = VF{ws.x32, V};
-    cudaMemsetAsync(ws.p32, 0, sizeof(float2) * n * nsys, st);
-    cudaMemsetAsync(ws.x32, 0, sizeof(float2) * n * nsys, st);
-  } else {
-    fr = vr;
-    fp = VF{ws.p64};
-    ft = vt;
-    fx = vx;
-    cudaMemsetAsync(ws.p64, 0, sizeof(double2) * n * nsys, st);
-  }
-
-  // |b| = 0: the solution is x = 0
-  cudaMemcpyAsync(hs, S, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, st);
-  if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
-  bool any_zero = false;
-  for (int i = 0; i < nsys; ++i)
-    if (hs[i].b2 == 0.0) {
-      any_zero = true;
-      hs[i].status = ST_CONVERGED;
-      hs[i].rr_true = 0.0;
-      cudaMemsetAsync(a.x + (size_t)i * n, 0, sizeof(double2) * n, st);
-    }
-  if (any_zero) cudaMemcpyAsync(S, hs, sizeof(SysState) * nsys, cudaMemcpyHostToDevice, st);
-
-  auto reliable_update = [&]() {
-    if constexpr (MIXED)
-      accum_x<NC><<<dim3(gV, nsys), 256, 0, st>>>(V, a.x, fx.p, n, n, S);
-    apply_kernel<double, OpD><<<dim3(gA, nsys), kTile, 0, st>>>(g, opd, vx, vt, 0.0, mass_d, n, a.r, 0, S, ST_NEED_RU);
-    residual64<OpD><<<dim3(gR, nsys), kTile, 0, st>>>(g, opd, vt, vb, vr, bp, S, rb);
-    if constexpr (MIXED) demote_r<NC><<<dim3(gV, nsys), 256, 0, st>>>(V, r64, fr.p, n, n, S);
-    cg_k3<TF, VF, NC><<<dim3(gV, nsys), 256, 0, st>>>(V, fr, fp, n, S, ST_JUST_UPDATED);
-    commit_status<<<(nsys + 127) / 128, 128, 0, st>>>(nsys, S);
-    note_launches(MIXED ? 6 : 4);
-  };
-  // Algorithmic bytes of one stencil launch (every stored element touched
-  // once): the links (and transports) once per launch, plus per running
-  // system the vectors the kernel reads and writes (k1: p, t; k2: t, p, x and
-  // r read and written).
-  constexpr double kCx = 2.0 * sizeof(TF);
-  const double gauge_bytes = (double)V * OpF::kMats * 9 * kCx;
-  const double vec_bytes = (double)V * NC * kCx;
-  static const std::string cls1 = std::string(OpF::kName) + (MIXED ? ".k1.f32" : ".k1.f64");
-  static const std::string cls2 = std::string(OpF::kName) + (MIXED ? ".k2.f32" : ".k2.f64");
-  auto iterate = [&](int nrun) {
-    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-    if (nrun > 0) {
-      e0 = prof_event();
-      e1 = prof_event();
-      e2 = prof_event();
-      cudaEventRecord(e0, st);
-    }
-    cg_k1<TF, OpF><<<dim3(g1, nsys), kTile, 0, st>>>(g, opf, fp, ft, bp, S, rb);
-    if (nrun > 0) cudaEventRecord(e1, st);
-    cg_k2<TF, OpF, VF><<<dim3(g2, nsys), kTile, 0, st>>>(g, opf, ft, fp, fr, fx, bp, n, S, rb);
-    if (nrun > 0) {
-      cudaEventRecord(e2, st);
-      prof_push(cls1.c_str(), e0, e1, gauge_bytes + nrun * 2.0 * vec_bytes);
-      prof_push(cls2.c_str(), e1, e2, gauge_bytes + nrun * 6.0 * vec_bytes);
-    }
-    cg_k3<TF, VF, NC><<<dim3(gV, nsys), 256, 0, st>>>(V, fr, fp, n, S, ST_RUNNING);
-    note_launches(3);
-  };
-
-  // initial residual r = b - A x0 (all systems start in NEED_RU)
-  reliable_update();
-  const long long max_rounds = 4LL * (a.max_iter / kChunk + 2) + 1000;
+  Engine<OpD, OpF, MIXED> e(g, opd, opf, a.r, a.nsys, const_cast<double2*>(a.chi), a.x, ws, hs, hs + a.nsys,
+                            a.stream, nullptr);
+  for (int i = 0; i < a.nsys; ++i) e.stage(i, a.masses[i], a.tol, a.max_iter);
+  const long long max_rounds = 4LL * (a.max_iter / param_chunk() + 2) + 1000;
   int rc = SW_OK;
-  for (long long round = 0;; ++round) {
-    cudaMemcpyAsync(hs, S, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
-    bool need_ru = false, active = false;
-    int nrun = 0;
-    for (int i = 0; i < nsys; ++i) {
-      const int s = hs[i].status;
-      need_ru |= (s == ST_NEED_RU);
-      active |= (s == ST_RUNNING || s == ST_NEED_RU || s == ST_JUST_UPDATED);
-      nrun += (s == ST_RUNNING);
-    }
-    if (!active) break;
-    if (round > max_rounds) {
+  for (;;) {
+    e.issue();
+    const int active = e.complete();
+    if (active < 0) return active;
+    if (active == 0) break;
+    if (e.rounds() > max_rounds) {
       rc = SW_ERR_TIMEOUT;
       break;
     }
-    if (need_ru) {
-      reliable_update();
-      continue;
-    }
-    const bool prof = prof_enabled();
-    for (int i = 0; i < kChunk; ++i) iterate((prof && i == 0) ? nrun : 0);
-    if (cudaPeekAtLastError() != cudaSuccess) return SW_ERR_CUDA;
   }
-  if (cudaGetLastError() != cudaSuccess) return SW_ERR_CUDA;
+  e.flush_profile();
   prof_flush();
-
+  std::vector<double> hh;
+  if (a.infos) {
+    hh.resize((size_t)2 * kHist * a.nsys);
+    if (cudaMemcpyAsync(hh.data(), ws.hist, sizeof(double) * hh.size(), cudaMemcpyDeviceToHost, a.stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(a.stream) != cudaSuccess)
+      return SW_ERR_CUDA;
+  }
   const double secs = duration<double>(steady_clock::now() - t0).count();
   int worst = SW_OK;
-  for (int i = 0; i < nsys; ++i) {
-    const int code = (rc != SW_OK) ? rc : status_to_code(hs[i].status);
-    if (a.infos) {
-      sw_solve_info& inf = a.infos[i];
-      inf.iters = hs[i].iter;
-      inf.reliable_updates = hs[i].n_ru;
-      inf.status = code;
-      inf.precision = a.precision;
-      inf.true_rel_resid = hs[i].b2 > 0 ? sqrt(hs[i].rr_true / hs[i].b2) : 0.0;
-      inf.seconds = secs;
-    }
-    if (code < 0 && (worst >= 0 || code < worst)) worst = code;
-    if (code > 0 && worst == SW_OK) worst = code;
+  for (int i = 0; i < a.nsys; ++i) {
+    int code = fill_info(e.state(i), a.infos ? hh.data() + (size_t)i * 2 * kHist : nullptr, a.precision, secs,
+                         a.infos ? a.infos + i : nullptr);
+    if (rc != SW_OK) code = rc;
+    if (a.infos && rc != SW_OK) a.infos[i].status = rc;
+    worst = worst_code(worst, code);
   }
   return worst;
 }
@@ -321,7 +550,7 @@ int run_cgne(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a) 
   DevMem mem;
   if (!mem.alloc(workspace_bytes(g.V, OpD::NC, a.nsys, MIXED), a.stream)) return SW_ERR_OOM;
   SysState* hs = nullptr;
-  if (int e = pinned_states(a.nsys, &hs)) return e;
+  if (int e = pinned_states(2 * a.nsys, &hs)) return e;
   const Workspace ws = carve_workspace(mem.p, g.V, OpD::NC, a.nsys, MIXED);
   return run_cgne_ws<OpD, OpF, MIXED>(g, opd, opf, a, ws, hs);
 }

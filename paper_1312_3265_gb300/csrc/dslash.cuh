@@ -196,3 +196,148 @@ __device__ __forceinline__ Sp<T> wilson_site(const Geom& g, int n, const G& U, c
 }
 
 }  // namespace swc
+
+// ------------------------------------------------------------------ multi-system forms
+// The same operators applied to NS systems at once: each link / transport is
+// loaded once and applied to the NS vectors, so the gauge data crosses the
+// memory hierarchy once per site instead of once per system.  System s lives
+// `stride` complex numbers after system s-1; bit s of `act` selects the
+// systems to compute (others are neither loaded nor written).
+namespace swc {
+
+template <typename Vec> __device__ __forceinline__ Vec sys_at(Vec v, int s, size_t stride) {
+  v.p += s * stride;
+  return v;
+}
+
+template <typename T> __device__ __forceinline__ void axpy3(V3<T>& acc, T a, const V3<T>& v) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) acc.c[i] = acc.c[i] + a * v.c[i];
+}
+
+template <typename T, int NS, typename G, typename Wt, typename In>
+__device__ __forceinline__ void sw_site_multi(const Geom& g, int n, const G& U, const Wt& W, const In& in,
+                                              size_t stride, unsigned act, const T* mass, T r, bool dagger,
+                                              V3<T>* out) {
+  int x[4];
+  coords(g, n, x);
+  V3<T> acc[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) acc[s] = zero3<T>();
+  const T half = dagger ? T(-0.5) : T(0.5);
+  int par = 0;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int nf = hop(g, n, x, mu, +1), nb = hop(g, n, x, mu, -1);
+    const T eta = (par & 1) ? -half : half;
+    T cf = eta, cb = -eta;
+    if (mu == 3) {
+      if (bc_flip(g, x, +1)) cf = -cf;
+      if (bc_flip(g, x, -1)) cb = -cb;
+    }
+    const M3<T> Uf = U.link(n, mu);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (act & (1u << s)) axpy3(acc[s], cf, mv(Uf, ld3<In, T>(sys_at(in, s, stride), nf)));
+    const M3<T> Ub = U.link(nb, mu);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (act & (1u << s)) axpy3(acc[s], cb, mdv(Ub, ld3<In, T>(sys_at(in, s, stride), nb)));
+    par += x[mu];
+  }
+  const T hs = (eps_eta5_neg(x) ? r : -r) * T(0.0625);
+  const T hf = bc_flip(g, x, +1) ? -hs : hs, hb = bc_flip(g, x, -1) ? -hs : hs;
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) {
+    const int s0 = (k & 1) ? -1 : 1, s1 = (k & 2) ? -1 : 1, s2 = (k & 4) ? -1 : 1;
+    const int yf = corner(g, n, x, s0, s1, s2, +1);
+    const int yb = corner(g, n, x, -s0, -s1, -s2, -1);
+    const M3<T> Wf = W.mat(n, k);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (act & (1u << s)) axpy3(acc[s], hf, mv(Wf, ld3<In, T>(sys_at(in, s, stride), yf)));
+    const M3<T> Wb = W.mat(yb, k);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (act & (1u << s)) axpy3(acc[s], hb, mdv(Wb, ld3<In, T>(sys_at(in, s, stride), yb)));
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+    if (act & (1u << s)) {
+      const V3<T> self = ld3<In, T>(sys_at(in, s, stride), n);
+      axpy3(acc[s], r + mass[s], self);
+      out[s] = acc[s];
+    }
+}
+
+template <typename T, bool R1, int NS, typename G, typename In>
+__device__ __forceinline__ void wilson_site_multi(const Geom& g, int n, const G& U, const In& in, size_t stride,
+                                                  unsigned act, const T* mass, T r, bool dagger, Sp<T>* out) {
+  int x[4];
+  coords(g, n, x);
+  Sp<T> acc[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[s].s[k] = zero3<T>();
+  const T sg = dagger ? T(-1) : T(1);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int nf = hop(g, n, x, mu, +1), nb = hop(g, n, x, mu, -1);
+    const bool ff = (mu == 3) && bc_flip(g, x, +1), fb = (mu == 3) && bc_flip(g, x, -1);
+    const M3<T> Uf = U.link(n, mu);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      if (!(act & (1u << s))) continue;
+      const Sp<T> p = ld_sp<In, T>(sys_at(in, s, stride), nf);
+      if (R1) {
+        V3<T> h0, h1;
+        wproject(mu, sg, p, h0, h1);
+        V3<T> u0 = mv(Uf, h0), u1 = mv(Uf, h1);
+        if (ff) { neg3(u0); neg3(u1); }
+        wreconstruct(mu, sg, u0, u1, acc[s]);
+      } else {
+        Sp<T> f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          f.s[k] = mv(Uf, p.s[k]);
+          if (ff) neg3(f.s[k]);
+        }
+        wgeneral(mu, sg, r, f, acc[s]);
+      }
+    }
+    const M3<T> Ub = U.link(nb, mu);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      if (!(act & (1u << s))) continue;
+      const Sp<T> p = ld_sp<In, T>(sys_at(in, s, stride), nb);
+      if (R1) {
+        V3<T> h0, h1;
+        wproject(mu, -sg, p, h0, h1);
+        V3<T> u0 = mdv(Ub, h0), u1 = mdv(Ub, h1);
+        if (fb) { neg3(u0); neg3(u1); }
+        wreconstruct(mu, -sg, u0, u1, acc[s]);
+      } else {
+        Sp<T> f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          f.s[k] = mdv(Ub, p.s[k]);
+          if (fb) neg3(f.s[k]);
+        }
+        wgeneral(mu, -sg, r, f, acc[s]);
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    if (!(act & (1u << s))) continue;
+    const Sp<T> self = ld_sp<In, T>(sys_at(in, s, stride), n);
+    const T diag = T(4) * r + mass[s];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) out[s].s[k].c[i] = diag * self.s[k].c[i] - T(0.5) * acc[s].s[k].c[i];
+  }
+}
+
+}  // namespace swc

@@ -48,6 +48,8 @@ bool prof_enabled();
 cudaEvent_t prof_event();
 void prof_push(const char* cls, cudaEvent_t a, cudaEvent_t b, double bytes);
 void prof_flush();
+// Keep (or drop) the samples pushed since the last commit.
+void prof_commit(bool keep);
 // Kernel launches issued by the library (all entry points), for the caller's accounting.
 void note_launches(int k);
 

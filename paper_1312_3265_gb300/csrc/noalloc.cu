@@ -79,7 +79,7 @@ extern "C" int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, 
               static_cast<double2*>(x), 1, &mass, r, tol, max_iter, SW_PREC_F64, info,
               static_cast<cudaStream_t>(stream)};
   const Workspace ws = carve_workspace(scratch, g.V, NC, 1, false);
-  SysState hs[1];  // status words come back into ordinary host memory
+  SysState hs[2];  // status words travel through ordinary host memory
   int rc;
   if (op == SW_OP_STAGGERED_WILSON) {
     const SWd opd{GaugeC64{a.U}, TransC64{a.W}};

@@ -11,7 +11,7 @@ int sw_apply_f64(const Geom& g, const double2* U, const double2* W, const double
   const SW64 op{GaugeC64{U}, TransC64{W}};
   const int gx = (g.V + 127) / 128;
   apply_kernel<double, SW64><<<dim3(gx, 1), 128, 0, st>>>(g, op, VecC64<3>{const_cast<double2*>(in)},
-                                                          VecC64<3>{out}, mass, nullptr, 0, r, dagger,
+                                                          VecC64<3>{out}, mass, 0, r, dagger,
                                                           nullptr, 0);
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;

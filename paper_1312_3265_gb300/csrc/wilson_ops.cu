@@ -13,7 +13,7 @@ static int apply_impl(const Geom& g, const double2* U, const double2* in, double
   const W64<R1> op{GaugeC64{U}};
   const int gx = (g.V + 127) / 128;
   apply_kernel<double, W64<R1>><<<dim3(gx, 1), 128, 0, st>>>(g, op, VecC64<12>{const_cast<double2*>(in)},
-                                                             VecC64<12>{out}, mass, nullptr, 0, r, dagger,
+                                                             VecC64<12>{out}, mass, 0, r, dagger,
                                                              nullptr, 0);
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;

@@ -157,3 +157,95 @@ def test_full_size_solve(sw):
         x, info = P.solve(sw, chi, 1e-8, sw.SW_PREC_F32_RELIABLE)
         assert info.status == sw.SW_OK and info.true_rel_resid <= 1e-8
         assert P.true_resid(chi, x) <= 1.01e-8
+
+
+@pytest.mark.parametrize("op", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_is_bitwise_single(sw, op, prec):
+    """Each system of a batch gives bit-identical results to solving it alone:
+    the per-system arithmetic and the reduction order (fixed 128-site tiles) do
+    not depend on the batch.  5 systems (not a multiple of the register-blocking
+    width), different masses and sources."""
+    import torch
+    P = Problem(sw, (6, 4, 4, 6), op, 7, ls.PLAQ_EPS, 0.1, apbc=True)
+    masses = [0.05, 0.1, 0.2, 0.07, 0.3]
+    chis = np.stack([ls.gaussian_source(P.dims, P.nc, 20 + i).reshape((-1,) + P.internal) for i in range(5)])
+    chi = dev(chis)
+    x = torch.zeros_like(chi)
+    rc, infos = sw.cgne_solve_batch(P.dims, op, P.U, P.W, chi, x, masses, 1.0, 1e-9, 10000, prec, True)
+    assert rc == sw.SW_OK
+    xb = x.cpu().numpy()
+    for i, m in enumerate(masses):
+        xi = torch.zeros_like(chi[i])
+        info = sw.cgne_solve(P.dims, op, P.U, P.W, chi[i].contiguous(), xi, m, 1.0, 1e-9, 10000, prec, True)
+        assert info.iters == infos[i].iters and info.reliable_updates == infos[i].reliable_updates
+        assert np.array_equal(xi.cpu().numpy(), xb[i])
+        assert infos[i].true_rel_resid <= 1e-9
+
+
+def test_reliable_update_delta_param(sw):
+    P = Problem(sw, (6, 6, 4, 6), sw.SW_OP_WILSON, 2, ls.PLAQ_EPS, 0.05)
+    chi = ls.gaussian_source(P.dims, 12, 3).reshape(-1)
+    old = sw.sw_get_param(sw.SW_PARAM_RELIABLE_DELTA)
+    try:
+        counts = {}
+        for d in (0.1, 1e-3):
+            sw.sw_set_param(sw.SW_PARAM_RELIABLE_DELTA, d)
+            x, info = P.solve(sw, chi, 1e-9, sw.SW_PREC_F32_RELIABLE)
+            assert info.status == sw.SW_OK and P.true_resid(chi, x) <= 1.01e-9
+            counts[d] = info.reliable_updates
+        assert counts[1e-3] < counts[0.1]
+        with pytest.raises(sw.SWError):
+            sw.sw_set_param(sw.SW_PARAM_RELIABLE_DELTA, 1.5)
+    finally:
+        sw.sw_set_param(sw.SW_PARAM_RELIABLE_DELTA, old)
+
+
+def test_condition_number_estimates(sw):
+    """Ritz values from CG's coefficients against the paper's condition number
+    kappa = lmax/lmin of (D+m)^+(D+m) (Sec. 3): the free-field closed forms on 4^4
+    (SW: lmax = 4 + (1+m)^2, lmin = m^2; Wilson: (8+m)^2 and m^2), and the dense
+    oracle spectrum on an interacting 4^4 field."""
+    from oracle import dense
+    m = 0.1
+    for op, lmax in ((sw.SW_OP_STAGGERED_WILSON, 4 + (1 + m) ** 2), (sw.SW_OP_WILSON, (8 + m) ** 2)):
+        P = Problem(sw, (4, 4, 4, 4), op, 1, 0.0, m)
+        chi = ls.gaussian_source(P.dims, P.nc, 5).reshape(-1)
+        _, info = P.solve(sw, chi, 1e-12, sw.SW_PREC_F64)
+        assert abs(info.lambda_max - lmax) < 1e-6 * lmax
+        assert abs(info.lambda_min - m * m) < 1e-6 * m * m
+    P = Problem(sw, (4, 4, 4, 4), sw.SW_OP_STAGGERED_WILSON, 0, ls.LINK_EPS_SMALL, 0.05)
+    ev = dense.normal_spectrum(dense.sw_matrix(P.lat, P.U4, 0.05))
+    chi = ls.gaussian_source(P.dims, 3, 6).reshape(-1)
+    for prec in (sw.SW_PREC_F64, sw.SW_PREC_F32_RELIABLE):
+        _, info = P.solve(sw, chi, 1e-12, prec)
+        assert abs(info.lambda_max / ev[-1] - 1) < 1e-3
+        # Ritz values approach lambda_min from above and converge last when the
+        # low end of the spectrum is clustered: 1% after a 1e-12 solve
+        assert ev[0] * (1 - 1e-9) <= info.lambda_min < ev[0] * 1.01
+
+
+@pytest.mark.parametrize("op,widths", [(0, (1, 2, 4)), (1, (1, 2, 4))])
+def test_register_blocking_widths(sw, op, widths):
+    """The FP32 stencils computing 1, 2 or 4 systems per thread solve the same
+    systems to the same FP64 residual (7 systems: ragged groups)."""
+    import torch
+    P = Problem(sw, (6, 4, 4, 6), op, 8, ls.PLAQ_EPS, 0.1)
+    masses = [0.05, 0.1, 0.2, 0.07, 0.3, 0.02, 0.15]
+    chis = np.stack([ls.gaussian_source(P.dims, P.nc, 40 + i).reshape((-1,) + P.internal) for i in range(7)])
+    chi = dev(chis)
+    key = sw.SW_PARAM_NS_SW if op == 0 else sw.SW_PARAM_NS_WILSON
+    old = sw.sw_get_param(key)
+    try:
+        for ns in widths:
+            sw.sw_set_param(key, ns)
+            x = torch.zeros_like(chi)
+            rc, infos = sw.cgne_solve_batch(P.dims, op, P.U, P.W, chi, x, masses, 1.0, 1e-9, 10000,
+                                            sw.SW_PREC_F32_RELIABLE)
+            assert rc == sw.SW_OK
+            xs = x.cpu().numpy()
+            for i, m in enumerate(masses):
+                P.mass = m
+                assert P.true_resid(chis[i].reshape(-1), xs[i].reshape(-1)) <= 1.01e-9
+    finally:
+        sw.sw_set_param(key, old)
