@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["mixed", "f64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "f16", "f64"], default="mixed",
+                    help="inner iterations: FP32 (mixed), FP16 storage (f16) or FP64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--delta", type=float, default=None, help="reliable-update delta (library default if unset)")
@@ -68,6 +69,11 @@ def parse():
     ap.add_argument("--no-f64", action="store_true", help="skip the plain-FP64 comparison step")
     ap.add_argument("--masses", default=None, help="comma-separated bare masses (default: the workload's four)")
     ap.add_argument("--w-sources", type=int, default=12, help="Wilson spin-colour sources per mass (<= 12)")
+    ap.add_argument("--dims", default="16x16x16x32", help="lattice L0xL1xL2xL3 (L3 = time)")
+    ap.add_argument("--graphs", type=int, default=None, help="1/0: replay chunks as CUDA graphs (library default 1)")
+    ap.add_argument("--sources", default="point",
+                    help="'point': 3 colour (SW) / 12 spin-colour (W) point sources per mass; "
+                         "'z2:N': N real Z2-noise sources per mass for both operators")
     return ap.parse_args()
 
 
@@ -149,21 +155,29 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ workload inputs
-def host_inputs(seeds, masses=MASSES, w_sources=12):
+def host_inputs(seeds, masses=MASSES, w_sources=12, dims=DIMS, sources="point"):
+    """Links per configuration seed and the sources of one configuration's solves
+    (mass-major: all sources of the first mass, then the next mass, ...)."""
     import lattice_synth as ls
-    V = ls.volume(DIMS)
-    U = {s: ls.su3_links(DIMS, s, ls.PLAQ_EPS) for s in seeds}
-    chi_sw = np.zeros((len(masses) * 3, V, 3), dtype=np.complex128)
-    m_sw = []
+    V = ls.volume(dims)
+    nproc = min(16, os.cpu_count() or 1)
+    U = {s: ls.su3_links(dims, s, ls.PLAQ_EPS, processes=nproc) for s in seeds}
+    if sources.startswith("z2:"):
+        nz = int(sources.split(":")[1])
+        z_sw = [ls.z2_source(dims, 3, k) for k in range(nz)]
+        z_w = [ls.z2_source(dims, 12, k).reshape(V, 4, 3) for k in range(nz)]
+    else:
+        z_sw = [ls.point_source(dims, 3, a) for a in range(3)]
+        z_w = [ls.point_source(dims, 12, a).reshape(V, 4, 3) for a in range(w_sources)]
+    chi_sw = np.zeros((len(masses) * len(z_sw), V, 3), dtype=np.complex128)
+    chi_w = np.zeros((len(masses) * len(z_w), V, 4, 3), dtype=np.complex128)
+    m_sw, m_w = [], []
     for i, m in enumerate(masses):
-        for a in range(3):
-            chi_sw[3 * i + a] = ls.point_source(DIMS, 3, a)
+        for a, z in enumerate(z_sw):
+            chi_sw[len(z_sw) * i + a] = z
             m_sw.append(m)
-    chi_w = np.zeros((len(masses) * w_sources, V, 4, 3), dtype=np.complex128)
-    m_w = []
-    for i, m in enumerate(masses):
-        for a in range(w_sources):
-            chi_w[w_sources * i + a] = ls.point_source(DIMS, 12, a).reshape(V, 4, 3)
+        for a, z in enumerate(z_w):
+            chi_w[len(z_w) * i + a] = z
             m_w.append(m)
     return U, chi_sw, m_sw, chi_w, m_w
 
@@ -182,11 +196,13 @@ def run_ours(args):
     dev = torch.device("cuda", local if use_dist else 0)
     torch.cuda.set_device(dev)
     sw.lib()
-    prec = sw.SW_PREC_F32_RELIABLE if args.precision == "mixed" else sw.SW_PREC_F64
+    prec = {"mixed": sw.SW_PREC_F32_RELIABLE, "f16": sw.SW_PREC_F16_RELIABLE, "f64": sw.SW_PREC_F64}[args.precision]
     if args.delta is not None:
         sw.sw_set_param(sw.SW_PARAM_RELIABLE_DELTA, args.delta)
     if args.chunk is not None:
         sw.sw_set_param(sw.SW_PARAM_CHUNK, args.chunk)
+    if args.graphs is not None:
+        sw.sw_set_param(sw.SW_PARAM_GRAPHS, args.graphs)
     if args.ns_sw is not None:
         sw.sw_set_param(sw.SW_PARAM_NS_SW, args.ns_sw)
     if args.ns_wilson is not None:
@@ -194,8 +210,9 @@ def run_ours(args):
     K, Wm = args.steps, args.warmup
     seeds = sorted({seed_for(s, rank, world) for s in range(K + Wm)})
     masses = MASSES if args.masses is None else tuple(float(v) for v in args.masses.split(","))
-    Uh, chi_sw_h, m_sw, chi_w_h, m_w = host_inputs(seeds, masses, args.w_sources)
-    V = int(np.prod(DIMS))
+    dims = tuple(int(v) for v in args.dims.split("x"))
+    Uh, chi_sw_h, m_sw, chi_w_h, m_w = host_inputs(seeds, masses, args.w_sources, dims, args.sources)
+    V = int(np.prod(dims))
 
     U = {s: torch.from_numpy(Uh[s]).to(dev) for s in seeds}
     W = torch.empty((V, 8, 3, 3), dtype=torch.complex128, device=dev)
@@ -207,12 +224,12 @@ def run_ours(args):
 
     def step(seed, Ud, csw, cw, xsw, xw, precision=None):
         pr = prec if precision is None else precision
-        sw.sw_hypercube_build(DIMS, Ud, W, stream=stream)
+        sw.sw_hypercube_build(dims, Ud, W, stream=stream)
         xsw.zero_()
-        rc1, inf_sw = sw.cgne_solve_batch(DIMS, sw.SW_OP_STAGGERED_WILSON, Ud, W, csw, xsw, m_sw, 1.0, TOL,
+        rc1, inf_sw = sw.cgne_solve_batch(dims, sw.SW_OP_STAGGERED_WILSON, Ud, W, csw, xsw, m_sw, 1.0, TOL,
                                           100000, pr, stream=stream)
         xw.zero_()
-        rc2, inf_w = sw.cgne_solve_batch(DIMS, sw.SW_OP_WILSON, Ud, None, cw, xw, m_w, R_WILSON, TOL, 100000,
+        rc2, inf_w = sw.cgne_solve_batch(dims, sw.SW_OP_WILSON, Ud, None, cw, xw, m_w, R_WILSON, TOL, 100000,
                                          pr, stream=stream)
         for inf in inf_sw + inf_w:
             if inf.status != sw.SW_OK or not (inf.true_rel_resid <= TOL):
@@ -331,13 +348,17 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": K,
         "warmup": Wm, "ms_per_step": round(ms / K, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if prec == sw.SW_PREC_F32_RELIABLE else "f64",
+        "vs_baseline": None,
+        "dtype": {sw.SW_PREC_F32_RELIABLE: "f32+f64", sw.SW_PREC_F16_RELIABLE: "f16-storage/f32+f64"}.get(prec, "f64"),
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "masses": list(masses),
+        "config": {"workload": WORKLOAD if (dims == DIMS and args.sources == "point") else
+                   f"CGNE batch per configuration: {len(m_sw)} staggered Wilson + {len(m_w)} Wilson solves, "
+                   f"{args.sources} sources", "lattice": "x".join(map(str, dims)), "masses": list(masses),
                    "solves_per_step": len(m_sw) + len(m_w), "tol": TOL, "r": 1.0,
                    "precision": args.precision, "configurations": "seeds 0-9, mean plaquette 0.59",
                    "reliable_delta": sw.sw_get_param(sw.SW_PARAM_RELIABLE_DELTA),
                    "chunk": int(sw.sw_get_param(sw.SW_PARAM_CHUNK)),
+                   "graphs": int(sw.sw_get_param(sw.SW_PARAM_GRAPHS)),
                    "systems_per_thread": {"sw": int(sw.sw_get_param(sw.SW_PARAM_NS_SW)),
                                           "wilson": int(sw.sw_get_param(sw.SW_PARAM_NS_WILSON))},
                    "l2": "inputs larger than L2: a step touches ~10 GB and each step uses a new configuration",
@@ -364,7 +385,7 @@ def run_ours(args):
     if serving:
         line["serving"] = serving
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(Uh[seeds[0]], by_mass)
+        line["cpu_baseline"] = cpu_baseline(Uh[seeds[0]], by_mass, dims)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if use_dist:
@@ -384,7 +405,7 @@ def run_serving(sw, torch, dev, args, seed=0, slots=8):
     srv = sw.Server(200 << 30)
     engines, pools = [], []
     for li, dims in enumerate(lats):
-        Ud = torch.from_numpy(ls.su3_links(dims, 100 + li, ls.PLAQ_EPS)).to(dev)
+        Ud = torch.from_numpy(ls.su3_links(dims, 100 + li, ls.PLAQ_EPS, processes=min(16, os.cpu_count() or 1))).to(dev)
         for op in (sw.SW_OP_STAGGERED_WILSON, sw.SW_OP_WILSON):
             nc = 3 if op == sw.SW_OP_STAGGERED_WILSON else 12
             engines.append((dims, op, srv.add_engine(dims, op, Ud, 1.0, sw.SW_PREC_F32_RELIABLE, slots)))
@@ -466,14 +487,14 @@ def run_serving(sw, torch, dev, args, seed=0, slots=8):
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_iteration_seconds(Uflat, k_sw=2, k_w=3):
+def oracle_iteration_seconds(Uflat, k_sw=2, k_w=3, dims=DIMS):
     """Seconds per CG iteration of the oracle (numpy FP64) on the 16^3x32
     systems at m = 0.1: cg() run for k iterations, minus its final true-residual
     recomputation (two A applications, timed separately)."""
     import lattice_synth as ls
     from oracle import Lattice, operators as ops
     from oracle.cg import cg
-    lat = Lattice(DIMS)
+    lat = Lattice(dims)
     U4 = lat.links(Uflat)
     out = {}
     for name, k, nc in (("sw", k_sw, 3), ("wilson", k_w, 12)):
@@ -482,7 +503,7 @@ def oracle_iteration_seconds(Uflat, k_sw=2, k_w=3):
             A = lambda v: ops.sw_dslash(lat, U4, ops.sw_dslash(lat, U4, v, 0.1), 0.1, dagger=True)
         else:
             A = lambda v: ops.wilson_dslash(lat, U4, ops.wilson_dslash(lat, U4, v, 0.1), 0.1, dagger=True)
-        b = lat.field(ls.point_source(DIMS, nc, 0).reshape((-1,) + internal), internal)
+        b = lat.field(ls.point_source(dims, nc, 0).reshape((-1,) + internal), internal)
         t0 = time.perf_counter()
         A(b)
         tA = time.perf_counter() - t0
@@ -493,30 +514,33 @@ def oracle_iteration_seconds(Uflat, k_sw=2, k_w=3):
     return out
 
 
-def cpu_solves_per_s(per_iter, iters_by_mass):
+def cpu_solves_per_s(per_iter, iters_by_mass, nsrc=None):
     """Solves/s of the oracle on one configuration's 60 solves: per solve, its
     iteration count times the seconds per iteration, plus b = (D+m)^+ chi and the
     final residual (about 1.5 A applications)."""
     total, n = 0.0, 0
-    for op, nsrc in (("sw", 3), ("wilson", 12)):
+    nsrc = nsrc or {"sw": 3, "wilson": 12}
+    for op in ("sw", "wilson"):
         for m, its in iters_by_mass[op].items():
             mean_it = float(np.mean(its)) if isinstance(its, (list, tuple)) else float(its)
-            total += nsrc * (mean_it * per_iter[op]["s_per_iter"] + 1.5 * per_iter[op]["s_per_A"])
-            n += nsrc
+            k = len(its) if isinstance(its, (list, tuple)) else nsrc[op]
+            total += k * (mean_it * per_iter[op]["s_per_iter"] + 1.5 * per_iter[op]["s_per_A"])
+            n += k
     return n / total
 
 
-def cpu_baseline(Uflat, iters_by_mass):
+def cpu_baseline(Uflat, iters_by_mass, dims=DIMS):
     t0 = time.perf_counter()
-    per = oracle_iteration_seconds(Uflat)
+    per = oracle_iteration_seconds(Uflat, dims=dims)
     spent = time.perf_counter() - t0
     return {"value": round(cpu_solves_per_s(per, iters_by_mass), 6), "unit": "solves/s", "cores": 1,
             "kind": "oracle",
-            "sample": (f"oracle (numpy FP64, single thread) CG on 16^3x32 seed-0 links, m=0.1: "
+            "sample": (f"oracle (numpy FP64, single thread) CG on {'x'.join(map(str, dims))} links, m=0.1: "
                        f"{per['sw']['iters_sampled']} staggered Wilson + {per['wilson']['iters_sampled']} "
                        f"Wilson iterations timed ({spent:.1f} s); s/iter SW {per['sw']['s_per_iter']:.2f}, "
                        f"W {per['wilson']['s_per_iter']:.2f}; scaled to the workload's 60 solves with "
-                       f"this run's mean iteration counts per operator and mass")}
+                       f"this run's iteration counts per operator and mass (summed over the solves of one "
+                       f"configuration)")}
 
 
 # ------------------------------------------------------------------ reference arm (the oracle)
@@ -545,7 +569,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "masses": list(masses),
+        "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "masses": list(MASSES),
                    "tol": TOL, "parallelism": "cpu oracle, rank 0 only"},
         "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
                          "sample": sample},

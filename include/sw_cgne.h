@@ -73,7 +73,11 @@ enum { SW_OP_STAGGERED_WILSON = 0, SW_OP_WILSON = 1 };
  * with reliable updates (Sleijpen & van der Vorst 1996) that recompute the
  * residual b - A x in FP64; dot products accumulate in FP64, and convergence
  * is always decided on an FP64 residual.
- * SW_PREC_F16_RELIABLE: as F32, with FP16 storage of links and vectors. */
+ * SW_PREC_F16_RELIABLE: as F32, with FP16 storage of the links (first two
+ * rows, the third rebuilt as conj(row0 x row1): U must be SU(3) to 1e-5, else
+ * SW_ERR_ARG), of the hypercube transports, and of the stencil vectors p and
+ * t (FP16 psi/scale with one FP32 scale per site); r, x and all arithmetic
+ * stay FP32. */
 enum { SW_PREC_F64 = 0, SW_PREC_F32_RELIABLE = 1, SW_PREC_F16_RELIABLE = 2 };
 
 typedef struct {
@@ -165,12 +169,30 @@ int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, const void*
  *   thread of the FP32 stencil kernels computes, sharing every link and
  *   transport load (1, 2 or 4; defaults 2 for staggered Wilson, 1 for Wilson).
  *   Fixed per operator, so a system's arithmetic never depends on the batch.
+ * SW_PARAM_GRAPHS: 1 (default) replays each chunk of CG iterations as a CUDA
+ *   graph captured once per solve or server engine (one launch instead of
+ *   3 per iteration); 0 launches the kernels one by one.  cgne_solve_noalloc
+ *   never uses graphs.
  * None of these changes what a solve converges to: convergence is always
  * decided on an FP64 residual.  Returns SW_ERR_ARG for an unknown key or a
  * value out of range. */
-enum { SW_PARAM_CHUNK = 0, SW_PARAM_RELIABLE_DELTA = 1, SW_PARAM_NS_SW = 2, SW_PARAM_NS_WILSON = 3 };
+enum { SW_PARAM_CHUNK = 0, SW_PARAM_RELIABLE_DELTA = 1, SW_PARAM_NS_SW = 2, SW_PARAM_NS_WILSON = 3,
+       SW_PARAM_GRAPHS = 4 };
 int sw_set_param(int key, double value);
 int sw_get_param(int key, double* value);
+
+/* Autotuner for SW_PARAM_NS_SW / SW_PARAM_NS_WILSON (no counterpart in the
+ * paper).  Times the batched solve of nsys systems (deterministic
+ * pseudo-random sources, masses in [0.05, 0.125]) for `iters` iterations on
+ * the caller's links (and transports for staggered Wilson) with each width
+ * NS in {1, 2, 4}, best of 2, and sets the fastest for this operator.
+ * precision: SW_PREC_F32_RELIABLE or SW_PREC_F16_RELIABLE.  ms (HOST [3],
+ * may be NULL) receives the times in ms, best (HOST, may be NULL) the chosen
+ * width.  Allocates its own sources and solutions; blocks until done.
+ * The width is process-wide: a system solved alone and in a batch is
+ * bit-identical only under the same width, so tune before serving. */
+int sw_autotune(const sw_lattice* lat, int op, const void* U, const void* W, int nsys, int precision,
+                double r, int iters, double* ms, int* best, void* stream);
 
 /* Kernel timing.  Instrumentation with no counterpart in the paper.  While
  * enabled, the second iteration of every chunk of CG iterations has its two
@@ -211,9 +233,10 @@ int sw_server_create(size_t hbm_budget_bytes, sw_server* out);
 
 /* Add an engine before the first submit: the links U ([V][4][3][3] complex128,
  * device; copied, the caller may free U afterwards), operator, r, precision
- * (SW_PREC_F64 or SW_PREC_F32_RELIABLE) and slot count.  Its memory (links,
+ * (SW_PREC_*) and slot count.  Its memory (links,
  * hypercube transports, packed FP32 copies, per-slot vectors and workspace) is
- * charged against the budget; SW_ERR_OOM if it does not fit. */
+ * charged against the budget; SW_ERR_OOM if it does not fit.  precision may
+ * also be SW_PREC_F16_RELIABLE. */
 int sw_server_add_engine(sw_server srv, const sw_lattice* lat, int op, const void* U, double r,
                          int precision, int slots, int* engine);
 

@@ -142,13 +142,17 @@ def reunitarize(M):
     return np.stack([r0, r1, r2], axis=-2)
 
 
-def su3_links(dims, seed, eps, sites=None):
+def su3_links(dims, seed, eps, sites=None, processes=1):
     """Gauge links U[n][mu] = reunitarize(exp(i eps sum_a theta_a lambda_a)).
 
     theta_a(n, mu) ~ N(0,1) from Philox counter index 2*(4 n + mu) + j, j = 0,1,
     stream STREAM_LINKS, key = seed.  `sites` selects a subset of site indices
     (same values as the full field at those sites).  Returns (nsites, 4, 3, 3).
+    processes > 1 splits the sites over that many worker processes (spawned,
+    writing into shared memory); the values are the same.
     """
+    if sites is None and processes > 1 and volume(dims) >= 65536:
+        return _su3_links_parallel(dims, seed, eps, processes)
     if sites is None:
         sites = np.arange(volume(dims), dtype=np.int64)
     sites = np.asarray(sites, dtype=np.int64)
@@ -160,6 +164,37 @@ def su3_links(dims, seed, eps, sites=None):
     ph = np.exp(1j * eps * w)
     U = np.einsum("smik,smk,smjk->smij", V, ph, np.conj(V))
     return reunitarize(U)
+
+
+def _links_into(name, shape, dims, seed, eps, lo, hi):
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        out = np.ndarray(shape, dtype=np.complex128, buffer=shm.buf)
+        step = 1 << 16
+        for a in range(lo, hi, step):
+            b = min(hi, a + step)
+            out[a:b] = su3_links(dims, seed, eps, sites=np.arange(a, b, dtype=np.int64))
+    finally:
+        shm.close()
+
+
+def _su3_links_parallel(dims, seed, eps, processes):
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    V = volume(dims)
+    shape = (V, 4, 3, 3)
+    shm = shared_memory.SharedMemory(create=True, size=V * 4 * 9 * 16)
+    try:
+        bounds = np.linspace(0, V, processes * 4 + 1).astype(np.int64)
+        ctx = mp.get_context("spawn")  # safe after CUDA has been initialised in the parent
+        with ctx.Pool(processes) as pool:
+            pool.starmap(_links_into, [(shm.name, shape, tuple(dims), seed, eps, int(bounds[i]), int(bounds[i + 1]))
+                                       for i in range(len(bounds) - 1)])
+        return np.array(np.ndarray(shape, dtype=np.complex128, buffer=shm.buf))
+    finally:
+        shm.close()
+        shm.unlink()
 
 
 def _shift_index(dims, mu, step=1):

@@ -18,6 +18,7 @@ SW_PARAM_CHUNK = 0
 SW_PARAM_RELIABLE_DELTA = 1
 SW_PARAM_NS_SW = 2
 SW_PARAM_NS_WILSON = 3
+SW_PARAM_GRAPHS = 4
 
 
 class Lattice(ctypes.Structure):
@@ -94,6 +95,8 @@ def lib():
         for f in ("sw_server_create", "sw_server_add_engine", "sw_server_submit", "sw_server_poll",
                   "sw_server_drain", "sw_server_destroy"):
             getattr(L, f).restype = i
+        L.sw_autotune.argtypes = [lat, i, vp, vp, i, i, d, i, ctypes.POINTER(d), ctypes.POINTER(i), vp]
+        L.sw_autotune.restype = i
         L.sw_set_param.argtypes = [i, d]
         L.sw_get_param.argtypes = [i, ctypes.POINTER(d)]
         L.sw_set_param.restype = i
@@ -296,3 +299,13 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def sw_autotune(dims, op, U, W, nsys, precision=SW_PREC_F32_RELIABLE, r=1.0, iters=48, t_antiperiodic=False,
+                stream=None):
+    """Time register-blocking widths 1, 2, 4 and keep the fastest; returns (best, {width: ms})."""
+    ms = (ctypes.c_double * 3)()
+    best = ctypes.c_int()
+    _check(lib().sw_autotune(_lat(dims, t_antiperiodic), int(op), _ptr(U), _ptr(W), int(nsys), int(precision),
+                             float(r), int(iters), ms, ctypes.byref(best), _stream(stream)), "sw_autotune")
+    return best.value, {1: ms[0], 2: ms[1], 4: ms[2]}

@@ -49,6 +49,7 @@ std::atomic<int> g_param_chunk{16};
 std::atomic<double> g_param_delta{0.001};
 std::atomic<int> g_param_ns_sw{2};
 std::atomic<int> g_param_ns_wilson{1};
+std::atomic<int> g_param_graphs{1};
 thread_local std::vector<cudaEvent_t> t_used;
 }  // namespace
 
@@ -85,6 +86,7 @@ void prof_commit(bool keep) {
 int param_chunk() { return g_param_chunk.load(); }
 double param_delta() { return g_param_delta.load(); }
 int param_ns(int nc) { return nc == 3 ? g_param_ns_sw.load() : g_param_ns_wilson.load(); }
+bool param_graphs() { return g_param_graphs.load() != 0; }
 
 void prof_flush() {
   std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -200,6 +202,10 @@ int sw_set_param(int key, double value) {
       if (!(value > 0 && value < 1)) return SW_ERR_ARG;
       g_param_delta.store(value);
       return SW_OK;
+    case SW_PARAM_GRAPHS:
+      if (!(value == 0 || value == 1)) return SW_ERR_ARG;
+      g_param_graphs.store((int)value);
+      return SW_OK;
     case SW_PARAM_NS_SW:
     case SW_PARAM_NS_WILSON:
       if (!(value == 1 || value == 2 || value == 4)) return SW_ERR_ARG;
@@ -217,6 +223,7 @@ int sw_get_param(int key, double* value) {
     case SW_PARAM_RELIABLE_DELTA: *value = g_param_delta.load(); return SW_OK;
     case SW_PARAM_NS_SW: *value = g_param_ns_sw.load(); return SW_OK;
     case SW_PARAM_NS_WILSON: *value = g_param_ns_wilson.load(); return SW_OK;
+    case SW_PARAM_GRAPHS: *value = g_param_graphs.load(); return SW_OK;
     default: return SW_ERR_ARG;
   }
 }
@@ -302,7 +309,8 @@ int cgne_solve(const sw_lattice* lat, int op, const void* U, const void* W, cons
   Geom g;
   SW_TRY(make_geom(lat, &g));
   if (op != SW_OP_STAGGERED_WILSON && op != SW_OP_WILSON) return SW_ERR_ARG;
-  if (precision != SW_PREC_F64 && precision != SW_PREC_F32_RELIABLE) return SW_ERR_ARG;
+  if (precision != SW_PREC_F64 && precision != SW_PREC_F32_RELIABLE && precision != SW_PREC_F16_RELIABLE)
+    return SW_ERR_ARG;
   if (!(tol > 0.0) || !(tol < 1.0) || max_iter < 1) return SW_ERR_ARG;
   if (!(mass == mass) || !(r == r)) return SW_ERR_ARG;
   const size_t V = g.V;
@@ -334,7 +342,8 @@ int cgne_solve_batch(const sw_lattice* lat, int op, const void* U, const void* W
   Geom g;
   SW_TRY(make_geom(lat, &g));
   if (op != SW_OP_STAGGERED_WILSON && op != SW_OP_WILSON) return SW_ERR_ARG;
-  if (precision != SW_PREC_F64 && precision != SW_PREC_F32_RELIABLE) return SW_ERR_ARG;
+  if (precision != SW_PREC_F64 && precision != SW_PREC_F32_RELIABLE && precision != SW_PREC_F16_RELIABLE)
+    return SW_ERR_ARG;
   if (!(tol > 0.0) || !(tol < 1.0) || max_iter < 1) return SW_ERR_ARG;
   for (int i = 0; i < nsys; ++i)
     if (!(masses[i] == masses[i])) return SW_ERR_ARG;

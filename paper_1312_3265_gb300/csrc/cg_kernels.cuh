@@ -105,6 +105,8 @@ struct SWOp {
   static constexpr int NC = 3;
   static constexpr int kMats = 12;  // 4 links + 8 stored hypercube transports per site
   static constexpr const char* kName = "sw";
+  static constexpr int kGaugeBytes = G::kBytes + Wt::kBytes;  // stored links + transports per site
+  static constexpr const char* kPrec = G::kPrec;
   // default systems per thread in the CG kernels (FP32 shares each matrix load
   // over several systems; FP64 is ALU-bound and gains nothing from it)
   static constexpr int kNS = sizeof(T) == 4 ? 4 : 1;
@@ -135,6 +137,8 @@ struct WOp {
   static constexpr int NC = 12;
   static constexpr int kMats = 4;   // 4 links per site
   static constexpr const char* kName = "wilson";
+  static constexpr int kGaugeBytes = G::kBytes;
+  static constexpr const char* kPrec = G::kPrec;
   static constexpr int kNS = 1;
   using Vec = VA<12>;
   G U;
@@ -161,6 +165,34 @@ struct WOp {
   }
 };
 
+// Store a whole site: plain accessors component by component; FP16 vectors
+// with the site's scale (largest |re|, |im|) so the halves hold psi/scale.
+template <typename Vec, typename T, int NC>
+__device__ __forceinline__ void st_site(const Vec& v, int n, const CV<T, NC>& a) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) v.st(n, c, a.c[c]);
+}
+template <int NC>
+__device__ __forceinline__ void st_site(const VecP16<NC>& v, int n, const CV<float, NC>& a) {
+  float m = 0.f;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) m = fmaxf(m, fmaxf(fabsf(a.c[c].re), fabsf(a.c[c].im)));
+  // Sites below 1e-30 (far tails of point-source solutions reach FP32
+  // denormals, whose reciprocal overflows) are stored as exact zeros.
+  if (!(m > 1e-30f)) m = (m == m) ? 0.f : m;
+  const float inv = m > 0.f ? 1.f / m : 0.f;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) v.p[(size_t)c * v.V + n] = __floats2half2_rn(a.c[c].re * inv, a.c[c].im * inv);
+  reinterpret_cast<float*>(v.p + (size_t)NC * v.V)[n] = m;
+}
+
+template <int NC>
+__device__ __forceinline__ void st_site(const VecP32q<NC>& v, int n, const CV<float, NC>& a) {
+#pragma unroll
+  for (int q = 0; q < NC / 2; ++q)
+    v.p[(size_t)q * v.V + n] = make_float4(a.c[2 * q].re, a.c[2 * q].im, a.c[2 * q + 1].re, a.c[2 * q + 1].im);
+}
+
 // Per-system view of a batched vector: system `sys` starts `sys * sstride`
 // complex numbers after the base pointer (layout inside a system unchanged).
 template <typename Vec> __device__ __forceinline__ Vec sys_view(Vec v, int sys, size_t sstride) {
@@ -170,8 +202,9 @@ template <typename Vec> __device__ __forceinline__ Vec sys_view(Vec v, int sys, 
 
 struct BatchParams {
   double r;
-  size_t sstride;      // complex numbers between systems, low-precision vectors
+  size_t sstride;      // units between systems: inner-precision r and x
   size_t sstride64;    // same for FP64 canonical vectors
+  size_t vstride;      // same for the stencil vectors p and t
 };
 
 // ---------------------------------------------------------------- plain apply (ABI)
@@ -235,8 +268,17 @@ __device__ __forceinline__ unsigned running_mask(const SysState* S, int sys0, in
 // blockIdx.y = group of NS consecutive systems; tickets are per group.
 // nact (instrumentation, may be null): the systems this launch computes are
 // added to *nact, once per group.
+// Minimum resident blocks per SM requested from the compiler for the
+// inner-precision stencil kernels (caps their registers): they are
+// latency-bound, so more resident warps hide more of the L2 latency
+// (staggered Wilson 8 blocks = 64 registers, Wilson 6 = 80, chosen from the
+// spill counts of ptxas and GB300 timings).  FP64 kernels are ALU-bound: no cap.
+template <typename T, typename Op> constexpr int stencil_min_blocks() {
+  return sizeof(T) == 4 ? (Op::NC == 3 ? 8 : 6) : 1;
+}
+
 template <typename T, typename Op, int NS>
-__global__ void __launch_bounds__(kTile) cg_k1(Geom g, Op op, typename Op::Vec p, typename Op::Vec t,
+__global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k1(Geom g, Op op, typename Op::Vec p, typename Op::Vec t,
                                                BatchParams bp, int nsys, SysState* S, RedBuf rb, int* nact) {
   __shared__ double sm[NS * 32];
   __shared__ int last;
@@ -245,9 +287,12 @@ __global__ void __launch_bounds__(kTile) cg_k1(Geom g, Op op, typename Op::Vec p
   const unsigned act = running_mask<T, NS>(S, sys0, nsys, m);
   if (!act) return;
   if (nact && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nact, __popc(act));
-  p = sys_view(p, sys0, bp.sstride);
-  t = sys_view(t, sys0, bp.sstride);
+  p = sys_view(p, sys0, bp.vstride);
+  t = sys_view(t, sys0, bp.vstride);
   const int ntiles = (g.V + kTile - 1) / kTile;
+  // grid-stride over tiles: the blocks resident at a time cover neighbouring
+  // tiles, which keeps their neighbour reads together in L2 (measured faster
+  // on GB300 than giving each block one contiguous range of tiles)
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int n = tile * kTile + threadIdx.x;
     double acc[NS];
@@ -255,17 +300,14 @@ __global__ void __launch_bounds__(kTile) cg_k1(Geom g, Op op, typename Op::Vec p
     for (int s = 0; s < NS; ++s) acc[s] = 0.0;
     if (n < g.V) {
       CV<T, Op::NC> v[NS];
-      op.template apply_multi<NS>(g, n, p, bp.sstride, act, m, (T)bp.r, false, v);
+      op.template apply_multi<NS>(g, n, p, bp.vstride, act, m, (T)bp.r, false, v);
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         if (!(act & (1u << s))) continue;
-        const typename Op::Vec ts = sys_at(t, s, bp.sstride);
+        st_site(sys_at(t, s, bp.vstride), n, v[s]);
         T a = T(0);
 #pragma unroll
-        for (int c = 0; c < Op::NC; ++c) {
-          ts.st(n, c, v[s].c[c]);
-          a += norm2(v[s].c[c]);
-        }
+        for (int c = 0; c < Op::NC; ++c) a += norm2(v[s].c[c]);
         acc[s] = (double)a;
       }
     }
@@ -294,10 +336,10 @@ __global__ void __launch_bounds__(kTile) cg_k1(Geom g, Op op, typename Op::Vec p
 }
 
 // ---------------------------------------------------------------- k2: Ap = D^+ t; x, r update; |r|^2
-template <typename T, typename Op, int NS>
-__global__ void __launch_bounds__(kTile) cg_k2(Geom g, Op op, typename Op::Vec t, typename Op::Vec p,
-                                               typename Op::Vec r, typename Op::Vec x, BatchParams bp, int nsys,
-                                               SysState* S, RedBuf rb, int* nact) {
+template <typename T, typename Op, int NS, typename RVec>
+__global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(Geom g, Op op, typename Op::Vec t, typename Op::Vec p, RVec r,
+                                               RVec x, BatchParams bp, int nsys, SysState* S, RedBuf rb,
+                                               int* nact) {
   __shared__ double sm[NS * 32];
   __shared__ int last;
   const int sys0 = blockIdx.y * NS;
@@ -308,11 +350,14 @@ __global__ void __launch_bounds__(kTile) cg_k2(Geom g, Op op, typename Op::Vec t
   T alpha[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) alpha[s] = (act & (1u << s)) ? (T)S[sys0 + s].alpha : T(0);
-  t = sys_view(t, sys0, bp.sstride);
-  p = sys_view(p, sys0, bp.sstride);
+  t = sys_view(t, sys0, bp.vstride);
+  p = sys_view(p, sys0, bp.vstride);
   r = sys_view(r, sys0, bp.sstride);
   x = sys_view(x, sys0, bp.sstride);
   const int ntiles = (g.V + kTile - 1) / kTile;
+  // grid-stride over tiles: the blocks resident at a time cover neighbouring
+  // tiles, which keeps their neighbour reads together in L2 (measured faster
+  // on GB300 than giving each block one contiguous range of tiles)
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int n = tile * kTile + threadIdx.x;
     double acc[NS];
@@ -320,12 +365,12 @@ __global__ void __launch_bounds__(kTile) cg_k2(Geom g, Op op, typename Op::Vec t
     for (int s = 0; s < NS; ++s) acc[s] = 0.0;
     if (n < g.V) {
       CV<T, Op::NC> ap[NS];
-      op.template apply_multi<NS>(g, n, t, bp.sstride, act, m, (T)bp.r, true, ap);
+      op.template apply_multi<NS>(g, n, t, bp.vstride, act, m, (T)bp.r, true, ap);
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         if (!(act & (1u << s))) continue;
-        const typename Op::Vec ps = sys_at(p, s, bp.sstride), rs = sys_at(r, s, bp.sstride),
-                               xs = sys_at(x, s, bp.sstride);
+        const typename Op::Vec ps = sys_at(p, s, bp.vstride);
+        const RVec rs = sys_at(r, s, bp.sstride), xs = sys_at(x, s, bp.sstride);
         T a = T(0);
 #pragma unroll
         for (int c = 0; c < Op::NC; ++c) {
@@ -366,16 +411,19 @@ __global__ void __launch_bounds__(kTile) cg_k2(Geom g, Op op, typename Op::Vec t
 }
 
 // ---------------------------------------------------------------- k3: p = r + beta p
-template <typename T, typename Vec, int NC>
-__global__ void __launch_bounds__(256) cg_k3(int V, Vec r, Vec p, size_t sstride, const SysState* S, int only_status) {
+template <typename T, typename RVec, typename PVec, int NC>
+__global__ void __launch_bounds__(256) cg_k3(int V, RVec r, PVec p, size_t rstride, size_t pstride,
+                                             const SysState* S, int only_status) {
   const int sys = blockIdx.y;
   if (S[sys].status != only_status) return;
-  r = sys_view(r, sys, sstride);
-  p = sys_view(p, sys, sstride);
+  r = sys_view(r, sys, rstride);
+  p = sys_view(p, sys, pstride);
   const T beta = (T)S[sys].beta;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < V; n += gridDim.x * blockDim.x) {
+    CV<T, NC> v;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) p.st(n, c, r.ld(n, c) + beta * p.ld(n, c));
+    for (int c = 0; c < NC; ++c) v.c[c] = r.ld(n, c) + beta * p.ld(n, c);
+    st_site(p, n, v);
   }
 }
 

@@ -131,6 +131,8 @@ __device__ __forceinline__ bool bc_flip(const Geom& g, const int x[4], int s) {
 // ------------------------------------------------------------------ accessors
 // Canonical FP64 (the C ABI layout)
 struct GaugeC64 {
+  static constexpr int kBytes = 4 * 9 * 16;  // per site
+  static constexpr const char* kPrec = "f64";
   const double2* p;
   __device__ __forceinline__ M3<double> link(int n, int mu) const {
     const double2* q = p + ((size_t)n * 4 + mu) * 9;
@@ -143,6 +145,7 @@ struct GaugeC64 {
   }
 };
 struct TransC64 {
+  static constexpr int kBytes = 8 * 9 * 16;
   const double2* p;
   __device__ __forceinline__ M3<double> mat(int n, int k) const {
     const double2* q = p + ((size_t)n * 8 + k) * 9;
@@ -157,6 +160,8 @@ struct TransC64 {
 
 // Planar FP32: plane c of an object of `ncx` complex numbers per site at p[c*V + n]
 struct GaugeP32 {
+  static constexpr int kBytes = 4 * 9 * 8;
+  static constexpr const char* kPrec = "f32";
   const float2* p;
   int V;
   __device__ __forceinline__ M3<float> link(int n, int mu) const {
@@ -170,6 +175,7 @@ struct GaugeP32 {
   }
 };
 struct TransP32 {
+  static constexpr int kBytes = 8 * 9 * 8;
   const float2* p;
   int V;
   __device__ __forceinline__ M3<float> mat(int n, int k) const {
@@ -185,15 +191,99 @@ struct TransP32 {
 
 // Vector fields: NC complex components per site.
 template <int NC> struct VecC64 {  // canonical [V][NC] complex128
+  using unit = double2;
+  static size_t sys_units(int V) { return (size_t)V * NC; }
   double2* p;
   __device__ __forceinline__ cx<double> ld(int n, int c) const { double2 v = __ldg(p + (size_t)n * NC + c); return {v.x, v.y}; }
   __device__ __forceinline__ void st(int n, int c, cx<double> a) const { p[(size_t)n * NC + c] = make_double2(a.re, a.im); }
 };
 template <int NC> struct VecP32 {  // planar [NC][V] float2
+  using unit = float2;
+  static size_t sys_units(int V) { return (size_t)V * NC; }
   float2* p;
   int V;
   __device__ __forceinline__ cx<float> ld(int n, int c) const { float2 v = __ldg(p + (size_t)c * V + n); return {v.x, v.y}; }
   __device__ __forceinline__ void st(int n, int c, cx<float> a) const { p[(size_t)c * V + n] = make_float2(a.re, a.im); }
+};
+
+// Planar FP32 with two complex components per 16-byte plane element:
+// [NC/2][V] float4 holding components (2k, 2k+1).  Whole-site loads and stores
+// use half as many, twice as wide, memory instructions (NC even).
+template <int NC> struct VecP32q {
+  static_assert(NC % 2 == 0, "pairs of components");
+  using unit = float4;
+  static size_t sys_units(int V) { return (size_t)V * NC / 2; }
+  float4* p;
+  int V;
+  __device__ __forceinline__ cx<float> ld(int n, int c) const {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p + (size_t)(c >> 1) * V + n) + (c & 1));
+    return {v.x, v.y};
+  }
+  __device__ __forceinline__ void st(int n, int c, cx<float> a) const {
+    reinterpret_cast<float2*>(p + (size_t)(c >> 1) * V + n)[c & 1] = make_float2(a.re, a.im);
+  }
+};
+
+// Planar FP16 storage (mixed precision "half" mode; arithmetic stays FP32).
+//   links: the first two rows only (12 reals) as 6 half2 planes per direction,
+//          U16[mu*6 + c][V]; the third row is rebuilt as conj(row0 x row1),
+//          exact for SU(3) links
+//   transports: all 9 entries, W16[k*9 + c][V] (not unitary: no compression)
+//   vectors: NC half2 planes holding psi/scale, one float scale per site
+//          (the largest |re|, |im| of the site), so every site keeps FP16's
+//          relative precision whatever its magnitude
+__device__ __forceinline__ cx<float> h2c(__half2 h) {
+  const float2 f = __half22float2(h);
+  return {f.x, f.y};
+}
+
+struct GaugeP16 {
+  static constexpr int kBytes = 4 * 6 * 4;
+  static constexpr const char* kPrec = "f16";
+  const __half2* p;
+  int V;
+  __device__ __forceinline__ M3<float> link(int n, int mu) const {
+    const __half2* q = p + (size_t)mu * 6 * V + n;
+    M3<float> M;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) M.e[i][j] = h2c(__ldg(q + (size_t)(i * 3 + j) * V));
+    // row 2 = conj(row0 x row1)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int a = (j + 1) % 3, b = (j + 2) % 3;
+      const cx<float> c = cmul(M.e[0][a], M.e[1][b]) - cmul(M.e[0][b], M.e[1][a]);
+      M.e[2][j] = {c.re, -c.im};
+    }
+    return M;
+  }
+};
+struct TransP16 {
+  static constexpr int kBytes = 8 * 9 * 4;
+  const __half2* p;
+  int V;
+  __device__ __forceinline__ M3<float> mat(int n, int k) const {
+    const __half2* q = p + (size_t)k * 9 * V + n;
+    M3<float> M;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) M.e[i][j] = h2c(__ldg(q + (size_t)(i * 3 + j) * V));
+    return M;
+  }
+};
+template <int NC> struct VecP16 {  // per system: [NC][V] half2 planes, then [V] float scales
+  using unit = __half2;
+  static size_t sys_units(int V) { return (size_t)V * (NC + 1); }
+  __half2* p;
+  int V;
+  __device__ __forceinline__ const float* sc() const { return reinterpret_cast<const float*>(p + (size_t)NC * V); }
+  __device__ __forceinline__ cx<float> ld(int n, int c) const {
+    const cx<float> v = h2c(__ldg(p + (size_t)c * V + n));
+    const float s = __ldg(sc() + n);
+    return {v.re * s, v.im * s};
+  }
 };
 
 template <typename Acc, typename T> __device__ __forceinline__ V3<T> ld3(const Acc& a, int n, int off = 0) {

@@ -17,6 +17,7 @@
 #pragma once
 #include <algorithm>
 #include <chrono>
+#include <cstring>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -32,6 +33,7 @@ namespace swc {
 int param_chunk();
 double param_delta();
 int param_ns(int nc);  // systems per thread of the FP32 stencils (1, 2 or 4) for NC components
+bool param_graphs();   // replay chunks of iterations as captured CUDA graphs
 
 inline int grid_for(const void* kernel, int block, int V, int nsys, int cap) {
   static std::mutex mu;
@@ -73,6 +75,23 @@ struct DevMem {
   template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
+// FP16 links keep two rows and rebuild the third, which needs SU(3) links:
+// SW_ERR_ARG if any link of U deviates from SU(3) by more than 1e-5.
+inline int check_su3(const Geom& g, const double2* U, cudaStream_t st) {
+  DevMem m;
+  if (!m.alloc(sizeof(unsigned), st)) return SW_ERR_OOM;
+  cudaMemsetAsync(m.p, 0, sizeof(unsigned), st);
+  su3_deviation<<<sm_count() * 4, 256, 0, st>>>(g.V, U, m.as<unsigned>());
+  note_launches(1);
+  unsigned bits = 0;
+  if (cudaMemcpyAsync(&bits, m.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SW_ERR_CUDA;
+  float dev;
+  std::memcpy(&dev, &bits, sizeof(dev));
+  return (dev <= 1e-5f) ? SW_OK : SW_ERR_ARG;
+}
+
 inline int pinned_states(int nsys, SysState** out) {
   thread_local SysState* buf = nullptr;
   thread_local int cap = 0;
@@ -98,8 +117,9 @@ inline int status_to_code(int st) {
 
 // Device workspace of one batched solve, carved from a single block.
 struct Workspace {
-  double2 *b64, *r64, *t64, *p64;   // FP64 canonical; p64 only in F64 mode
-  float2 *r32, *p32, *t32, *x32;    // FP32 planar; MIXED mode only
+  double2 *b64, *r64, *t64;  // FP64 canonical
+  void *p_lo, *t_lo;         // stencil vectors p, t in the inner precision's storage
+  float2 *r32, *x32;         // FP32 residual and correction (mixed precision only)
   SysState* S;
   double* partials;
   unsigned* tickets;
@@ -113,19 +133,27 @@ constexpr int kProfSlots = 1024;  // sampled iterations per solve
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-// Bytes of workspace for nsys systems of NC complex components per site.
-inline size_t workspace_bytes(int V, int NC, int nsys, bool mixed) {
+// Bytes of workspace for nsys systems of NC complex components per site; pt:
+// bytes of one system's p (or t) in the inner precision's storage.
+inline size_t workspace_bytes_pt(int V, int NC, int nsys, bool mixed, size_t pt) {
   const size_t n = (size_t)V * NC * nsys;
   const size_t ntiles = (size_t)(V + kTile - 1) / kTile;
   size_t b = 3 * align_up(sizeof(double2) * n);
-  b += mixed ? 4 * align_up(sizeof(float2) * n) : align_up(sizeof(double2) * n);
+  b += mixed ? 2 * align_up(pt * nsys) + 2 * align_up(sizeof(float2) * n) : align_up(pt * nsys);
   b += align_up(sizeof(SysState) * nsys) + align_up(sizeof(double) * 2 * ntiles * nsys) +
        align_up(sizeof(unsigned) * nsys) + align_up(sizeof(double) * nsys) +
        align_up(sizeof(double) * 2 * kHist * nsys) + align_up(sizeof(int) * 2 * kProfSlots);
   return b;
 }
+// FP64 or FP32 storage of p and t
+inline size_t workspace_bytes(int V, int NC, int nsys, bool mixed) {
+  return workspace_bytes_pt(V, NC, nsys, mixed, (size_t)V * NC * (mixed ? sizeof(float2) : sizeof(double2)));
+}
+template <class PVec> inline size_t workspace_bytes_for(int V, int NC, int nsys, bool mixed) {
+  return workspace_bytes_pt(V, NC, nsys, mixed, sizeof(typename PVec::unit) * PVec::sys_units(V));
+}
 
-inline Workspace carve_workspace(void* base, int V, int NC, int nsys, bool mixed) {
+inline Workspace carve_workspace_pt(void* base, int V, int NC, int nsys, bool mixed, size_t pt) {
   const size_t n = (size_t)V * NC * nsys;
   const size_t ntiles = (size_t)(V + kTile - 1) / kTile;
   char* c = static_cast<char*>(base);
@@ -139,12 +167,13 @@ inline Workspace carve_workspace(void* base, int V, int NC, int nsys, bool mixed
   w.r64 = (double2*)take(sizeof(double2) * n);
   w.t64 = (double2*)take(sizeof(double2) * n);
   if (mixed) {
+    w.p_lo = take(pt * nsys);
+    w.t_lo = take(pt * nsys);
     w.r32 = (float2*)take(sizeof(float2) * n);
-    w.p32 = (float2*)take(sizeof(float2) * n);
-    w.t32 = (float2*)take(sizeof(float2) * n);
     w.x32 = (float2*)take(sizeof(float2) * n);
   } else {
-    w.p64 = (double2*)take(sizeof(double2) * n);
+    w.p_lo = take(pt * nsys);
+    w.t_lo = w.t64;
   }
   w.S = (SysState*)take(sizeof(SysState) * nsys);
   w.partials = (double*)take(sizeof(double) * 2 * ntiles * nsys);  // 2nd half: norm_b's |x0|^2
@@ -153,6 +182,13 @@ inline Workspace carve_workspace(void* base, int V, int NC, int nsys, bool mixed
   w.hist = (double*)take(sizeof(double) * 2 * kHist * nsys);
   w.pcount = (int*)take(sizeof(int) * 2 * kProfSlots);
   return w;
+}
+inline Workspace carve_workspace(void* base, int V, int NC, int nsys, bool mixed) {
+  return carve_workspace_pt(base, V, NC, nsys, mixed,
+                            (size_t)V * NC * (mixed ? sizeof(float2) : sizeof(double2)));
+}
+template <class PVec> inline Workspace carve_workspace_for(void* base, int V, int NC, int nsys, bool mixed) {
+  return carve_workspace_pt(base, V, NC, nsys, mixed, sizeof(typename PVec::unit) * PVec::sys_units(V));
 }
 
 // Extreme eigenvalues of the k x k Lanczos tridiagonal built from CG's
@@ -219,37 +255,42 @@ class Engine {
  public:
   static constexpr int NC = OpD::NC;
   using V64 = typename OpD::Vec;
-  using VF = typename OpF::Vec;
+  using VF = typename OpF::Vec;  // stencil vectors p, t
   using TF = typename std::conditional<MIXED, float, double>::type;
+  using VR = typename std::conditional<MIXED, VecP32<NC>, V64>::type;  // r and x of the inner iteration
 
   // chi, x: cap slots in the canonical layout (x: initial guess in, solution
   // out).  hs_read / hs_stage: host arrays [cap] (pinned for overlap).
   // ev: event marking the status copy (nullptr: complete() syncs the stream).
+  // use_graphs: replay chunks as a captured CUDA graph (creating the graph
+  // allocates driver resources, so allocation-free callers pass false).
   Engine(const Geom& g, const OpD& opd, const OpF& opf, double r, int cap, double2* chi, double2* x,
-         const Workspace& ws, SysState* hs_read, SysState* hs_stage, cudaStream_t st, cudaEvent_t ev)
+         const Workspace& ws, SysState* hs_read, SysState* hs_stage, cudaStream_t st, cudaEvent_t ev,
+         bool use_graphs = true)
       : g_(g), opd_(opd), opf_(opf), r_(r), cap_(cap), chi_(chi), x_(x), ws_(ws), hr_(hs_read), hst_(hs_stage),
-        st_(st), ev_(ev), n_((size_t)g.V * NC) {
+        st_(st), ev_(ev), n_((size_t)g.V * NC), use_graphs_(use_graphs && param_graphs()) {
     pstride_ = (g.V + kTile - 1) / kTile;
     rb_ = RedBuf{ws.partials, ws.tickets, pstride_, ws.hist};
-    bp_ = BatchParams{r, n_, n_};
+    vunits_ = VF::sys_units(g.V);
+    bp_ = BatchParams{r, n_, n_, vunits_};
     ns_ = MIXED ? param_ns(NC) : 1;
     ngrp_ = (cap + ns_ - 1) / ns_;
     gA_ = grid_for((const void*)apply_kernel<double, OpD>, kTile, g.V, cap, pstride_);
     gR_ = grid_for((const void*)residual64<OpD>, kTile, g.V, cap, pstride_);
-    gV_ = grid_for((const void*)cg_k3<TF, VF, NC>, 256, g.V, cap, pstride_);
+    gV_ = grid_for((const void*)cg_k3<TF, VR, VF, NC>, 256, g.V, cap, pstride_);
     gN_ = grid_for((const void*)norm_b<NC>, kTile, g.V, cap, pstride_);
     g1_ = grid_for(k1_ptr(), kTile, g.V, ngrp_, pstride_);
     g2_ = grid_for(k2_ptr(), kTile, g.V, ngrp_, pstride_);
     if constexpr (MIXED) {
-      fr_ = VF{ws.r32, g.V};
-      fp_ = VF{ws.p32, g.V};
-      ft_ = VF{ws.t32, g.V};
-      fx_ = VF{ws.x32, g.V};
+      fr_ = VR{ws.r32, g.V};
+      fx_ = VR{ws.x32, g.V};
+      fp_ = VF{static_cast<typename VF::unit*>(ws.p_lo), g.V};
+      ft_ = VF{static_cast<typename VF::unit*>(ws.t_lo), g.V};
     } else {
-      fr_ = VF{ws.r64};
-      fp_ = VF{ws.p64};
+      fr_ = VR{ws.r64};
+      fx_ = VR{x};
+      fp_ = VF{static_cast<double2*>(ws.p_lo)};
       ft_ = VF{ws.t64};
-      fx_ = VF{x};
     }
     reported_.assign(cap, 1);
     for (int i = 0; i < cap; ++i) {
@@ -272,18 +313,27 @@ class Engine {
       cudaGetLastError();
       return;
     }
-    constexpr double kCx = 2.0 * sizeof(TF);
-    const double gauge = (double)g_.V * OpF::kMats * 9 * kCx, vec = (double)n_ * kCx;
-    static const std::string c1 = std::string(OpF::kName) + (MIXED ? ".k1.f32" : ".k1.f64");
-    static const std::string c2 = std::string(OpF::kName) + (MIXED ? ".k2.f32" : ".k2.f64");
+    // bytes of the stored gauge data (links, transports) and of one system's
+    // stencil vector (p or t) and inner-precision vector (r or x)
+    const double gauge = (double)g_.V * OpF::kGaugeBytes;
+    const double pv = (double)sizeof(typename VF::unit) * vunits_;
+    const double rv = (double)sizeof(typename VR::unit) * n_;
+    static const std::string c1 = std::string(OpF::kName) + ".k1." + OpF::kPrec;
+    static const std::string c2 = std::string(OpF::kName) + ".k2." + OpF::kPrec;
     for (size_t k = 0; k < samples_.size(); ++k) {
-      prof_push(c1.c_str(), samples_[k].e0, samples_[k].e1, gauge + cnt[2 * k] * 2.0 * vec);
-      prof_push(c2.c_str(), samples_[k].e1, samples_[k].e2, gauge + cnt[2 * k + 1] * 6.0 * vec);
+      prof_push(c1.c_str(), samples_[k].e0, samples_[k].e1, gauge + cnt[2 * k] * 2.0 * pv);
+      prof_push(c2.c_str(), samples_[k].e1, samples_[k].e2, gauge + cnt[2 * k + 1] * (2.0 * pv + 4.0 * rv));
     }
     prof_commit(true);
     samples_.clear();
     cudaMemset(ws_.pcount, 0, sizeof(int) * 2 * kProfSlots);
   }
+
+  ~Engine() {
+    if (gexec_) cudaGraphExecDestroy(gexec_);
+  }
+  Engine(const Engine&) = delete;
+  Engine& operator=(const Engine&) = delete;
 
   int cap() const { return cap_; }
   size_t slot_elems() const { return n_; }
@@ -314,10 +364,9 @@ class Engine {
     bool ru = need_ru_;
     if (!staged_.empty()) {
       upload_staged();
-      if constexpr (MIXED)
-        admit_clear<NC, float2><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, ws_.p32, ws_.x32, n_, S);
-      else
-        admit_clear<NC, double2><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, ws_.p64, nullptr, n_, S);
+      using PU = typename VF::unit;
+      admit_clear<PU><<<dim3(gV_, cap_), 256, 0, st_>>>(vunits_, static_cast<PU*>(ws_.p_lo), vunits_,
+                                                         MIXED ? ws_.x32 : nullptr, MIXED ? n_ : 0, S);
       apply_kernel<double, OpD><<<dim3(gA_, cap_), kTile, 0, st_>>>(g_, opd_, V64{chi_}, V64{ws_.b64}, 0.0, n_,
                                                                     r_, 1, S, ST_ADMIT);
       norm_b<NC><<<dim3(gN_, cap_), kTile, 0, st_>>>(g_.V, ws_.b64, x_, n_, S, rb_);
@@ -330,10 +379,17 @@ class Engine {
     // After reliable updates with nothing known to be running, read the
     // statuses first rather than launch a chunk that may find nothing to do.
     if (!ru || nrun_ > 0) {
-      // time the second iteration of the chunk: by then the queue is full, so
-      // the events time the kernels rather than the host's launch latency
-      const bool prof = prof_enabled() && chunk_ > 1 && samples_.size() < (size_t)kProfSlots;
-      for (int i = 0; i < chunk_; ++i) iterate(prof && i == 1);
+      // every 4th chunk is timed when profiling, on its second iteration: by
+      // then the queue is full, so the events time the kernels rather than the
+      // host's launch latency
+      const bool prof = prof_enabled() && chunk_ > 1 && samples_.size() < (size_t)kProfSlots &&
+                        (chunks_ % 4 == 0);
+      ++chunks_;
+      if (!prof && use_graphs_ && chunks_ > 1) {
+        launch_chunk_graph();
+      } else {
+        for (int i = 0; i < chunk_; ++i) iterate(prof && i == 1);
+      }
     }
     cudaMemcpyAsync(hr_, S, sizeof(SysState) * cap_, cudaMemcpyDeviceToHost, st_);
     if (ev_) cudaEventRecord(ev_, st_);
@@ -396,9 +452,35 @@ class Engine {
     residual64<OpD><<<dim3(gR_, cap_), kTile, 0, st_>>>(g_, opd_, V64{ws_.t64}, V64{ws_.b64}, V64{ws_.r64}, bp_, S,
                                                         rb_);
     if constexpr (MIXED) demote_r<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, ws_.r64, ws_.r32, n_, n_, S);
-    cg_k3<TF, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, S, ST_JUST_UPDATED);
+    cg_k3<TF, VR, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, vunits_, S, ST_JUST_UPDATED);
     commit_status<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S);
     note_launches(MIXED ? 6 : 4);
+  }
+
+  // One chunk of iterations as a CUDA graph, captured on first use: every
+  // kernel argument is fixed for the engine's life, so the graph is replayed.
+  void launch_chunk_graph() {
+    if (!gexec_ && !graph_failed_) {
+      cudaGraph_t graph = nullptr;
+      bool ok = cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        for (int i = 0; i < chunk_; ++i) iterate(false, false);
+        ok = cudaStreamEndCapture(st_, &graph) == cudaSuccess && graph;
+      }
+      ok = ok && cudaGraphInstantiate(&gexec_, graph, 0) == cudaSuccess;
+      if (graph) cudaGraphDestroy(graph);
+      if (!ok) {
+        cudaGetLastError();
+        gexec_ = nullptr;
+        graph_failed_ = true;
+      }
+    }
+    if (gexec_) {
+      cudaGraphLaunch(gexec_, st_);
+      note_launches(3 * chunk_);
+    } else {
+      for (int i = 0; i < chunk_; ++i) iterate(false);
+    }
   }
 
   const void* k1_ptr() const {
@@ -410,25 +492,25 @@ class Engine {
   }
   const void* k2_ptr() const {
     switch (ns_) {
-      case 2: return (const void*)cg_k2<TF, OpF, 2>;
-      case 4: return (const void*)cg_k2<TF, OpF, 4>;
-      default: return (const void*)cg_k2<TF, OpF, 1>;
+      case 2: return (const void*)cg_k2<TF, OpF, 2, VR>;
+      case 4: return (const void*)cg_k2<TF, OpF, 4, VR>;
+      default: return (const void*)cg_k2<TF, OpF, 1, VR>;
     }
   }
   template <int NS> void launch_k12(int* c) {
     SysState* S = ws_.S;
     cg_k1<TF, OpF, NS><<<dim3(g1_, ngrp_), kTile, 0, st_>>>(g_, opf_, fp_, ft_, bp_, cap_, S, rb_, c);
     if (c) cudaEventRecord(samples_.back().e1, st_);
-    cg_k2<TF, OpF, NS><<<dim3(g2_, ngrp_), kTile, 0, st_>>>(g_, opf_, ft_, fp_, fr_, fx_, bp_, cap_, S, rb_,
-                                                             c ? c + 1 : nullptr);
+    cg_k2<TF, OpF, NS, VR><<<dim3(g2_, ngrp_), kTile, 0, st_>>>(g_, opf_, ft_, fp_, fr_, fx_, bp_, cap_, S, rb_,
+                                                                 c ? c + 1 : nullptr);
   }
 
   // One CG iteration (k1, k2, k3).  A sampled iteration is bracketed by
   // events, and its stencil kernels count the systems they compute; the
   // algorithmic bytes of a launch (every stored element touched once) are the
   // links (and transports) once plus, per computed system, the vectors read
-  // and written: k1 p, t; k2 t, p and x, r read and written.
-  void iterate(bool sample) {
+  // and written: k1 p read, t written; k2 t, p read and x, r read and written.
+  void iterate(bool sample, bool count = true) {
     SysState* S = ws_.S;
     int* c = nullptr;
     if (sample) {
@@ -442,8 +524,8 @@ class Engine {
       default: launch_k12<1>(c); break;
     }
     if (sample) cudaEventRecord(samples_.back().e2, st_);
-    cg_k3<TF, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, S, ST_RUNNING);
-    note_launches(3);
+    cg_k3<TF, VR, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, vunits_, S, ST_RUNNING);
+    if (count) note_launches(3);
   }
 
   struct Sample {
@@ -465,13 +547,17 @@ class Engine {
   int pstride_ = 0, ngrp_ = 0, gA_ = 0, gR_ = 0, gV_ = 0, gN_ = 0, g1_ = 0, g2_ = 0;
   RedBuf rb_{};
   BatchParams bp_{};
-  VF fr_{}, fp_{}, ft_{}, fx_{};
+  VF fp_{}, ft_{};
+  VR fr_{}, fx_{};
+  size_t vunits_ = 0;
   int chunk_ = 16;
   double delta_ = 0.1;
   bool need_ru_ = false;
   int nrun_ = 0, ns_ = 1;
   std::vector<Sample> samples_;
-  long long rounds_ = 0;
+  long long rounds_ = 0, chunks_ = 0;
+  bool use_graphs_ = true, graph_failed_ = false;
+  cudaGraphExec_t gexec_ = nullptr;
   std::vector<int> staged_;
   std::vector<char> reported_;
 };
@@ -503,11 +589,11 @@ inline int worst_code(int worst, int code) {
 // staging).
 template <class OpD, class OpF, bool MIXED>
 int run_cgne_ws(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a, const Workspace& ws,
-                SysState* hs) {
+                SysState* hs, bool use_graphs = true) {
   using namespace std::chrono;
   const auto t0 = steady_clock::now();
   Engine<OpD, OpF, MIXED> e(g, opd, opf, a.r, a.nsys, const_cast<double2*>(a.chi), a.x, ws, hs, hs + a.nsys,
-                            a.stream, nullptr);
+                            a.stream, nullptr, use_graphs);
   for (int i = 0; i < a.nsys; ++i) e.stage(i, a.masses[i], a.tol, a.max_iter);
   const long long max_rounds = 4LL * (a.max_iter / param_chunk() + 2) + 1000;
   int rc = SW_OK;
@@ -547,11 +633,12 @@ int run_cgne_ws(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& 
 // pinned host buffer for the status words.
 template <class OpD, class OpF, bool MIXED>
 int run_cgne(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a) {
+  using VF = typename OpF::Vec;
   DevMem mem;
-  if (!mem.alloc(workspace_bytes(g.V, OpD::NC, a.nsys, MIXED), a.stream)) return SW_ERR_OOM;
+  if (!mem.alloc(workspace_bytes_for<VF>(g.V, OpD::NC, a.nsys, MIXED), a.stream)) return SW_ERR_OOM;
   SysState* hs = nullptr;
   if (int e = pinned_states(2 * a.nsys, &hs)) return e;
-  const Workspace ws = carve_workspace(mem.p, g.V, OpD::NC, a.nsys, MIXED);
+  const Workspace ws = carve_workspace_for<VF>(mem.p, g.V, OpD::NC, a.nsys, MIXED);
   return run_cgne_ws<OpD, OpF, MIXED>(g, opd, opf, a, ws, hs);
 }
 

@@ -82,11 +82,30 @@ __device__ __forceinline__ V3<T> sw_site(const Geom& g, int n, const G& U, const
 
 template <typename T> struct Sp { V3<T> s[4]; };
 
-template <typename In, typename T> __device__ __forceinline__ Sp<T> ld_sp(const In& in, int n) {
-  Sp<T> p;
+template <typename In, typename T> struct SpLoader {
+  static __device__ __forceinline__ Sp<T> load(const In& in, int n) {
+    Sp<T> p;
 #pragma unroll
-  for (int s = 0; s < 4; ++s) p.s[s] = ld3<In, T>(in, n, 3 * s);
-  return p;
+    for (int s = 0; s < 4; ++s) p.s[s] = ld3<In, T>(in, n, 3 * s);
+    return p;
+  }
+};
+// float4 planes: a spinor is 6 sixteen-byte loads
+template <> struct SpLoader<VecP32q<12>, float> {
+  static __device__ __forceinline__ Sp<float> load(const VecP32q<12>& in, int n) {
+    Sp<float> p;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const float4 v = __ldg(in.p + (size_t)q * in.V + n);
+      const int c0 = 2 * q, c1 = 2 * q + 1;
+      p.s[c0 / 3].c[c0 % 3] = {v.x, v.y};
+      p.s[c1 / 3].c[c1 % 3] = {v.z, v.w};
+    }
+    return p;
+  }
+};
+template <typename In, typename T> __device__ __forceinline__ Sp<T> ld_sp(const In& in, int n) {
+  return SpLoader<In, T>::load(in, n);
 }
 
 // h = (psi_u - c A_mu psi_d): the two independent spin rows of (1 - c g_mu) psi

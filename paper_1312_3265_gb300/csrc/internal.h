@@ -32,6 +32,10 @@ int wilson_apply_f64(const Geom& g, const double2* U, const double2* in, double2
 int sw_cgne(const Geom& g, const SolveArgs& a);
 int wilson_cgne(const Geom& g, const SolveArgs& a);
 
+// Tunables set through the C ABI (api.cu), also used by the autotuner.
+extern "C" int sw_set_param(int key, double value);
+extern "C" int sw_get_param(int key, double* value);
+
 // Argument checks shared by the entry points (api.cu).
 int make_geom(const sw_lattice* lat, Geom* g);
 int check_buf(const void* p, size_t bytes);

@@ -15,6 +15,63 @@ static __global__ void pack_mats_p32(int V, int nobj, const double2* __restrict_
   }
 }
 
+// canonical FP64 links [V][4][9] -> FP16 12-real planes [4*6][V] (rows 0, 1)
+static __global__ void pack_links_h12(int V, const double2* __restrict__ src, __half2* __restrict__ dst) {
+  const size_t total = (size_t)V * 4 * 6;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t n = i / 24, r = i - n * 24, mu = r / 6, c = r - mu * 6;
+    const double2 v = src[(n * 4 + mu) * 9 + c];
+    dst[(mu * 6 + c) * V + n] = __floats2half2_rn((float)v.x, (float)v.y);
+  }
+}
+
+// canonical FP64 [V][nobj][9] -> FP16 planes [nobj*9][V]
+static __global__ void pack_mats_h(int V, int nobj, const double2* __restrict__ src, __half2* __restrict__ dst) {
+  const size_t total = (size_t)V * nobj * 9;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t n = i / ((size_t)nobj * 9);
+    const size_t c = i - n * nobj * 9;
+    const double2 v = src[i];
+    dst[c * V + n] = __floats2half2_rn((float)v.x, (float)v.y);
+  }
+}
+
+// Largest deviation of a link from SU(3): max over entries of |U U^+ - 1| and
+// |det U - 1|, into *dev (as float bits; non-negative floats order like ints).
+// The 12-real FP16 links rebuild the third row, which is exact only in SU(3).
+static __global__ void su3_deviation(int V, const double2* __restrict__ U, unsigned* dev) {
+  float worst = 0.f;
+  for (size_t l = blockIdx.x * (size_t)blockDim.x + threadIdx.x; l < (size_t)V * 4; l += (size_t)gridDim.x * blockDim.x) {
+    const double2* q = U + l * 9;
+    double a[3][3][2];
+    for (int i = 0; i < 9; ++i) {
+      a[i / 3][i % 3][0] = q[i].x;
+      a[i / 3][i % 3][1] = q[i].y;
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double re = 0, im = 0;
+        for (int k = 0; k < 3; ++k) {  // (U U^+)_ij = sum_k U_ik conj(U_jk)
+          re += a[i][k][0] * a[j][k][0] + a[i][k][1] * a[j][k][1];
+          im += a[i][k][1] * a[j][k][0] - a[i][k][0] * a[j][k][1];
+        }
+        worst = fmaxf(worst, (float)hypot(re - (i == j), im));
+      }
+    // det = sum over the first row of U_0j times the cofactor
+    double dre = 0, dim = 0;
+    for (int j = 0; j < 3; ++j) {
+      const int b = (j + 1) % 3, c = (j + 2) % 3;
+      const double cre = a[1][b][0] * a[2][c][0] - a[1][b][1] * a[2][c][1] - (a[1][c][0] * a[2][b][0] - a[1][c][1] * a[2][b][1]);
+      const double cim = a[1][b][0] * a[2][c][1] + a[1][b][1] * a[2][c][0] - (a[1][c][0] * a[2][b][1] + a[1][c][1] * a[2][b][0]);
+      dre += a[0][j][0] * cre - a[0][j][1] * cim;
+      dim += a[0][j][0] * cim + a[0][j][1] * cre;
+    }
+    worst = fmaxf(worst, (float)hypot(dre - 1.0, dim));
+  }
+  if (!(worst == worst)) worst = 3.0e38f;
+  atomicMax(dev, __float_as_uint(worst));
+}
+
 // x64 (canonical) += x32 (planar); x32 = 0   -- systems with status NEED_RU
 template <int NC>
 __global__ void accum_x(int V, double2* x64, float2* x32, size_t s64, size_t s32, const SysState* S) {
@@ -52,17 +109,18 @@ __global__ void demote_r(int V, const double2* r64, float2* r32, size_t s64, siz
 }
 
 // Admission, step 1 (systems in ST_ADMIT): clear the search direction (and the
-// FP32 correction), which may hold a previous system's values.
-template <int NC, typename TP>
-__global__ void admit_clear(int V, TP* p, float2* x32, size_t s, const SysState* S) {
+// FP32 correction), which may hold a previous system's values.  units: the
+// storage units of one system's p (FP16 vectors include their scales).
+template <typename TP>
+__global__ void admit_clear(size_t units, TP* p, size_t pstride, float2* x32, size_t xunits, const SysState* S) {
   const int sys = blockIdx.y;
   if (S[sys].status != ST_ADMIT) return;
-  p += sys * s;
-  if (x32) x32 += sys * s;
-  const size_t n = (size_t)V * NC;
+  p += sys * pstride;
+  if (x32) x32 += sys * xunits;
+  const size_t n = units > xunits ? units : xunits;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    p[i] = TP{};
-    if (x32) x32[i] = make_float2(0.f, 0.f);
+    if (i < units) p[i] = TP{};
+    if (x32 && i < xunits) x32[i] = make_float2(0.f, 0.f);
   }
 }
 

@@ -83,13 +83,13 @@ extern "C" int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, 
   int rc;
   if (op == SW_OP_STAGGERED_WILSON) {
     const SWd opd{GaugeC64{a.U}, TransC64{a.W}};
-    rc = run_cgne_ws<SWd, SWd, false>(g, opd, opd, a, ws, hs);
+    rc = run_cgne_ws<SWd, SWd, false>(g, opd, opd, a, ws, hs, false);
   } else if (r == 1.0) {
     const Wd<true> opd{GaugeC64{a.U}};
-    rc = run_cgne_ws<Wd<true>, Wd<true>, false>(g, opd, opd, a, ws, hs);
+    rc = run_cgne_ws<Wd<true>, Wd<true>, false>(g, opd, opd, a, ws, hs, false);
   } else {
     const Wd<false> opd{GaugeC64{a.U}};
-    rc = run_cgne_ws<Wd<false>, Wd<false>, false>(g, opd, opd, a, ws, hs);
+    rc = run_cgne_ws<Wd<false>, Wd<false>, false>(g, opd, opd, a, ws, hs, false);
   }
   if (info) {
     info->status = rc;

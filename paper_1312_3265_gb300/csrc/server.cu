@@ -92,8 +92,10 @@ struct EngineImpl : EngineBase {
 
 using SW64 = SWOp<double, GaugeC64, TransC64, VecC64>;
 using SW32 = SWOp<float, GaugeP32, TransP32, VecP32>;
+using SW16 = SWOp<float, GaugeP16, TransP16, VecP16>;
 template <bool R1> using W64 = WOp<double, GaugeC64, VecC64, R1>;
-template <bool R1> using W32 = WOp<float, GaugeP32, VecP32, R1>;
+template <bool R1> using W32 = WOp<float, GaugeP32, VecP32q, R1>;
+template <bool R1> using W16 = WOp<float, GaugeP16, VecP16, R1>;
 
 // Allocate on `st`, remembering the block for the engine's destructor.
 static void* own(std::vector<DevMem*>& owned, size_t bytes, cudaStream_t st) {
@@ -120,10 +122,10 @@ static int build_engine(const Geom& g, int cap, double r, int prec, MakeOps make
   const size_t n = (size_t)g.V * OpD::NC;
   double2* chi = (double2*)own(impl->owned, sizeof(double2) * n * cap, impl->st);
   double2* x = (double2*)own(impl->owned, sizeof(double2) * n * cap, impl->st);
-  void* wsm = own(impl->owned, workspace_bytes(g.V, OpD::NC, cap, MIXED), impl->st);
+  void* wsm = own(impl->owned, workspace_bytes_for<typename OpF::Vec>(g.V, OpD::NC, cap, MIXED), impl->st);
   if (!chi || !x || !wsm) return SW_ERR_OOM;
   if (cudaMallocHost((void**)&impl->hs, sizeof(SysState) * 2 * cap) != cudaSuccess) return SW_ERR_OOM;
-  const Workspace ws = carve_workspace(wsm, g.V, OpD::NC, cap, MIXED);
+  const Workspace ws = carve_workspace_for<typename OpF::Vec>(wsm, g.V, OpD::NC, cap, MIXED);
   impl->e = std::make_unique<Engine<OpD, OpF, MIXED>>(g, opd, opf, r, cap, chi, x, ws, impl->hs, impl->hs + cap,
                                                       impl->st, impl->ev);
   if (cudaStreamSynchronize(impl->st) != cudaSuccess) return SW_ERR_CUDA;
@@ -138,8 +140,12 @@ static size_t engine_bytes(const Geom& g, int op, int prec, int cap) {
   const int nc = op == SW_OP_WILSON ? 12 : 3;
   const bool mixed = prec != SW_PREC_F64;
   size_t b = V * 576 + (op == SW_OP_WILSON ? 0 : V * 1152);
-  if (mixed) b += V * 288 + (op == SW_OP_WILSON ? 0 : V * 576);
-  b += 2 * V * nc * 16 * (size_t)cap + workspace_bytes(g.V, nc, cap, mixed) + (8u << 10) * 8;
+  if (prec == SW_PREC_F32_RELIABLE) b += V * 288 + (op == SW_OP_WILSON ? 0 : V * 576);
+  if (prec == SW_PREC_F16_RELIABLE) b += V * 96 + (op == SW_OP_WILSON ? 0 : V * 288);
+  const size_t ws = prec == SW_PREC_F16_RELIABLE
+                        ? workspace_bytes_pt(g.V, nc, cap, true, 4 * V * (nc + 1))
+                        : workspace_bytes(g.V, nc, cap, mixed);
+  b += 2 * V * nc * 16 * (size_t)cap + ws + (8u << 10) * 8;
   return b;
 }
 
@@ -167,6 +173,21 @@ static int make_engine(const Geom& g, int op, const double2* U, double r, int pr
         *d = *f = SW64{GaugeC64{Ur}, TransC64{Wr}};
         return (int)SW_OK;
       }, out);
+    if (prec == SW_PREC_F16_RELIABLE)
+      return build_engine<SW64, SW16, true>(g, cap, r, prec, [&](auto& owned, cudaStream_t st, SW64* d, SW16* f) {
+        double2 *Ur, *Wr;
+        if (int e = sw_common(owned, st, &Ur, &Wr)) return e;
+        if (int e = check_su3(g, Ur, st)) return e;
+        __half2* u16 = (__half2*)own(owned, V * 96, st);
+        __half2* w16 = (__half2*)own(owned, V * 288, st);
+        if (!u16 || !w16) return (int)SW_ERR_OOM;
+        pack_links_h12<<<gp, 256, 0, st>>>(g.V, Ur, u16);
+        pack_mats_h<<<gp, 256, 0, st>>>(g.V, 8, Wr, w16);
+        note_launches(2);
+        *d = SW64{GaugeC64{Ur}, TransC64{Wr}};
+        *f = SW16{GaugeP16{u16, g.V}, TransP16{w16, g.V}};
+        return (int)SW_OK;
+      }, out);
     return build_engine<SW64, SW32, true>(g, cap, r, prec, [&](auto& owned, cudaStream_t st, SW64* d, SW32* f) {
       double2 *Ur, *Wr;
       if (int e = sw_common(owned, st, &Ur, &Wr)) return e;
@@ -189,6 +210,20 @@ static int make_engine(const Geom& g, int op, const double2* U, double r, int pr
         double2* Ur;
         if (int e = copy_links(owned, st, &Ur)) return e;
         *d = *f = W64<R1>{GaugeC64{Ur}};
+        return (int)SW_OK;
+      }, out);
+    if (prec == SW_PREC_F16_RELIABLE)
+      return build_engine<W64<R1>, W16<R1>, true>(g, cap, r, prec,
+                                                  [&](auto& owned, cudaStream_t st, W64<R1>* d, W16<R1>* f) {
+        double2* Ur;
+        if (int e = copy_links(owned, st, &Ur)) return e;
+        if (int e = check_su3(g, Ur, st)) return e;
+        __half2* u16 = (__half2*)own(owned, V * 96, st);
+        if (!u16) return (int)SW_ERR_OOM;
+        pack_links_h12<<<gp, 256, 0, st>>>(g.V, Ur, u16);
+        note_launches(1);
+        *d = W64<R1>{GaugeC64{Ur}};
+        *f = W16<R1>{GaugeP16{u16, g.V}};
         return (int)SW_OK;
       }, out);
     return build_engine<W64<R1>, W32<R1>, true>(g, cap, r, prec,
@@ -371,7 +406,8 @@ int sw_server_add_engine(sw_server srv, const sw_lattice* lat, int op, const voi
   Geom g;
   if (int e = make_geom(lat, &g)) return e;
   if (op != SW_OP_STAGGERED_WILSON && op != SW_OP_WILSON) return SW_ERR_ARG;
-  if (precision != SW_PREC_F64 && precision != SW_PREC_F32_RELIABLE) return SW_ERR_ARG;
+  if (precision != SW_PREC_F64 && precision != SW_PREC_F32_RELIABLE && precision != SW_PREC_F16_RELIABLE)
+    return SW_ERR_ARG;
   if (slots < 1 || slots > 4096 || !(r == r)) return SW_ERR_ARG;
   if (int e = check_buf(U, (size_t)g.V * 576)) return e;
   const size_t need = engine_bytes(g, op, precision, slots);

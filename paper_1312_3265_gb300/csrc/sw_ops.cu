@@ -5,6 +5,7 @@ namespace swc {
 
 using SW64 = SWOp<double, GaugeC64, TransC64, VecC64>;
 using SW32 = SWOp<float, GaugeP32, TransP32, VecP32>;
+using SW16 = SWOp<float, GaugeP16, TransP16, VecP16>;
 
 int sw_apply_f64(const Geom& g, const double2* U, const double2* W, const double2* in, double2* out,
                  double mass, double r, int dagger, cudaStream_t st) {
@@ -31,6 +32,19 @@ int sw_cgne(const Geom& g, const SolveArgs& a) {
     note_launches(2);
     const SW32 opf{GaugeP32{mu.as<float2>(), g.V}, TransP32{mw.as<float2>(), g.V}};
     return run_cgne<SW64, SW32, true>(g, opd, opf, a);
+  }
+  if (a.precision == SW_PREC_F16_RELIABLE) {
+    if (int e = check_su3(g, a.U, a.stream)) return e;
+    DevMem mu, mw;
+    if (!mu.alloc(sizeof(__half2) * 24 * (size_t)g.V, a.stream) ||
+        !mw.alloc(sizeof(__half2) * 72 * (size_t)g.V, a.stream))
+      return SW_ERR_OOM;
+    const int gp = sm_count() * 8;
+    pack_links_h12<<<gp, 256, 0, a.stream>>>(g.V, a.U, mu.as<__half2>());
+    pack_mats_h<<<gp, 256, 0, a.stream>>>(g.V, 8, a.W, mw.as<__half2>());
+    note_launches(2);
+    const SW16 opf{GaugeP16{mu.as<__half2>(), g.V}, TransP16{mw.as<__half2>(), g.V}};
+    return run_cgne<SW64, SW16, true>(g, opd, opf, a);
   }
   return SW_ERR_ARG;
 }

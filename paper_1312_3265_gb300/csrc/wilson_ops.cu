@@ -5,7 +5,8 @@
 namespace swc {
 
 template <bool R1> using W64 = WOp<double, GaugeC64, VecC64, R1>;
-template <bool R1> using W32 = WOp<float, GaugeP32, VecP32, R1>;
+template <bool R1> using W32 = WOp<float, GaugeP32, VecP32q, R1>;
+template <bool R1> using W16 = WOp<float, GaugeP16, VecP16, R1>;
 
 template <bool R1>
 static int apply_impl(const Geom& g, const double2* U, const double2* in, double2* out, double mass, double r,
@@ -36,6 +37,15 @@ static int cgne_impl(const Geom& g, const SolveArgs& a) {
     note_launches(1);
     const W32<R1> opf{GaugeP32{mu.as<float2>(), g.V}};
     return run_cgne<W64<R1>, W32<R1>, true>(g, opd, opf, a);
+  }
+  if (a.precision == SW_PREC_F16_RELIABLE) {
+    if (int e = check_su3(g, a.U, a.stream)) return e;
+    DevMem mu;
+    if (!mu.alloc(sizeof(__half2) * 24 * (size_t)g.V, a.stream)) return SW_ERR_OOM;
+    pack_links_h12<<<sm_count() * 8, 256, 0, a.stream>>>(g.V, a.U, mu.as<__half2>());
+    note_launches(1);
+    const W16<R1> opf{GaugeP16{mu.as<__half2>(), g.V}};
+    return run_cgne<W64<R1>, W16<R1>, true>(g, opd, opf, a);
   }
   return SW_ERR_ARG;
 }

@@ -93,7 +93,7 @@ def test_small_workload_sw(sw):
     check(sw, P, chi, sw.SW_PREC_F32_RELIABLE)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("alpha", [0, 7])
 def test_small_workload_wilson(sw, prec, alpha):
     P = Problem(sw, (4, 4, 4, 4), sw.SW_OP_WILSON, 0, ls.LINK_EPS_SMALL, 0.05)
@@ -105,7 +105,7 @@ def test_small_workload_wilson(sw, prec, alpha):
 
 
 @pytest.mark.parametrize("op", [0, 1])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_ragged_antiperiodic(sw, op, prec):
     P = Problem(sw, (6, 6, 4, 6), op, 2, ls.PLAQ_EPS, 0.1, apbc=True)
     chi = ls.gaussian_source(P.dims, P.nc, 3).reshape(-1)
@@ -117,6 +117,7 @@ def test_wilson_general_r(sw):
     chi = ls.gaussian_source(P.dims, 12, 1).reshape(-1)
     check(sw, P, chi, sw.SW_PREC_F64)
     check(sw, P, chi, sw.SW_PREC_F32_RELIABLE)
+    check(sw, P, chi, sw.SW_PREC_F16_RELIABLE)
 
 
 def test_edge_cases(sw):
@@ -154,13 +155,14 @@ def test_full_size_solve(sw):
     for op in (sw.SW_OP_STAGGERED_WILSON, sw.SW_OP_WILSON):
         P = Problem(sw, (16, 16, 16, 32), op, 0, ls.PLAQ_EPS, 0.1)
         chi = ls.point_source(P.dims, P.nc, 0).reshape(-1)
-        x, info = P.solve(sw, chi, 1e-8, sw.SW_PREC_F32_RELIABLE)
-        assert info.status == sw.SW_OK and info.true_rel_resid <= 1e-8
-        assert P.true_resid(chi, x) <= 1.01e-8
+        for prec in (sw.SW_PREC_F32_RELIABLE, sw.SW_PREC_F16_RELIABLE):
+            x, info = P.solve(sw, chi, 1e-8, prec)
+            assert info.status == sw.SW_OK and info.true_rel_resid <= 1e-8
+            assert P.true_resid(chi, x) <= 1.01e-8
 
 
 @pytest.mark.parametrize("op", [0, 1])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_batch_is_bitwise_single(sw, op, prec):
     """Each system of a batch gives bit-identical results to solving it alone:
     the per-system arithmetic and the reduction order (fixed 128-site tiles) do
@@ -249,3 +251,54 @@ def test_register_blocking_widths(sw, op, widths):
                 assert P.true_resid(chis[i].reshape(-1), xs[i].reshape(-1)) <= 1.01e-9
     finally:
         sw.sw_set_param(key, old)
+
+
+
+def test_half_precision_needs_su3_links(sw):
+    """FP16 storage keeps two rows of each link and rebuilds the third, so links
+    that are not SU(3) are refused before anything runs."""
+    import torch
+    P = Problem(sw, (4, 4, 4, 4), sw.SW_OP_WILSON, 3, 0.3, 0.1)
+    chi = dev(ls.gaussian_source(P.dims, 12, 2).reshape(-1, 4, 3))
+    x = torch.zeros_like(chi)
+    with pytest.raises(sw.SWError) as e:
+        sw.cgne_solve(P.dims, P.op, P.U * 1.01, None, chi, x, 0.1, 1.0, 1e-8, 1000, sw.SW_PREC_F16_RELIABLE)
+    assert e.value.code == -8
+    info = sw.cgne_solve(P.dims, P.op, P.U * 1.01, None, chi, x, 0.1, 1.0, 1e-8, 1000, sw.SW_PREC_F32_RELIABLE)
+    assert info.status == sw.SW_OK  # FP32 keeps all 18 reals: any links work
+
+
+def test_graph_replay_is_bitwise_launches(sw):
+    """Chunks of iterations replayed as a captured CUDA graph give exactly the
+    results of launching the kernels one by one."""
+    import torch
+    P = Problem(sw, (6, 4, 4, 6), sw.SW_OP_WILSON, 9, ls.PLAQ_EPS, 0.05)
+    chis = np.stack([ls.gaussian_source(P.dims, 12, 60 + i).reshape(-1, 4, 3) for i in range(3)])
+    chi = dev(chis)
+    out = {}
+    old = sw.sw_get_param(sw.SW_PARAM_GRAPHS)
+    try:
+        for gflag in (0, 1):
+            sw.sw_set_param(sw.SW_PARAM_GRAPHS, gflag)
+            x = torch.zeros_like(chi)
+            rc, infos = sw.cgne_solve_batch(P.dims, P.op, P.U, None, chi, x, [0.05, 0.1, 0.2], 1.0, 1e-10, 10000,
+                                            sw.SW_PREC_F32_RELIABLE)
+            assert rc == sw.SW_OK and infos[0].iters > 3 * 16  # several chunks, so replays happen
+            out[gflag] = x.cpu().numpy()
+    finally:
+        sw.sw_set_param(sw.SW_PARAM_GRAPHS, old)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_autotune_picks_a_width_and_solves(sw):
+    import torch
+    P = Problem(sw, (8, 8, 8, 8), sw.SW_OP_STAGGERED_WILSON, 4, ls.PLAQ_EPS, 0.1)
+    old = sw.sw_get_param(sw.SW_PARAM_NS_SW)
+    try:
+        best, times = sw.sw_autotune(P.dims, P.op, P.U, P.W, 6, sw.SW_PREC_F32_RELIABLE, iters=32)
+        assert best in (1, 2, 4) and sw.sw_get_param(sw.SW_PARAM_NS_SW) == best
+        assert all(t > 0 for t in times.values()) and times[best] == min(times.values())
+        chi = ls.gaussian_source(P.dims, 3, 8).reshape(-1)
+        check(sw, P, chi, sw.SW_PREC_F32_RELIABLE)
+    finally:
+        sw.sw_set_param(sw.SW_PARAM_NS_SW, old)

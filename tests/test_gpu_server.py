@@ -29,7 +29,7 @@ def links(dims, seed):
     return torch.from_numpy(ls.su3_links(dims, seed, ls.PLAQ_EPS)).cuda()
 
 
-ENGINES = [((4, 4, 4, 4), 0, 1), ((6, 4, 4, 6), 1, 1), ((4, 4, 2, 6), 0, 0), ((4, 4, 4, 4), 1, 0)]
+ENGINES = [((4, 4, 4, 4), 0, 1), ((6, 4, 4, 6), 1, 1), ((4, 4, 2, 6), 0, 0), ((4, 4, 4, 4), 1, 2)]
 # (dims, op, precision)
 
 

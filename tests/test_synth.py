@@ -69,3 +69,10 @@ def test_sources():
     O = ls.haar_su3(dims, 2)
     assert np.abs(O @ np.conj(np.swapaxes(O, -1, -2)) - np.eye(3)).max() < 1e-13
     assert np.abs(np.linalg.det(O) - 1).max() < 1e-13
+
+
+def test_parallel_link_generation_is_identical():
+    dims = (16, 16, 16, 16)
+    a = ls.su3_links(dims, 4, 0.2)
+    b = ls.su3_links(dims, 4, 0.2, processes=3)
+    assert np.array_equal(a, b)
