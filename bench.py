@@ -49,6 +49,15 @@ ITERS_TABLE = {"sw": {0.02: 41.0, 0.05: 39.0, 0.1: 36.9, 0.2: 32.0},
                "wilson": {0.02: 118.0, 0.05: 113.6, 0.1: 107.0, 0.2: 94.9}}
 
 
+# DRAM traffic of the dominant kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, profiles/ncu_wilson_k2_fp32_16x16x16x32_12sys.md):
+# bytes of one launch over `systems` running systems and the algorithmic bytes
+# of that launch.  A bench launch's traffic is scaled by its algorithmic bytes
+# (traffic grows with the systems computed).  Set to None when the kernel
+# changes after the capture.
+NCU_TRAFFIC = {"wilson.k2.f32": {"bytes": 947.0e6, "algorithmic": 943.7e6, "systems": 12}}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,9 +346,12 @@ def run_ours(args):
     if dom:
         name, d = dom
         ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        bpl = d["bytes"] / d["launches"]
+        cap = NCU_TRAFFIC.get(name)
+        traffic = round(cap["bytes"] * bpl / cap["algorithmic"]) if cap else None
         roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "traffic": None, "peak_kind": peak_kind,
-                "bytes_per_launch": d["bytes"] / d["launches"], "launch_ms": d["ms"] / d["launches"]}
+                "frac": round(ach / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                "bytes_per_launch": bpl, "launch_ms": d["ms"] / d["launches"]}
     kernels = {k: {"launches": v["launches"], "ms_per_launch": round(v["ms"] / v["launches"], 4),
                    "GB/s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1),
                    "frac_hbm": round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / peak, 4)}

@@ -57,6 +57,7 @@ struct EngineBase {
   virtual const double* hist() const = 0;  // device [cap][kHist][2]
   virtual cudaStream_t stream() const = 0;
   virtual int precision() const = 0;
+  virtual void flush_profile() = 0;
 };
 
 template <class OpD, class OpF, bool MIXED>
@@ -88,6 +89,7 @@ struct EngineImpl : EngineBase {
   const double* hist() const override { return e->hist(); }
   cudaStream_t stream() const override { return st; }
   int precision() const override { return prec; }
+  void flush_profile() override { e->flush_profile(); }
 };
 
 using SW64 = SWOp<double, GaugeC64, TransC64, VecC64>;
@@ -306,6 +308,10 @@ struct Server {
           if (act < 0) {
             fail(act);
             return;
+          }
+          if (prof_enabled()) {  // the stream is idle: hand timing samples to the profiler
+            e.flush_profile();
+            prof_flush();
           }
           has_work[k] = act > 0;
           fin.clear();

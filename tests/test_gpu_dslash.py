@@ -145,3 +145,31 @@ def test_abi_rejects_bad_arguments(sw):
     with pytest.raises(sw.SWError) as e:  # in and out overlap
         sw.sw_dslash_apply(dims, U, W, v, v, 0.1)
     assert e.value.code == -8
+
+
+def test_large_lattice_sampled_sites(sw):
+    """24^3x48 (the batched multi-source workload's lattice; FP32 links no longer
+    fit in L2): sampled output sites of both FP64 operators against the one-site
+    oracle, periodic in time."""
+    import torch
+    dims = (24, 24, 24, 48)
+    V = ls.volume(dims)
+    Uh = ls.su3_links(dims, 0, ls.PLAQ_EPS, processes=8)
+    U = dev(Uh)
+    W = torch.empty((V, 8, 3, 3), dtype=torch.complex128, device="cuda")
+    sw.sw_hypercube_build(dims, U, W)
+    psi_h = rand_vec(V, 3, 17)
+    spn_h = rand_vec(V, 12, 18).reshape(V, 4, 3)
+    psi, spn = dev(psi_h), dev(spn_h)
+    o1, o2 = torch.empty_like(psi), torch.empty_like(spn)
+    sw.sw_dslash_apply(dims, U, W, psi, o1, 0.05, 1.0, False)
+    sw.wilson_dslash_apply(dims, U, spn, o2, 0.05, 1.0, True)
+    torch.cuda.synchronize()
+    a, b = o1.cpu().numpy(), o2.cpu().numpy()
+    rng = np.random.default_rng(1)
+    for n in np.concatenate([[0, V - 1], rng.integers(0, V, 14)]):
+        n = int(n)
+        want = site.sw_dslash_site(Uh, psi_h, dims, n, 0.05, 1.0, False, False)
+        assert np.abs(a[n] - want).max() < TOL * np.abs(want).max() * 10
+        want = site.wilson_dslash_site(Uh, spn_h, dims, n, 0.05, 1.0, True, False)
+        assert np.abs(b[n] - want).max() < TOL * np.abs(want).max() * 10
