@@ -76,7 +76,11 @@ def check(sw, P, chi, prec, tol=1e-8):
     x, info = P.solve(sw, chi, tol, prec)
     assert info.status == sw.SW_OK
     assert info.true_rel_resid <= tol
-    assert P.true_resid(chi, x) <= tol * 1.01
+    rr = P.true_resid(chi, x)
+    assert rr <= tol * 1.01
+    # the solver's own residual recomputation (FP64, or double-single in the
+    # mixed modes) agrees with the oracle's FP64 one
+    assert abs(info.true_rel_resid - rr) <= 1e-13 + 1e-3 * rr
     ref, _ = P.oracle(chi, 1e-12)
     assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-6
     return x, info
