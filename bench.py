@@ -57,6 +57,10 @@ ITERS_TABLE = {"sw": {0.02: 41.0, 0.05: 39.0, 0.1: 36.9, 0.2: 32.0},
 # changes after the capture.
 NCU_TRAFFIC = {"wilson.k2.f32": {"bytes": 947.0e6, "algorithmic": 943.7e6, "systems": 12}}
 
+# FP64 peak of a GB300 (nominal 1.25 TFLOP/s; not in the measured-peaks file):
+# denominator of the FP64-ALU-bound reliable-update matvecs.
+FP64_PEAK_TFLOPS = 1.25
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -80,6 +84,10 @@ def parse():
     ap.add_argument("--w-sources", type=int, default=12, help="Wilson spin-colour sources per mass (<= 12)")
     ap.add_argument("--dims", default="16x16x16x32", help="lattice L0xL1xL2xL3 (L3 = time)")
     ap.add_argument("--graphs", type=int, default=None, help="1/0: replay chunks as CUDA graphs (library default 1)")
+    ap.add_argument("--site-blocking", type=int, default=None, help="1/0: blocked site order of packed fields")
+    ap.add_argument("--group-fast", type=int, default=None, help="1/0: system groups fastest in the stencil grid")
+    ap.add_argument("--ops", choices=["both", "sw", "wilson"], default="both",
+                    help="operators of a step (the large-volume runs take one per lattice)")
     ap.add_argument("--sources", default="point",
                     help="'point': 3 colour (SW) / 12 spin-colour (W) point sources per mass; "
                          "'z2:N': N real Z2-noise sources per mass for both operators")
@@ -212,6 +220,10 @@ def run_ours(args):
         sw.sw_set_param(sw.SW_PARAM_CHUNK, args.chunk)
     if args.graphs is not None:
         sw.sw_set_param(sw.SW_PARAM_GRAPHS, args.graphs)
+    if args.site_blocking is not None:
+        sw.sw_set_param(sw.SW_PARAM_SITE_BLOCKING, args.site_blocking)
+    if args.group_fast is not None:
+        sw.sw_set_param(sw.SW_PARAM_GROUP_FAST, args.group_fast)
     if args.ns_sw is not None:
         sw.sw_set_param(sw.SW_PARAM_NS_SW, args.ns_sw)
     if args.ns_wilson is not None:
@@ -223,8 +235,12 @@ def run_ours(args):
     Uh, chi_sw_h, m_sw, chi_w_h, m_w = host_inputs(seeds, masses, args.w_sources, dims, args.sources)
     V = int(np.prod(dims))
 
+    if args.ops == "sw":
+        chi_w_h, m_w = chi_w_h[:0], []
+    if args.ops == "wilson":
+        chi_sw_h, m_sw = chi_sw_h[:0], []
     U = {s: torch.from_numpy(Uh[s]).to(dev) for s in seeds}
-    W = torch.empty((V, 8, 3, 3), dtype=torch.complex128, device=dev)
+    W = torch.empty((V if args.ops != "wilson" else 1, 8, 3, 3), dtype=torch.complex128, device=dev)
     chi_sw = torch.from_numpy(chi_sw_h).to(dev)
     chi_w = torch.from_numpy(chi_w_h).to(dev)
     x_sw = torch.empty_like(chi_sw)
@@ -233,13 +249,16 @@ def run_ours(args):
 
     def step(seed, Ud, csw, cw, xsw, xw, precision=None):
         pr = prec if precision is None else precision
-        sw.sw_hypercube_build(dims, Ud, W, stream=stream)
-        xsw.zero_()
-        rc1, inf_sw = sw.cgne_solve_batch(dims, sw.SW_OP_STAGGERED_WILSON, Ud, W, csw, xsw, m_sw, 1.0, TOL,
-                                          100000, pr, stream=stream)
-        xw.zero_()
-        rc2, inf_w = sw.cgne_solve_batch(dims, sw.SW_OP_WILSON, Ud, None, cw, xw, m_w, R_WILSON, TOL, 100000,
-                                         pr, stream=stream)
+        inf_sw, inf_w = [], []
+        if args.ops in ("both", "sw"):
+            sw.sw_hypercube_build(dims, Ud, W, stream=stream)
+            xsw.zero_()
+            rc1, inf_sw = sw.cgne_solve_batch(dims, sw.SW_OP_STAGGERED_WILSON, Ud, W, csw, xsw, m_sw, 1.0, TOL,
+                                              100000, pr, stream=stream)
+        if args.ops in ("both", "wilson"):
+            xw.zero_()
+            rc2, inf_w = sw.cgne_solve_batch(dims, sw.SW_OP_WILSON, Ud, None, cw, xw, m_w, R_WILSON, TOL, 100000,
+                                             pr, stream=stream)
         for inf in inf_sw + inf_w:
             if inf.status != sw.SW_OK or not (inf.true_rel_resid <= TOL):
                 raise RuntimeError(f"solve failed: {inf}")
@@ -336,9 +355,9 @@ def run_ours(args):
             by_mass["sw"].setdefault(m, []).append(i.iters)
         for m, i in zip(m_w, st[1]):
             by_mass["wilson"].setdefault(m, []).append(i.iters)
-    lat_sw = [st[0][0].seconds * 1e3 for st in infos]
-    lat_w = [st[1][0].seconds * 1e3 for st in infos]
-    lats = sorted([v for v in lat_sw for _ in m_sw] + [v for v in lat_w for _ in m_w])
+    lat_sw = [st[0][0].seconds * 1e3 for st in infos if st[0]]
+    lat_w = [st[1][0].seconds * 1e3 for st in infos if st[1]]
+    lats = sorted([v for v in lat_sw for _ in m_sw] + [v for v in lat_w for _ in m_w]) or [0.0]
 
     peak, peak_kind = measured_peaks()
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
@@ -352,10 +371,17 @@ def run_ours(args):
         roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                 "bytes_per_launch": bpl, "launch_ms": d["ms"] / d["launches"]}
-    kernels = {k: {"launches": v["launches"], "ms_per_launch": round(v["ms"] / v["launches"], 4),
-                   "GB/s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1),
-                   "frac_hbm": round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / peak, 4)}
-               for k, v in prof.items()}
+    kernels = {}
+    for k, v in prof.items():
+        e = {"launches": v["launches"], "ms_per_launch": round(v["ms"] / v["launches"], 4)}
+        if v.get("flops", 0) > 0:  # FP64-ALU-bound matvecs: TFLOP/s against the FP64 peak
+            tf = v["flops"] / (v["ms"] / 1e3) / 1e12
+            e.update({"TFLOP/s": round(tf, 3), "frac_fp64": round(tf / FP64_PEAK_TFLOPS, 4)})
+        else:
+            e.update({"GB/s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1),
+                      "frac_hbm": round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / peak, 4)})
+        kernels[k] = e
+    prof = {k: v for k, v in prof.items() if not v.get("flops", 0) > 0}  # the HBM roofline's candidates
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": K,
@@ -371,6 +397,8 @@ def run_ours(args):
                    "reliable_delta": sw.sw_get_param(sw.SW_PARAM_RELIABLE_DELTA),
                    "chunk": int(sw.sw_get_param(sw.SW_PARAM_CHUNK)),
                    "graphs": int(sw.sw_get_param(sw.SW_PARAM_GRAPHS)),
+                   "site_blocking": int(sw.sw_get_param(sw.SW_PARAM_SITE_BLOCKING)),
+                   "group_fast": int(sw.sw_get_param(sw.SW_PARAM_GROUP_FAST)),
                    "systems_per_thread": {"sw": int(sw.sw_get_param(sw.SW_PARAM_NS_SW)),
                                           "wilson": int(sw.sw_get_param(sw.SW_PARAM_NS_WILSON))},
                    "l2": "inputs larger than L2: a step touches ~10 GB and each step uses a new configuration",
@@ -380,13 +408,13 @@ def run_ours(args):
                        "p99": round(float(np.percentile(lats, 99)), 2),
                        "note": "time to solution of each solve's batch"},
         "operators": {
-            "sw": {"solves": len(m_sw), "iters_mean": float(np.mean(it_sw)),
-                   "batch_ms_mean": float(np.mean(lat_sw)),
+            "sw": {"solves": len(m_sw), "iters_mean": float(np.mean(it_sw)) if it_sw else None,
+                   "batch_ms_mean": float(np.mean(lat_sw)) if lat_sw else None,
                    "iters_by_mass": {str(m): float(np.mean(v)) for m, v in by_mass["sw"].items()}},
-            "wilson": {"solves": len(m_w), "iters_mean": float(np.mean(it_w)),
-                       "batch_ms_mean": float(np.mean(lat_w)),
+            "wilson": {"solves": len(m_w), "iters_mean": float(np.mean(it_w)) if it_w else None,
+                       "batch_ms_mean": float(np.mean(lat_w)) if lat_w else None,
                        "iters_by_mass": {str(m): float(np.mean(v)) for m, v in by_mass["wilson"].items()}},
-            "iters_ratio_w_over_sw": float(np.mean(it_w) / np.mean(it_sw)),
+            "iters_ratio_w_over_sw": float(np.mean(it_w) / np.mean(it_sw)) if it_sw and it_w else None,
             "paper_context": "Sec. 3: iteration ratio W/SW almost 2 on thermalised beta=6 fields "
                              "(not comparable: synthetic links)"},
     }

@@ -173,11 +173,16 @@ int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, const void*
  *   graph captured once per solve or server engine (one launch instead of
  *   3 per iteration); 0 launches the kernels one by one.  cgne_solve_noalloc
  *   never uses graphs.
+ * SW_PARAM_SITE_BLOCKING: 1 stores the packed FP32/FP16 fields in blocks of
+ *   up to 4x4x4x2 sites (each block contiguous), 0 (default) in lexicographic
+ *   order.
+ * SW_PARAM_GROUP_FAST: 1 makes the system groups the fastest grid dimension
+ *   of the stencil kernels, 0 (default) the tiles.
  * None of these changes what a solve converges to: convergence is always
  * decided on an FP64 residual.  Returns SW_ERR_ARG for an unknown key or a
  * value out of range. */
 enum { SW_PARAM_CHUNK = 0, SW_PARAM_RELIABLE_DELTA = 1, SW_PARAM_NS_SW = 2, SW_PARAM_NS_WILSON = 3,
-       SW_PARAM_GRAPHS = 4 };
+       SW_PARAM_GRAPHS = 4, SW_PARAM_SITE_BLOCKING = 5, SW_PARAM_GROUP_FAST = 6 };
 int sw_set_param(int key, double value);
 int sw_get_param(int key, double* value);
 
@@ -204,6 +209,12 @@ int sw_autotune(const sw_lattice* lat, int op, const void* U, const void* W, int
  * The stencil kernels of a sampled iteration count the systems they compute
  * on the device, so the byte count matches the work done.
  * Classes are named "<operator>.<kernel>.<precision>", e.g. "sw.k1.f32".
+ * The FP64 matvecs of the reliable updates and of the right-hand side are
+ * timed as class "<operator>.ru.f64" (the two launches of a residual
+ * recomputation) and "<operator>.rhs.f64": they are bound by the FP64 units,
+ * so they carry flops -- the paper's count per site and application (Eq. 4:
+ * 1743 staggered Wilson, 1392 Wilson) times sites, applications and the
+ * systems the launch computed -- and bytes 0.
  * Process-wide and thread-safe; disabled by default. */
 int sw_profile_enable(int on);
 /* Total kernel launches this library has issued in the process (always on). */
@@ -214,7 +225,7 @@ int sw_profile_count(void);
 /* Class i (0 <= i < count): name into name[name_len], totals into the other
  * HOST pointers (each may be NULL).  Returns SW_ERR_ARG for a bad index. */
 int sw_profile_entry(int i, char* name, int name_len, long long* launches, double* total_ms,
-                     double* total_bytes);
+                     double* total_bytes, double* total_flops);
 
 /* ---- Continuous-batching solve server -------------------------------------
  * Serving counterpart of the batched solve: gauge fields stay resident on the

@@ -19,6 +19,8 @@ SW_PARAM_RELIABLE_DELTA = 1
 SW_PARAM_NS_SW = 2
 SW_PARAM_NS_WILSON = 3
 SW_PARAM_GRAPHS = 4
+SW_PARAM_SITE_BLOCKING = 5
+SW_PARAM_GROUP_FAST = 6
 
 
 class Lattice(ctypes.Structure):
@@ -107,7 +109,7 @@ def lib():
         L.sw_profile_reset.argtypes = []
         L.sw_profile_count.argtypes = []
         L.sw_profile_entry.argtypes = [i, ctypes.c_char_p, i, ctypes.POINTER(ctypes.c_longlong),
-                                       ctypes.POINTER(d), ctypes.POINTER(d)]
+                                       ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]
         for f in ("sw_profile_enable", "sw_profile_reset", "sw_profile_count", "sw_profile_entry"):
             getattr(L, f).restype = i
         L.sw_status_string.argtypes = [i]
@@ -202,15 +204,15 @@ def sw_profile_reset():
 
 
 def sw_profile_read():
-    """{class: {"launches", "ms", "bytes"}} accumulated since the last reset."""
+    """{class: {"launches", "ms", "bytes", "flops"}} accumulated since the last reset."""
     out = {}
     L = lib()
     for i in range(L.sw_profile_count()):
         name = ctypes.create_string_buffer(64)
-        n, ms, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
-        _check(L.sw_profile_entry(i, name, 64, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)),
-               "sw_profile_entry")
-        out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "bytes": by.value}
+        n, ms, by, fl = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(L.sw_profile_entry(i, name, 64, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by),
+                                  ctypes.byref(fl)), "sw_profile_entry")
+        out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "bytes": by.value, "flops": fl.value}
     return out
 
 

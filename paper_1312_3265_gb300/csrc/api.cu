@@ -32,11 +32,12 @@ struct ProfStat {
   long long launches = 0;
   double ms = 0.0;
   double bytes = 0.0;
+  double flops = 0.0;
 };
 struct Pending {
   std::string cls;
   cudaEvent_t a, b;
-  double bytes;
+  double bytes, flops;
 };
 std::mutex g_prof_mu;
 std::atomic<long long> g_launches{0};
@@ -50,6 +51,8 @@ std::atomic<double> g_param_delta{0.001};
 std::atomic<int> g_param_ns_sw{2};
 std::atomic<int> g_param_ns_wilson{1};
 std::atomic<int> g_param_graphs{1};
+std::atomic<int> g_param_site_block{0};
+std::atomic<int> g_param_group_fast{0};
 thread_local std::vector<cudaEvent_t> t_used;
 }  // namespace
 
@@ -74,8 +77,8 @@ cudaEvent_t prof_event() {
   return e;
 }
 
-void prof_push(const char* cls, cudaEvent_t a, cudaEvent_t b, double bytes) {
-  t_staged.push_back(Pending{cls, a, b, bytes});
+void prof_push(const char* cls, cudaEvent_t a, cudaEvent_t b, double bytes, double flops) {
+  t_staged.push_back(Pending{cls, a, b, bytes, flops});
 }
 
 void prof_commit(bool keep) {
@@ -87,6 +90,8 @@ int param_chunk() { return g_param_chunk.load(); }
 double param_delta() { return g_param_delta.load(); }
 int param_ns(int nc) { return nc == 3 ? g_param_ns_sw.load() : g_param_ns_wilson.load(); }
 bool param_graphs() { return g_param_graphs.load() != 0; }
+bool param_site_blocking() { return g_param_site_block.load() != 0; }
+bool param_group_fast() { return g_param_group_fast.load() != 0; }
 
 void prof_flush() {
   std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -97,6 +102,7 @@ void prof_flush() {
       s.launches += 1;
       s.ms += ms;
       s.bytes += p.bytes;
+      s.flops += p.flops;
     } else {
       cudaGetLastError();
     }
@@ -203,8 +209,12 @@ int sw_set_param(int key, double value) {
       g_param_delta.store(value);
       return SW_OK;
     case SW_PARAM_GRAPHS:
+    case SW_PARAM_SITE_BLOCKING:
+    case SW_PARAM_GROUP_FAST:
       if (!(value == 0 || value == 1)) return SW_ERR_ARG;
-      g_param_graphs.store((int)value);
+      (key == SW_PARAM_GRAPHS ? g_param_graphs
+                              : key == SW_PARAM_SITE_BLOCKING ? g_param_site_block : g_param_group_fast)
+          .store((int)value);
       return SW_OK;
     case SW_PARAM_NS_SW:
     case SW_PARAM_NS_WILSON:
@@ -224,6 +234,8 @@ int sw_get_param(int key, double* value) {
     case SW_PARAM_NS_SW: *value = g_param_ns_sw.load(); return SW_OK;
     case SW_PARAM_NS_WILSON: *value = g_param_ns_wilson.load(); return SW_OK;
     case SW_PARAM_GRAPHS: *value = g_param_graphs.load(); return SW_OK;
+    case SW_PARAM_SITE_BLOCKING: *value = g_param_site_block.load(); return SW_OK;
+    case SW_PARAM_GROUP_FAST: *value = g_param_group_fast.load(); return SW_OK;
     default: return SW_ERR_ARG;
   }
 }
@@ -248,7 +260,7 @@ int sw_profile_count(void) {
 }
 
 int sw_profile_entry(int i, char* name, int name_len, long long* launches, double* total_ms,
-                     double* total_bytes) {
+                     double* total_bytes, double* total_flops) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (i < 0 || i >= (int)g_prof.size()) return SW_ERR_ARG;
   auto it = g_prof.begin();
@@ -260,6 +272,7 @@ int sw_profile_entry(int i, char* name, int name_len, long long* launches, doubl
   if (launches) *launches = it->second.launches;
   if (total_ms) *total_ms = it->second.ms;
   if (total_bytes) *total_bytes = it->second.bytes;
+  if (total_flops) *total_flops = it->second.flops;
   return SW_OK;
 }
 

@@ -82,13 +82,14 @@ __device__ __forceinline__ double finalize_sum(const RedBuf& rb, int sys, int nt
   return block_sum(v, smem);
 }
 
-// Returns true in every thread of the block that is the last to finish for `sys`.
-__device__ __forceinline__ bool block_done(const RedBuf& rb, int sys, int* flag_smem) {
+// Returns true in every thread of the block that is the last of the
+// `nblocks` blocks of system (or group) `sys` to finish.
+__device__ __forceinline__ bool block_done(const RedBuf& rb, int sys, int* flag_smem, unsigned nblocks) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned t = atomicAdd(rb.tickets + sys, 1u);
-    *flag_smem = (t == gridDim.x - 1);
+    *flag_smem = (t == nblocks - 1);
     if (*flag_smem) rb.tickets[sys] = 0u;
   }
   __syncthreads();
@@ -106,6 +107,7 @@ struct SWOp {
   static constexpr int kMats = 12;  // 4 links + 8 stored hypercube transports per site
   static constexpr const char* kName = "sw";
   static constexpr int kGaugeBytes = G::kBytes + Wt::kBytes;  // stored links + transports per site
+  static constexpr double kFlops = 1743.0;  // per site and application (Eq. 4)
   static constexpr const char* kPrec = G::kPrec;
   // default systems per thread in the CG kernels (FP32 shares each matrix load
   // over several systems; FP64 is ALU-bound and gains nothing from it)
@@ -120,8 +122,8 @@ struct SWOp {
     for (int i = 0; i < 3; ++i) v.c[i] = o.c[i];
     return v;
   }
-  template <int NS>
-  __device__ __forceinline__ void apply_multi(const Geom& g, int n, const Vec& in, size_t stride, unsigned act,
+  template <int NS, typename GG>
+  __device__ __forceinline__ void apply_multi(const GG& g, int n, const Vec& in, size_t stride, unsigned act,
                                               const T* m, T r, bool dag, CV<T, 3>* out) const {
     V3<T> o[NS];
     sw_site_multi<T, NS>(g, n, U, W, in, stride, act, m, r, dag, o);
@@ -139,6 +141,7 @@ struct WOp {
   static constexpr const char* kName = "wilson";
   static constexpr int kGaugeBytes = G::kBytes;
   static constexpr const char* kPrec = G::kPrec;
+  static constexpr double kFlops = 1392.0;  // per site and application (Eq. 4)
   static constexpr int kNS = 1;
   using Vec = VA<12>;
   G U;
@@ -151,8 +154,8 @@ struct WOp {
       for (int i = 0; i < 3; ++i) v.c[3 * s + i] = o.s[s].c[i];
     return v;
   }
-  template <int NS>
-  __device__ __forceinline__ void apply_multi(const Geom& g, int n, const Vec& in, size_t stride, unsigned act,
+  template <int NS, typename GG>
+  __device__ __forceinline__ void apply_multi(const GG& g, int n, const Vec& in, size_t stride, unsigned act,
                                               const T* m, T r, bool dag, CV<T, 12>* out) const {
     Sp<T> o[NS];
     wilson_site_multi<T, R1, NS>(g, n, U, in, stride, act, m, r, dag, o);
@@ -211,10 +214,12 @@ struct BatchParams {
 template <typename T, typename Op>
 __global__ void __launch_bounds__(kTile) apply_kernel(Geom g, Op op, typename Op::Vec in, typename Op::Vec out,
                                                     double mass0, size_t sstride, double r, int dagger,
-                                                    const SysState* S, int only_status) {
-  // mass: mass0, or each system's own mass when the launch is filtered by status
+                                                    const SysState* S, int only_status, int* nact = nullptr) {
+  // mass: mass0, or each system's own mass when the launch is filtered by status;
+  // nact (instrumentation, may be null) counts the systems computed
   const int sys = blockIdx.y;
   if (S && S[sys].status != only_status) return;
+  if (nact && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nact, 1);
   in = sys_view(in, sys, sstride);
   out = sys_view(out, sys, sstride);
   const T m = (T)(S ? S[sys].mass : mass0);
@@ -277,30 +282,36 @@ template <typename T, typename Op> constexpr int stencil_min_blocks() {
   return sizeof(T) == 4 ? (Op::NC == 3 ? 8 : 6) : 1;
 }
 
-template <typename T, typename Op, int NS>
-__global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k1(Geom g, Op op, typename Op::Vec p, typename Op::Vec t,
-                                               BatchParams bp, int nsys, SysState* S, RedBuf rb, int* nact) {
+template <typename T, typename Op, int NS, typename GG>
+__global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k1(GG g, Op op, typename Op::Vec p, typename Op::Vec t,
+                                               BatchParams bp, int nsys, SysState* S, RedBuf rb, int* nact,
+                                               int gfast) {
   __shared__ double sm[NS * 32];
   __shared__ int last;
-  const int sys0 = blockIdx.y * NS;
+  // gfast: blockIdx.x = group of NS systems (the groups working on the same
+  // tiles are launched side by side), blockIdx.y strides over the tiles;
+  // otherwise the other way round
+  const int grp = gfast ? blockIdx.x : blockIdx.y, bt = gfast ? blockIdx.y : blockIdx.x;
+  const int nbt = gfast ? gridDim.y : gridDim.x;
+  const int sys0 = grp * NS;
   T m[NS];
   const unsigned act = running_mask<T, NS>(S, sys0, nsys, m);
   if (!act) return;
-  if (nact && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nact, __popc(act));
+  if (nact && bt == 0 && threadIdx.x == 0) atomicAdd(nact, __popc(act));
   p = sys_view(p, sys0, bp.vstride);
   t = sys_view(t, sys0, bp.vstride);
   const int ntiles = (g.V + kTile - 1) / kTile;
   // grid-stride over tiles: the blocks resident at a time cover neighbouring
   // tiles, which keeps their neighbour reads together in L2 (measured faster
   // on GB300 than giving each block one contiguous range of tiles)
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int tile = bt; tile < ntiles; tile += nbt) {
     const int n = tile * kTile + threadIdx.x;
     double acc[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) acc[s] = 0.0;
     if (n < g.V) {
       CV<T, Op::NC> v[NS];
-      op.template apply_multi<NS>(g, n, p, bp.vstride, act, m, (T)bp.r, false, v);
+      op.template apply_multi<NS, GG>(g, n, p, bp.vstride, act, m, (T)bp.r, false, v);
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         if (!(act & (1u << s))) continue;
@@ -316,7 +327,7 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k1(Geom
     for (int s = 0; s < NS; ++s)
       if (act & (1u << s)) put_tile(rb, sys0 + s, tile, acc[s]);
   }
-  if (block_done(rb, blockIdx.y, &last)) {
+  if (block_done(rb, grp, &last, nbt)) {
 #pragma unroll 1
     for (int s = 0; s < NS; ++s) {
       if (!(act & (1u << s))) continue;
@@ -336,17 +347,22 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k1(Geom
 }
 
 // ---------------------------------------------------------------- k2: Ap = D^+ t; x, r update; |r|^2
-template <typename T, typename Op, int NS, typename RVec>
-__global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(Geom g, Op op, typename Op::Vec t, typename Op::Vec p, RVec r,
+template <typename T, typename Op, int NS, typename RVec, typename GG>
+__global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(GG g, Op op, typename Op::Vec t, typename Op::Vec p, RVec r,
                                                RVec x, BatchParams bp, int nsys, SysState* S, RedBuf rb,
-                                               int* nact) {
+                                               int* nact, int gfast) {
   __shared__ double sm[NS * 32];
   __shared__ int last;
-  const int sys0 = blockIdx.y * NS;
+  // gfast: blockIdx.x = group of NS systems (the groups working on the same
+  // tiles are launched side by side), blockIdx.y strides over the tiles;
+  // otherwise the other way round
+  const int grp = gfast ? blockIdx.x : blockIdx.y, bt = gfast ? blockIdx.y : blockIdx.x;
+  const int nbt = gfast ? gridDim.y : gridDim.x;
+  const int sys0 = grp * NS;
   T m[NS];
   const unsigned act = running_mask<T, NS>(S, sys0, nsys, m);
   if (!act) return;
-  if (nact && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nact, __popc(act));
+  if (nact && bt == 0 && threadIdx.x == 0) atomicAdd(nact, __popc(act));
   T alpha[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) alpha[s] = (act & (1u << s)) ? (T)S[sys0 + s].alpha : T(0);
@@ -358,14 +374,14 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(Geom
   // grid-stride over tiles: the blocks resident at a time cover neighbouring
   // tiles, which keeps their neighbour reads together in L2 (measured faster
   // on GB300 than giving each block one contiguous range of tiles)
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int tile = bt; tile < ntiles; tile += nbt) {
     const int n = tile * kTile + threadIdx.x;
     double acc[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) acc[s] = 0.0;
     if (n < g.V) {
       CV<T, Op::NC> ap[NS];
-      op.template apply_multi<NS>(g, n, t, bp.vstride, act, m, (T)bp.r, true, ap);
+      op.template apply_multi<NS, GG>(g, n, t, bp.vstride, act, m, (T)bp.r, true, ap);
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         if (!(act & (1u << s))) continue;
@@ -387,7 +403,7 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(Geom
     for (int s = 0; s < NS; ++s)
       if (act & (1u << s)) put_tile(rb, sys0 + s, tile, acc[s]);
   }
-  if (block_done(rb, blockIdx.y, &last)) {
+  if (block_done(rb, grp, &last, nbt)) {
 #pragma unroll 1
     for (int s = 0; s < NS; ++s) {
       if (!(act & (1u << s))) continue;
@@ -431,11 +447,13 @@ __global__ void __launch_bounds__(256) cg_k3(int V, RVec r, PVec p, size_t rstri
 // r64 = b - (D+m)^+ t64, |r64|^2, then the convergence decision.
 template <typename Op>
 __global__ void __launch_bounds__(kTile) residual64(Geom g, Op op, typename Op::Vec t, typename Op::Vec b,
-                                                  typename Op::Vec r, BatchParams bp, SysState* S, RedBuf rb) {
+                                                  typename Op::Vec r, BatchParams bp, SysState* S, RedBuf rb,
+                                                  int* nact = nullptr) {
   __shared__ double sm[32];
   __shared__ int last;
   const int sys = blockIdx.y;
   if (S[sys].status != ST_NEED_RU) return;
+  if (nact && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nact, 1);
   t = sys_view(t, sys, bp.sstride64);
   b = sys_view(b, sys, bp.sstride64);
   r = sys_view(r, sys, bp.sstride64);
@@ -455,7 +473,7 @@ __global__ void __launch_bounds__(kTile) residual64(Geom g, Op op, typename Op::
     }
     put_tile(rb, sys, tile, block_sum(acc, sm));
   }
-  if (block_done(rb, sys, &last)) {
+  if (block_done(rb, sys, &last, gridDim.x)) {
     const double rr = finalize_sum(rb, sys, ntiles, sm);
     if (threadIdx.x == 0) {
       SysState& s = S[sys];

@@ -128,6 +128,104 @@ __device__ __forceinline__ bool bc_flip(const Geom& g, const int x[4], int s) {
   return g.apbc && ((s > 0) ? (x[3] == g.L[3] - 1) : (x[3] == 0));
 }
 
+// Blocked site order of the inner-precision (FP32/FP16) planar storage: the
+// lattice is cut into blocks of B0 x B1 x B2 x B3 sites (powers of two up to
+// 4, 4, 4, 2), stored one after the other in lexicographic block order, the
+// sites of a block contiguous in lexicographic order inside it.  A 128-site
+// tile then covers a compact 4-D region, so most of a site's neighbours lie
+// in the tile its block has just loaded.  The index is a sum of one term per
+// direction, so a hop changes one term: n = sum_mu (b_mu bs_mu + l_mu ls_mu).
+struct GeomBlk {
+  int L[4];
+  int lb[4];     // log2 B_mu
+  int NB[4];     // blocks per direction
+  int ls[4];     // stride of the in-block coordinate
+  int bs[4];     // stride of the block coordinate (in sites)
+  int V;
+  int apbc;
+};
+
+// blocking = false gives B = 1 everywhere, i.e. the lexicographic order.
+__host__ __device__ inline GeomBlk make_blocked(const Geom& g, bool blocking = true) {
+  GeomBlk b;
+  const int cap[4] = {blocking ? 4 : 1, blocking ? 4 : 1, blocking ? 4 : 1, blocking ? 2 : 1};
+  int bsz = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    int B = 1, lg = 0;
+    while (B * 2 <= cap[mu] && g.L[mu] % (B * 2) == 0) {
+      B *= 2;
+      ++lg;
+    }
+    b.L[mu] = g.L[mu];
+    b.lb[mu] = lg;
+    b.NB[mu] = g.L[mu] >> lg;
+    b.ls[mu] = bsz;
+    bsz *= B;
+  }
+  int st = bsz;  // sites per block
+  for (int mu = 0; mu < 4; ++mu) {
+    b.bs[mu] = st;
+    st *= b.NB[mu];
+  }
+  b.V = g.V;
+  b.apbc = g.apbc;
+  return b;
+}
+
+// blocked index of the site with coordinates x
+__host__ __device__ inline int blk_index(const GeomBlk& g, const int x[4]) {
+  int n = 0;
+  for (int mu = 0; mu < 4; ++mu) {
+    const int B = 1 << g.lb[mu];
+    n += (x[mu] >> g.lb[mu]) * g.bs[mu] + (x[mu] & (B - 1)) * g.ls[mu];
+  }
+  return n;
+}
+
+__host__ __device__ inline void coords(const GeomBlk& g, int n, int x[4]) {
+  // block index then in-block index, both lexicographic
+  const int bsite = 1 << (g.lb[0] + g.lb[1] + g.lb[2] + g.lb[3]);
+  int blk = n >> (g.lb[0] + g.lb[1] + g.lb[2] + g.lb[3]);
+  int loc = n & (bsite - 1);
+  for (int mu = 0; mu < 4; ++mu) {
+    const int b = (mu < 3) ? blk % g.NB[mu] : blk;
+    blk = (mu < 3) ? blk / g.NB[mu] : 0;
+    const int B = 1 << g.lb[mu];
+    const int l = loc & (B - 1);
+    loc >>= g.lb[mu];
+    x[mu] = (b << g.lb[mu]) + l;
+  }
+}
+
+__host__ __device__ inline int hop(const GeomBlk& g, int n, const int x[4], int mu, int s) {
+  const int B = 1 << g.lb[mu];
+  const int l = x[mu] & (B - 1);
+  if (s > 0) {
+    if (l < B - 1) return n + g.ls[mu];
+    n -= (B - 1) * g.ls[mu];
+    return (x[mu] == g.L[mu] - 1) ? n - (g.NB[mu] - 1) * g.bs[mu] : n + g.bs[mu];
+  }
+  if (l > 0) return n - g.ls[mu];
+  n += (B - 1) * g.ls[mu];
+  return (x[mu] == 0) ? n + (g.NB[mu] - 1) * g.bs[mu] : n - g.bs[mu];
+}
+
+__device__ __forceinline__ bool bc_flip(const GeomBlk& g, const int x[4], int s) {
+  return g.apbc && ((s > 0) ? (x[3] == g.L[3] - 1) : (x[3] == 0));
+}
+
+// lexicographic site index -> blocked index (host and device)
+__host__ __device__ inline int lex_to_blk(const GeomBlk& g, int n) {
+  int x[4];
+  x[0] = n % g.L[0];
+  int q = n / g.L[0];
+  x[1] = q % g.L[1];
+  q /= g.L[1];
+  x[2] = q % g.L[2];
+  x[3] = q / g.L[2];
+  return blk_index(g, x);
+}
+
 // ------------------------------------------------------------------ accessors
 // Canonical FP64 (the C ABI layout)
 struct GaugeC64 {

@@ -33,6 +33,8 @@ namespace swc {
 int param_chunk();
 double param_delta();
 int param_ns(int nc);  // systems per thread of the FP32 stencils (1, 2 or 4) for NC components
+bool param_site_blocking();  // blocked site order for the packed FP32/FP16 storage
+bool param_group_fast();     // system groups as the fastest grid dimension of the stencils
 bool param_graphs();   // replay chunks of iterations as captured CUDA graphs
 
 inline int grid_for(const void* kernel, int block, int V, int nsys, int cap) {
@@ -258,6 +260,9 @@ class Engine {
   using VF = typename OpF::Vec;  // stencil vectors p, t
   using TF = typename std::conditional<MIXED, float, double>::type;
   using VR = typename std::conditional<MIXED, VecP32<NC>, V64>::type;  // r and x of the inner iteration
+  // geometry of the inner iteration: blocked site order for the packed
+  // FP32/FP16 storage, the canonical order for FP64
+  using GK = typename std::conditional<MIXED, GeomBlk, Geom>::type;
 
   // chi, x: cap slots in the canonical layout (x: initial guess in, solution
   // out).  hs_read / hs_stage: host arrays [cap] (pinned for overlap).
@@ -270,6 +275,10 @@ class Engine {
       : g_(g), opd_(opd), opf_(opf), r_(r), cap_(cap), chi_(chi), x_(x), ws_(ws), hr_(hs_read), hst_(hs_stage),
         st_(st), ev_(ev), n_((size_t)g.V * NC), use_graphs_(use_graphs && param_graphs()) {
     pstride_ = (g.V + kTile - 1) / kTile;
+    gb_ = make_blocked(g, param_site_blocking());
+    if constexpr (MIXED) gk_ = gb_;
+    else gk_ = g;
+    gfast_ = param_group_fast() ? 1 : 0;
     rb_ = RedBuf{ws.partials, ws.tickets, pstride_, ws.hist};
     vunits_ = VF::sys_units(g.V);
     bp_ = BatchParams{r, n_, n_, vunits_};
@@ -305,11 +314,28 @@ class Engine {
     delta_ = param_delta();
   }
 
+  // FP64 matvec launches (right-hand side: 1 application; residual: 2) are
+  // timed with events and count the systems they compute.
+  struct FpSample {
+    cudaEvent_t e0, e1;
+    int* cnt;
+    int apps;
+  };
+  FpSample* fp_sample(int apps) {
+    if (!prof_enabled() || fsamples_.size() >= (size_t)kProfSlots / 2) return nullptr;
+    FpSample f{prof_event(), prof_event(), ws_.pcount + 2 * kProfSlots - 1 - fsamples_.size(), apps};
+    cudaEventRecord(f.e0, st_);
+    fsamples_.push_back(f);
+    return &fsamples_.back();
+  }
+
   // Turn the sampled launches into profiler records (after the stream is idle).
   void flush_profile() {
+    flush_fp_samples();
     if (samples_.empty()) return;
     std::vector<int> cnt(2 * samples_.size());
-    if (cudaMemcpy(cnt.data(), ws_.pcount, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (cnt.empty() ||
+        cudaMemcpy(cnt.data(), ws_.pcount, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
       cudaGetLastError();
       return;
     }
@@ -326,7 +352,7 @@ class Engine {
     }
     prof_commit(true);
     samples_.clear();
-    cudaMemset(ws_.pcount, 0, sizeof(int) * 2 * kProfSlots);
+    cudaMemset(ws_.pcount, 0, sizeof(int) * kProfSlots);
   }
 
   ~Engine() {
@@ -367,8 +393,10 @@ class Engine {
       using PU = typename VF::unit;
       admit_clear<PU><<<dim3(gV_, cap_), 256, 0, st_>>>(vunits_, static_cast<PU*>(ws_.p_lo), vunits_,
                                                          MIXED ? ws_.x32 : nullptr, MIXED ? n_ : 0, S);
+      FpSample* fs = fp_sample(1);
       apply_kernel<double, OpD><<<dim3(gA_, cap_), kTile, 0, st_>>>(g_, opd_, V64{chi_}, V64{ws_.b64}, 0.0, n_,
-                                                                    r_, 1, S, ST_ADMIT);
+                                                                    r_, 1, S, ST_ADMIT, fs ? fs->cnt : nullptr);
+      if (fs) cudaEventRecord(fs->e1, st_);
       norm_b<NC><<<dim3(gN_, cap_), kTile, 0, st_>>>(g_.V, ws_.b64, x_, n_, S, rb_);
       admit_vectors<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, ws_.b64, n_, S);
       admit_states<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S);
@@ -382,7 +410,7 @@ class Engine {
       // every 4th chunk is timed when profiling, on its second iteration: by
       // then the queue is full, so the events time the kernels rather than the
       // host's launch latency
-      const bool prof = prof_enabled() && chunk_ > 1 && samples_.size() < (size_t)kProfSlots &&
+      const bool prof = prof_enabled() && chunk_ > 1 && samples_.size() < (size_t)kProfSlots / 2 &&
                         (chunks_ % 4 == 0);
       ++chunks_;
       if (!prof && use_graphs_ && chunks_ > 1) {
@@ -446,12 +474,14 @@ class Engine {
 
   void reliable_update() {
     SysState* S = ws_.S;
-    if constexpr (MIXED) accum_x<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, x_, ws_.x32, n_, n_, S);
+    if constexpr (MIXED) accum_x<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(gb_, x_, ws_.x32, n_, n_, S);
+    FpSample* fs = fp_sample(2);
     apply_kernel<double, OpD><<<dim3(gA_, cap_), kTile, 0, st_>>>(g_, opd_, V64{x_}, V64{ws_.t64}, 0.0, n_, r_, 0,
-                                                                  S, ST_NEED_RU);
+                                                                  S, ST_NEED_RU, fs ? fs->cnt : nullptr);
     residual64<OpD><<<dim3(gR_, cap_), kTile, 0, st_>>>(g_, opd_, V64{ws_.t64}, V64{ws_.b64}, V64{ws_.r64}, bp_, S,
                                                         rb_);
-    if constexpr (MIXED) demote_r<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, ws_.r64, ws_.r32, n_, n_, S);
+    if (fs) cudaEventRecord(fs->e1, st_);
+    if constexpr (MIXED) demote_r<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(gb_, ws_.r64, ws_.r32, n_, n_, S);
     cg_k3<TF, VR, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, vunits_, S, ST_JUST_UPDATED);
     commit_status<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S);
     note_launches(MIXED ? 6 : 4);
@@ -483,26 +513,47 @@ class Engine {
     }
   }
 
+  void flush_fp_samples() {
+    if (fsamples_.empty()) return;
+    std::vector<int> cnt(2 * kProfSlots);
+    if (cudaMemcpy(cnt.data(), ws_.pcount, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    static const std::string cr = std::string(OpD::kName) + ".ru.f64";
+    static const std::string cb = std::string(OpD::kName) + ".rhs.f64";
+    for (size_t k = 0; k < fsamples_.size(); ++k) {
+      const FpSample& f = fsamples_[k];
+      const int systems = cnt[2 * kProfSlots - 1 - k];
+      prof_push(f.apps == 2 ? cr.c_str() : cb.c_str(), f.e0, f.e1, 0.0,
+                OpD::kFlops * g_.V * f.apps * systems);
+    }
+    prof_commit(true);
+    fsamples_.clear();
+    cudaMemset(ws_.pcount + kProfSlots, 0, sizeof(int) * kProfSlots);
+  }
+
   const void* k1_ptr() const {
     switch (ns_) {
-      case 2: return (const void*)cg_k1<TF, OpF, 2>;
-      case 4: return (const void*)cg_k1<TF, OpF, 4>;
-      default: return (const void*)cg_k1<TF, OpF, 1>;
+      case 2: return (const void*)cg_k1<TF, OpF, 2, GK>;
+      case 4: return (const void*)cg_k1<TF, OpF, 4, GK>;
+      default: return (const void*)cg_k1<TF, OpF, 1, GK>;
     }
   }
   const void* k2_ptr() const {
     switch (ns_) {
-      case 2: return (const void*)cg_k2<TF, OpF, 2, VR>;
-      case 4: return (const void*)cg_k2<TF, OpF, 4, VR>;
-      default: return (const void*)cg_k2<TF, OpF, 1, VR>;
+      case 2: return (const void*)cg_k2<TF, OpF, 2, VR, GK>;
+      case 4: return (const void*)cg_k2<TF, OpF, 4, VR, GK>;
+      default: return (const void*)cg_k2<TF, OpF, 1, VR, GK>;
     }
   }
   template <int NS> void launch_k12(int* c) {
     SysState* S = ws_.S;
-    cg_k1<TF, OpF, NS><<<dim3(g1_, ngrp_), kTile, 0, st_>>>(g_, opf_, fp_, ft_, bp_, cap_, S, rb_, c);
+    const dim3 grid1 = gfast_ ? dim3(ngrp_, g1_) : dim3(g1_, ngrp_), grid2 = gfast_ ? dim3(ngrp_, g2_) : dim3(g2_, ngrp_);
+    cg_k1<TF, OpF, NS, GK><<<grid1, kTile, 0, st_>>>(gk_, opf_, fp_, ft_, bp_, cap_, S, rb_, c, gfast_);
     if (c) cudaEventRecord(samples_.back().e1, st_);
-    cg_k2<TF, OpF, NS, VR><<<dim3(g2_, ngrp_), kTile, 0, st_>>>(g_, opf_, ft_, fp_, fr_, fx_, bp_, cap_, S, rb_,
-                                                                 c ? c + 1 : nullptr);
+    cg_k2<TF, OpF, NS, VR, GK><<<grid2, kTile, 0, st_>>>(gk_, opf_, ft_, fp_, fr_, fx_, bp_, cap_, S, rb_,
+                                                         c ? c + 1 : nullptr, gfast_);
   }
 
   // One CG iteration (k1, k2, k3).  A sampled iteration is bracketed by
@@ -532,6 +583,8 @@ class Engine {
     cudaEvent_t e0, e1, e2;
   };
   Geom g_;
+  GK gk_;
+  GeomBlk gb_;
   OpD opd_;
   OpF opf_;
   double r_;
@@ -553,8 +606,9 @@ class Engine {
   int chunk_ = 16;
   double delta_ = 0.1;
   bool need_ru_ = false;
-  int nrun_ = 0, ns_ = 1;
+  int nrun_ = 0, ns_ = 1, gfast_ = 0;
   std::vector<Sample> samples_;
+  std::vector<FpSample> fsamples_;
   long long rounds_ = 0, chunks_ = 0;
   bool use_graphs_ = true, graph_failed_ = false;
   cudaGraphExec_t gexec_ = nullptr;

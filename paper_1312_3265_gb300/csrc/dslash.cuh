@@ -29,7 +29,8 @@ template <typename T> __device__ __forceinline__ void neg3(V3<T>& v) {
 }
 
 // Hypercube corner of n displaced by s = (s0, s1, s2, s3), each +-1.
-__device__ __forceinline__ int corner(const Geom& g, int n, const int x[4], int s0, int s1, int s2, int s3) {
+template <typename GG>
+__device__ __forceinline__ int corner(const GG& g, int n, const int x[4], int s0, int s1, int s2, int s3) {
   n = hop(g, n, x, 0, s0);
   n = hop(g, n, x, 1, s1);
   n = hop(g, n, x, 2, s2);
@@ -234,8 +235,8 @@ template <typename T> __device__ __forceinline__ void axpy3(V3<T>& acc, T a, con
   for (int i = 0; i < 3; ++i) acc.c[i] = acc.c[i] + a * v.c[i];
 }
 
-template <typename T, int NS, typename G, typename Wt, typename In>
-__device__ __forceinline__ void sw_site_multi(const Geom& g, int n, const G& U, const Wt& W, const In& in,
+template <typename T, int NS, typename G, typename Wt, typename In, typename GG>
+__device__ __forceinline__ void sw_site_multi(const GG& g, int n, const G& U, const Wt& W, const In& in,
                                               size_t stride, unsigned act, const T* mass, T r, bool dagger,
                                               V3<T>* out) {
   int x[4];
@@ -289,8 +290,8 @@ __device__ __forceinline__ void sw_site_multi(const Geom& g, int n, const G& U, 
     }
 }
 
-template <typename T, bool R1, int NS, typename G, typename In>
-__device__ __forceinline__ void wilson_site_multi(const Geom& g, int n, const G& U, const In& in, size_t stride,
+template <typename T, bool R1, int NS, typename G, typename In, typename GG>
+__device__ __forceinline__ void wilson_site_multi(const GG& g, int n, const G& U, const In& in, size_t stride,
                                                   unsigned act, const T* mass, T r, bool dagger, Sp<T>* out) {
   int x[4];
   coords(g, n, x);

@@ -50,7 +50,7 @@ int sm_count();
 // algorithmic bytes those launches moved.
 bool prof_enabled();
 cudaEvent_t prof_event();
-void prof_push(const char* cls, cudaEvent_t a, cudaEvent_t b, double bytes);
+void prof_push(const char* cls, cudaEvent_t a, cudaEvent_t b, double bytes, double flops = 0.0);
 void prof_flush();
 // Keep (or drop) the samples pushed since the last commit.
 void prof_commit(bool keep);

@@ -4,35 +4,40 @@
 
 namespace swc {
 
-// canonical FP64 [V][nobj][9] -> planar FP32 [nobj*9][V]
-static __global__ void pack_mats_p32(int V, int nobj, const double2* __restrict__ src, float2* __restrict__ dst) {
+// canonical FP64 [V][nobj][9] -> planar FP32 [nobj*9][V], blocked site order
+static __global__ void pack_mats_p32(GeomBlk gb, int nobj, const double2* __restrict__ src,
+                                     float2* __restrict__ dst) {
+  const int V = gb.V;
   const size_t total = (size_t)V * nobj * 9;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const size_t n = i / ((size_t)nobj * 9);
     const size_t c = i - n * nobj * 9;
     const double2 v = src[i];
-    dst[c * V + n] = make_float2((float)v.x, (float)v.y);
+    dst[c * V + lex_to_blk(gb, (int)n)] = make_float2((float)v.x, (float)v.y);
   }
 }
 
-// canonical FP64 links [V][4][9] -> FP16 12-real planes [4*6][V] (rows 0, 1)
-static __global__ void pack_links_h12(int V, const double2* __restrict__ src, __half2* __restrict__ dst) {
+// canonical FP64 links [V][4][9] -> FP16 12-real planes [4*6][V] (rows 0, 1), blocked order
+static __global__ void pack_links_h12(GeomBlk gb, const double2* __restrict__ src, __half2* __restrict__ dst) {
+  const int V = gb.V;
   const size_t total = (size_t)V * 4 * 6;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const size_t n = i / 24, r = i - n * 24, mu = r / 6, c = r - mu * 6;
     const double2 v = src[(n * 4 + mu) * 9 + c];
-    dst[(mu * 6 + c) * V + n] = __floats2half2_rn((float)v.x, (float)v.y);
+    dst[(mu * 6 + c) * V + lex_to_blk(gb, (int)n)] = __floats2half2_rn((float)v.x, (float)v.y);
   }
 }
 
-// canonical FP64 [V][nobj][9] -> FP16 planes [nobj*9][V]
-static __global__ void pack_mats_h(int V, int nobj, const double2* __restrict__ src, __half2* __restrict__ dst) {
+// canonical FP64 [V][nobj][9] -> FP16 planes [nobj*9][V], blocked order
+static __global__ void pack_mats_h(GeomBlk gb, int nobj, const double2* __restrict__ src,
+                                   __half2* __restrict__ dst) {
+  const int V = gb.V;
   const size_t total = (size_t)V * nobj * 9;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const size_t n = i / ((size_t)nobj * 9);
     const size_t c = i - n * nobj * 9;
     const double2 v = src[i];
-    dst[c * V + n] = __floats2half2_rn((float)v.x, (float)v.y);
+    dst[c * V + lex_to_blk(gb, (int)n)] = __floats2half2_rn((float)v.x, (float)v.y);
   }
 }
 
@@ -72,38 +77,42 @@ static __global__ void su3_deviation(int V, const double2* __restrict__ U, unsig
   atomicMax(dev, __float_as_uint(worst));
 }
 
-// x64 (canonical) += x32 (planar); x32 = 0   -- systems with status NEED_RU
+// x64 (canonical) += x32 (planar, blocked order); x32 = 0   -- systems with status NEED_RU
 template <int NC>
-__global__ void accum_x(int V, double2* x64, float2* x32, size_t s64, size_t s32, const SysState* S) {
+__global__ void accum_x(GeomBlk gb, double2* x64, float2* x32, size_t s64, size_t s32, const SysState* S) {
   const int sys = blockIdx.y;
   if (S[sys].status != ST_NEED_RU) return;
+  const int V = gb.V;
   x64 += sys * s64;
   x32 += sys * s32;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < V; n += gridDim.x * blockDim.x) {
+    const int nb = lex_to_blk(gb, n);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      const float2 a = x32[(size_t)c * V + n];
+      const float2 a = x32[(size_t)c * V + nb];
       double2 b = x64[(size_t)n * NC + c];
       b.x += (double)a.x;
       b.y += (double)a.y;
       x64[(size_t)n * NC + c] = b;
-      x32[(size_t)c * V + n] = make_float2(0.f, 0.f);
+      x32[(size_t)c * V + nb] = make_float2(0.f, 0.f);
     }
   }
 }
 
-// r32 (planar) = (float) r64 (canonical)   -- systems with status JUST_UPDATED
+// r32 (planar, blocked order) = (float) r64 (canonical)   -- systems with status JUST_UPDATED
 template <int NC>
-__global__ void demote_r(int V, const double2* r64, float2* r32, size_t s64, size_t s32, const SysState* S) {
+__global__ void demote_r(GeomBlk gb, const double2* r64, float2* r32, size_t s64, size_t s32, const SysState* S) {
   const int sys = blockIdx.y;
   if (S[sys].status != ST_JUST_UPDATED) return;
+  const int V = gb.V;
   r64 += sys * s64;
   r32 += sys * s32;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < V; n += gridDim.x * blockDim.x) {
+    const int nb = lex_to_blk(gb, n);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const double2 a = r64[(size_t)n * NC + c];
-      r32[(size_t)c * V + n] = make_float2((float)a.x, (float)a.y);
+      r32[(size_t)c * V + nb] = make_float2((float)a.x, (float)a.y);
     }
   }
 }
@@ -156,7 +165,7 @@ __global__ void __launch_bounds__(kTile) norm_b(int V, const double2* b, const d
     put_tile(rb, sys, tile, acc[0]);
     put_tile(rx, sys, tile, acc[1]);
   }
-  if (block_done(rb, sys, &last)) {
+  if (block_done(rb, sys, &last, gridDim.x)) {
     const double s = finalize_sum(rb, sys, ntiles, sm);
     const double sx = finalize_sum(rx, sys, ntiles, sm);
     if (threadIdx.x == 0) {

@@ -1,0 +1,48 @@
+// Host-side check of the blocked site order used by the inner-precision
+// storage (GeomBlk in common.cuh): the order is a permutation of the sites,
+// coords() inverts blk_index(), and a hop in the blocked order lands on the
+// blocked index of the lexicographic neighbour, for every site, direction and
+// sign (periodic wrap included).  Prints "ok" or the first mismatch.
+#include <cstdio>
+#include <vector>
+
+#include "../../paper_1312_3265_gb300/csrc/common.cuh"
+
+using namespace swc;
+
+static int check(int L0, int L1, int L2, int L3) {
+  Geom g;
+  g.L[0] = L0; g.L[1] = L1; g.L[2] = L2; g.L[3] = L3;
+  g.stride[0] = 1; g.stride[1] = L0; g.stride[2] = L0 * L1; g.stride[3] = L0 * L1 * L2;
+  g.V = L0 * L1 * L2 * L3;
+  g.apbc = 0;
+  const GeomBlk b = make_blocked(g);
+  std::vector<int> seen(g.V, 0);
+  for (int n = 0; n < g.V; ++n) {
+    int x[4] = {n % L0, (n / L0) % L1, (n / (L0 * L1)) % L2, n / (L0 * L1 * L2)};
+    const int nb = lex_to_blk(b, n);
+    if (nb < 0 || nb >= g.V || seen[nb]++) { printf("not a permutation at %d (%dx%dx%dx%d)\n", n, L0, L1, L2, L3); return 1; }
+    int y[4];
+    coords(b, nb, y);
+    for (int mu = 0; mu < 4; ++mu)
+      if (y[mu] != x[mu]) { printf("coords mismatch at %d\n", n); return 1; }
+    for (int mu = 0; mu < 4; ++mu)
+      for (int s = -1; s <= 1; s += 2) {
+        int z[4] = {x[0], x[1], x[2], x[3]};
+        z[mu] = (z[mu] + s + g.L[mu]) % g.L[mu];
+        const int want = blk_index(b, z);
+        const int got = hop(b, nb, x, mu, s);
+        if (got != want) { printf("hop mismatch n=%d mu=%d s=%d (%dx%dx%dx%d)\n", n, mu, s, L0, L1, L2, L3); return 1; }
+      }
+  }
+  return 0;
+}
+
+int main() {
+  const int dims[][4] = {{2, 2, 2, 2}, {4, 4, 4, 4}, {6, 6, 4, 6}, {16, 16, 16, 32}, {2, 4, 6, 2}, {10, 4, 6, 10},
+                         {24, 24, 24, 48}, {12, 12, 12, 24}, {8, 8, 8, 8}};
+  for (auto& d : dims)
+    if (check(d[0], d[1], d[2], d[3])) return 1;
+  printf("ok\n");
+  return 0;
+}

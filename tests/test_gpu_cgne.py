@@ -306,3 +306,34 @@ def test_autotune_picks_a_width_and_solves(sw):
         check(sw, P, chi, sw.SW_PREC_F32_RELIABLE)
     finally:
         sw.sw_set_param(sw.SW_PARAM_NS_SW, old)
+
+
+@pytest.mark.parametrize("blocking", [0, 1])
+@pytest.mark.parametrize("gfast", [0, 1])
+def test_site_order_and_grid_order(sw, blocking, gfast):
+    """The packed fields' site order (blocked or lexicographic) and the stencil
+    grid order solve the same systems; the grid order does not even change a
+    bit (the reductions go over the same site tiles)."""
+    import torch
+    P = Problem(sw, (8, 4, 6, 8), sw.SW_OP_STAGGERED_WILSON, 6, ls.PLAQ_EPS, 0.07, apbc=True)
+    chis = np.stack([ls.gaussian_source(P.dims, 3, 70 + i) for i in range(5)])
+    chi = dev(chis)
+    old = (sw.sw_get_param(sw.SW_PARAM_SITE_BLOCKING), sw.sw_get_param(sw.SW_PARAM_GROUP_FAST))
+    outs = {}
+    try:
+        sw.sw_set_param(sw.SW_PARAM_SITE_BLOCKING, blocking)
+        for gf in (gfast, 1 - gfast):
+            sw.sw_set_param(sw.SW_PARAM_GROUP_FAST, gf)
+            for prec in (sw.SW_PREC_F32_RELIABLE, sw.SW_PREC_F16_RELIABLE):
+                x = torch.zeros_like(chi)
+                rc, infos = sw.cgne_solve_batch(P.dims, P.op, P.U, P.W, chi, x, [0.07] * 5, 1.0, 1e-9, 10000, prec,
+                                                True)
+                assert rc == sw.SW_OK
+                outs[(gf, prec)] = x.cpu().numpy()
+                for i in range(5):
+                    assert P.true_resid(chis[i].reshape(-1), outs[(gf, prec)][i].reshape(-1)) <= 1.01e-9
+    finally:
+        sw.sw_set_param(sw.SW_PARAM_SITE_BLOCKING, old[0])
+        sw.sw_set_param(sw.SW_PARAM_GROUP_FAST, old[1])
+    for prec in (sw.SW_PREC_F32_RELIABLE, sw.SW_PREC_F16_RELIABLE):
+        assert np.array_equal(outs[(0, prec)], outs[(1, prec)])
