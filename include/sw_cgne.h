@@ -273,6 +273,10 @@ int sw_server_destroy(sw_server srv);
 
 /* Human-readable name of a status code (static string). */
 const char* sw_status_string(int status);
+/* Name of the CUDA error (cudaGetErrorName) behind the most recent
+ * SW_ERR_CUDA returned by any call of this library in the process;
+ * "cudaSuccess" if there was none.  Static string, not to be freed. */
+const char* sw_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

@@ -57,7 +57,10 @@ class SolveInfo:
 class SWError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
-        super().__init__(f"{where}: {sw_status_string(code)} (status {code})")
+        msg = f"{where}: {sw_status_string(code)} (status {code})"
+        if code == -4:
+            msg += f" [{sw_last_cuda_error()}]"
+        super().__init__(msg)
 
 
 def lib_path():
@@ -114,6 +117,8 @@ def lib():
             getattr(L, f).restype = i
         L.sw_status_string.argtypes = [i]
         L.sw_status_string.restype = ctypes.c_char_p
+        L.sw_last_cuda_error.argtypes = []
+        L.sw_last_cuda_error.restype = ctypes.c_char_p
         for f in ("sw_hypercube_build", "sw_dslash_apply", "wilson_dslash_apply", "cgne_solve", "cgne_solve_batch"):
             getattr(L, f).restype = i
         _lib = L
@@ -122,6 +127,10 @@ def lib():
 
 def sw_status_string(code):
     return lib().sw_status_string(int(code)).decode()
+
+
+def sw_last_cuda_error():
+    return lib().sw_last_cuda_error().decode()
 
 
 def _lat(dims, t_antiperiodic):

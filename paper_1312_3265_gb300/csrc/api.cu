@@ -58,6 +58,12 @@ thread_local std::vector<cudaEvent_t> t_used;
 
 void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+std::atomic<int> g_last_cuda_error{0};
+int cuda_fail(cudaError_t e) {
+  g_last_cuda_error.store((int)e);
+  return SW_ERR_CUDA;
+}
+
 bool prof_enabled() {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   return g_prof_on;
@@ -181,6 +187,8 @@ bool overlap(const void* a, size_t na, const void* b, size_t nb) {
 using namespace swc;
 
 extern "C" {
+
+const char* sw_last_cuda_error(void) { return cudaGetErrorName((cudaError_t)g_last_cuda_error.load()); }
 
 const char* sw_status_string(int s) {
   switch (s) {

@@ -430,7 +430,8 @@ class Engine {
   // slots still in flight, or a negative SW_ERR_* code.
   int complete() {
     const cudaError_t e = ev_ ? cudaEventSynchronize(ev_) : cudaStreamSynchronize(st_);
-    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return SW_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (const cudaError_t l = cudaGetLastError(); l != cudaSuccess) return cuda_fail(l);
     int active = 0, nrun = 0;
     need_ru_ = false;
     for (int i = 0; i < cap_; ++i) {

@@ -56,7 +56,8 @@ int hypercube_build_f64(const Geom& g, const double2* U, double2* W, cudaStream_
   const long long grid = (total + block - 1) / block;
   hypercube_kernel<<<(unsigned)grid, block, 0, st>>>(g, GaugeC64{U}, W);
   note_launches(1);
-  return cudaGetLastError() == cudaSuccess ? 0 : -4;
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : cuda_fail(e);
 }
 
 }  // namespace swc

@@ -56,5 +56,7 @@ void prof_flush();
 void prof_commit(bool keep);
 // Kernel launches issued by the library (all entry points), for the caller's accounting.
 void note_launches(int k);
+// Record the CUDA error behind an SW_ERR_CUDA return (sw_last_cuda_error).
+int cuda_fail(cudaError_t e);
 
 }  // namespace swc

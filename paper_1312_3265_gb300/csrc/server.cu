@@ -130,7 +130,7 @@ static int build_engine(const Geom& g, int cap, double r, int prec, MakeOps make
   const Workspace ws = carve_workspace_for<typename OpF::Vec>(wsm, g.V, OpD::NC, cap, MIXED);
   impl->e = std::make_unique<Engine<OpD, OpF, MIXED>>(g, opd, opf, r, cap, chi, x, ws, impl->hs, impl->hs + cap,
                                                       impl->st, impl->ev);
-  if (cudaStreamSynchronize(impl->st) != cudaSuccess) return SW_ERR_CUDA;
+  if (const cudaError_t e = cudaStreamSynchronize(impl->st); e != cudaSuccess) return cuda_fail(e);
   *out = std::move(impl);
   return SW_OK;
 }
@@ -362,7 +362,7 @@ struct Server {
         copies.pop_front();
         event_pool.push_back(c.ev);
         if (q != cudaSuccess) {
-          fail(SW_ERR_CUDA);
+          fail(cuda_fail(q));
           return;
         }
         c.done.info.seconds =

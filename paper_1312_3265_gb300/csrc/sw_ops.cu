@@ -15,7 +15,8 @@ int sw_apply_f64(const Geom& g, const double2* U, const double2* W, const double
                                                           VecC64<3>{out}, mass, 0, r, dagger,
                                                           nullptr, 0);
   note_launches(1);
-  return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SW_OK : cuda_fail(e);
 }
 
 int sw_cgne(const Geom& g, const SolveArgs& a) {

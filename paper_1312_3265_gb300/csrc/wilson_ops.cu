@@ -17,7 +17,8 @@ static int apply_impl(const Geom& g, const double2* U, const double2* in, double
                                                              VecC64<12>{out}, mass, 0, r, dagger,
                                                              nullptr, 0);
   note_launches(1);
-  return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SW_OK : cuda_fail(e);
 }
 
 int wilson_apply_f64(const Geom& g, const double2* U, const double2* in, double2* out, double mass, double r,

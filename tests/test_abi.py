@@ -49,6 +49,8 @@ def test_status_strings(lib):
     assert lib.sw_status_string(0) == b"ok"
     assert b"aligned" in lib.sw_status_string(-3)
     assert lib.sw_status_string(12345) == b"unknown status"
+    lib.sw_last_cuda_error.restype = ctypes.c_char_p
+    assert lib.sw_last_cuda_error() == b"cudaSuccess"
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
