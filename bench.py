@@ -49,13 +49,19 @@ ITERS_TABLE = {"sw": {0.02: 41.0, 0.05: 39.0, 0.1: 36.9, 0.2: 32.0},
                "wilson": {0.02: 118.0, 0.05: 113.6, 0.1: 107.0, 0.2: 94.9}}
 
 
-# DRAM traffic of the dominant kernel from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, profiles/ncu_wilson_k2_fp32_16x16x16x32_12sys.md):
-# bytes of one launch over `systems` running systems and the algorithmic bytes
-# of that launch.  A bench launch's traffic is scaled by its algorithmic bytes
-# (traffic grows with the systems computed).  Set to None when the kernel
-# changes after the capture.
-NCU_TRAFFIC = {"wilson.k2.f32": {"bytes": 947.0e6, "algorithmic": 943.7e6, "systems": 12}}
+# DRAM traffic of a kernel class from one ncu capture of the current kernel
+# build (dram__bytes_read.sum + dram__bytes_write.sum): bytes of one launch
+# over `systems` running systems and the algorithmic bytes of that launch.  A
+# bench launch's traffic is scaled by its algorithmic bytes (traffic grows
+# with the systems computed).  Entries are removed when the kernel changes.
+NCU_TRAFFIC = {
+    # profiles/ncu_sw_k1k2_fp32_16x16x16x32_12sys.md
+    "sw.k1.f32": {"bytes": 209.9e6, "algorithmic": 188.7e6, "systems": 12},
+    "sw.k2.f32": {"bytes": 366.0e6, "algorithmic": 339.7e6, "systems": 12},
+    # profiles/ncu_wilson_k1k2_fp32_16x16x16x32_12sys.md
+    "wilson.k1.f32": {"bytes": 325.4e6, "algorithmic": 339.7e6, "systems": 12},
+    "wilson.k2.f32": {"bytes": 945.1e6, "algorithmic": 943.7e6, "systems": 12},
+}
 
 # FP64 peak of a GB300 (nominal 1.25 TFLOP/s; not in the measured-peaks file):
 # denominator of the FP64-ALU-bound reliable-update matvecs.
@@ -199,6 +205,60 @@ def host_inputs(seeds, masses=MASSES, w_sources=12, dims=DIMS, sources="point"):
     return U, chi_sw, m_sw, chi_w, m_w
 
 
+# ------------------------------------------------------------------ rooflines
+# FP32 peak of a GB300 from its unit counts and clock: 152 SMs x 128 FP32
+# lanes x 2 flop (FMA) x 2.07 GHz (the maximum SM clock).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def classify_kernels(prof, hbm_peak, peak_kind):
+    """Per kernel class: time per launch, and the fraction of the roofline
+    that bounds it.  FP32/FP16 stencils: algorithmic bytes against the
+    measured HBM bandwidth and the paper's flops (Eq. 4) against the FP32 peak;
+    the bound is the resource whose roofline time is longer (the launch's
+    arithmetic intensity against the ridge).  FP64 matvecs: flops against the
+    nominal FP64 peak.  Returns (kernels, roofline of the kernel with the most
+    total time, roofline of the HBM-bound kernel with the most total time)."""
+    kernels, cand = {}, []
+    for k, v in prof.items():
+        ms = v["ms"] / v["launches"]
+        bpl, fpl = v["bytes"] / v["launches"], v.get("flops", 0.0) / v["launches"]
+        e = {"launches": v["launches"], "ms_per_launch": round(ms, 4)}
+        res = []
+        if bpl > 0:
+            gbs = bpl / (ms / 1e3) / 1e9
+            e.update({"GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4)})
+            res.append(("hbm", bpl / (hbm_peak * 1e9), gbs, hbm_peak, "GB/s", bpl, peak_kind))
+        if fpl > 0:
+            tf = fpl / (ms / 1e3) / 1e12
+            fp64 = bpl == 0
+            pk = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+            e.update({"TFLOP/s": round(tf, 3), ("frac_fp64" if fp64 else "frac_fp32"): round(tf / pk, 4)})
+            res.append(("alu", fpl / (pk * 1e12), tf, pk, "TFLOP/s", fpl,
+                        "nominal FP64" if fp64 else "FP32 from unit counts and clock"))
+        if not res:
+            continue
+        bound = max(res, key=lambda r: r[1])
+        e["bound"] = bound[0] if bound[0] == "hbm" else ("alu-fp64" if bpl == 0 else "alu-fp32")
+        kernels[k] = e
+        cand.append((v["ms"], k, bound, ms))
+
+    def roof_of(item):
+        total, name, b, ms = item
+        kind, _, ach, pk, unit, amount, pkind = b
+        cap = NCU_TRAFFIC.get(name)
+        traffic = None
+        if cap and prof[name]["bytes"] > 0:
+            traffic = round(cap["bytes"] * (prof[name]["bytes"] / prof[name]["launches"]) / cap["algorithmic"])
+        return {"kernel": name, "bound": kind, "achieved": round(ach, 3), "peak": round(pk, 2), "unit": unit,
+                "frac": round(ach / pk, 4), "traffic": traffic, "peak_kind": pkind,
+                ("bytes_per_launch" if unit == "GB/s" else "flops_per_launch"): amount, "launch_ms": ms}
+
+    top = max(cand, default=None)
+    top_hbm = max((c for c in cand if c[2][0] == "hbm"), default=None)
+    return kernels, (roof_of(top) if top else None), (roof_of(top_hbm) if top_hbm else None)
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -215,7 +275,8 @@ def run_ours(args):
     sw.lib()
     prec = {"mixed": sw.SW_PREC_F32_RELIABLE, "f16": sw.SW_PREC_F16_RELIABLE, "f64": sw.SW_PREC_F64}[args.precision]
     if args.delta is not None:
-        sw.sw_set_param(sw.SW_PARAM_RELIABLE_DELTA, args.delta)
+        sw.sw_set_param(sw.SW_PARAM_RELIABLE_DELTA_F16 if args.precision == "f16" else sw.SW_PARAM_RELIABLE_DELTA,
+                        args.delta)
     if args.chunk is not None:
         sw.sw_set_param(sw.SW_PARAM_CHUNK, args.chunk)
     if args.graphs is not None:
@@ -360,28 +421,7 @@ def run_ours(args):
     lats = sorted([v for v in lat_sw for _ in m_sw] + [v for v in lat_w for _ in m_w]) or [0.0]
 
     peak, peak_kind = measured_peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
-    roof = None
-    if dom:
-        name, d = dom
-        ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        bpl = d["bytes"] / d["launches"]
-        cap = NCU_TRAFFIC.get(name)
-        traffic = round(cap["bytes"] * bpl / cap["algorithmic"]) if cap else None
-        roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
-                "bytes_per_launch": bpl, "launch_ms": d["ms"] / d["launches"]}
-    kernels = {}
-    for k, v in prof.items():
-        e = {"launches": v["launches"], "ms_per_launch": round(v["ms"] / v["launches"], 4)}
-        if v.get("flops", 0) > 0:  # FP64-ALU-bound matvecs: TFLOP/s against the FP64 peak
-            tf = v["flops"] / (v["ms"] / 1e3) / 1e12
-            e.update({"TFLOP/s": round(tf, 3), "frac_fp64": round(tf / FP64_PEAK_TFLOPS, 4)})
-        else:
-            e.update({"GB/s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1),
-                      "frac_hbm": round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / peak, 4)})
-        kernels[k] = e
-    prof = {k: v for k, v in prof.items() if not v.get("flops", 0) > 0}  # the HBM roofline's candidates
+    kernels, roof, roof_hbm = classify_kernels(prof, peak, peak_kind)
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": K,
@@ -394,7 +434,8 @@ def run_ours(args):
                    f"{args.sources} sources", "lattice": "x".join(map(str, dims)), "masses": list(masses),
                    "solves_per_step": len(m_sw) + len(m_w), "tol": TOL, "r": 1.0,
                    "precision": args.precision, "configurations": "seeds 0-9, mean plaquette 0.59",
-                   "reliable_delta": sw.sw_get_param(sw.SW_PARAM_RELIABLE_DELTA),
+                   "reliable_delta": sw.sw_get_param(sw.SW_PARAM_RELIABLE_DELTA_F16 if args.precision == "f16"
+                                                     else sw.SW_PARAM_RELIABLE_DELTA),
                    "chunk": int(sw.sw_get_param(sw.SW_PARAM_CHUNK)),
                    "graphs": int(sw.sw_get_param(sw.SW_PARAM_GRAPHS)),
                    "site_blocking": int(sw.sw_get_param(sw.SW_PARAM_SITE_BLOCKING)),
@@ -403,7 +444,8 @@ def run_ours(args):
                                           "wilson": int(sw.sw_get_param(sw.SW_PARAM_NS_WILSON))},
                    "l2": "inputs larger than L2: a step touches ~10 GB and each step uses a new configuration",
                    "parallelism": f"replicas x{world}"},
-        "clocks": ck, "gpu_launches": int(launches), "roofline": roof, "kernels": kernels,
+        "clocks": ck, "gpu_launches": int(launches), "roofline": roof, "roofline_hbm_top": roof_hbm,
+        "kernels": kernels,
         "latency_ms": {"p50": round(float(np.percentile(lats, 50)), 2),
                        "p99": round(float(np.percentile(lats, 99)), 2),
                        "note": "time to solution of each solve's batch"},

@@ -164,7 +164,12 @@ int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, const void*
  * SW_PARAM_RELIABLE_DELTA: mixed precision only; the FP32 correction is
  *   folded into the FP64 solution and r = b - A x recomputed in FP64 when the
  *   iterated |r| falls below delta times its maximum since the last such
- *   update (Sleijpen & van der Vorst 1996); (0, 1), default 0.001.
+ *   update (Sleijpen & van der Vorst 1996); (0, 1), default 3e-5.  Applies to
+ *   SW_PREC_F32_RELIABLE.
+ * SW_PARAM_RELIABLE_DELTA_F16: the same trigger for SW_PREC_F16_RELIABLE,
+ *   default 1e-3: FP16 storage drifts from the true residual about four
+ *   orders of magnitude sooner than FP32, and CG loses its conjugacy if the
+ *   residual is not replaced before that.
  * SW_PARAM_NS_SW, SW_PARAM_NS_WILSON: mixed precision only; systems each
  *   thread of the FP32 stencil kernels computes, sharing every link and
  *   transport load (1, 2 or 4; defaults 2 for staggered Wilson, 1 for Wilson).
@@ -182,7 +187,8 @@ int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, const void*
  * decided on an FP64 residual.  Returns SW_ERR_ARG for an unknown key or a
  * value out of range. */
 enum { SW_PARAM_CHUNK = 0, SW_PARAM_RELIABLE_DELTA = 1, SW_PARAM_NS_SW = 2, SW_PARAM_NS_WILSON = 3,
-       SW_PARAM_GRAPHS = 4, SW_PARAM_SITE_BLOCKING = 5, SW_PARAM_GROUP_FAST = 6 };
+       SW_PARAM_GRAPHS = 4, SW_PARAM_SITE_BLOCKING = 5, SW_PARAM_GROUP_FAST = 6,
+       SW_PARAM_RELIABLE_DELTA_F16 = 9 };
 int sw_set_param(int key, double value);
 int sw_get_param(int key, double* value);
 

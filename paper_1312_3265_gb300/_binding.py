@@ -21,6 +21,7 @@ SW_PARAM_NS_WILSON = 3
 SW_PARAM_GRAPHS = 4
 SW_PARAM_SITE_BLOCKING = 5
 SW_PARAM_GROUP_FAST = 6
+SW_PARAM_RELIABLE_DELTA_F16 = 9
 
 
 class Lattice(ctypes.Structure):

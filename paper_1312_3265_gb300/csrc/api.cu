@@ -47,7 +47,8 @@ std::vector<cudaEvent_t> g_pool;
 thread_local std::vector<Pending> t_pending;
 thread_local std::vector<Pending> t_staged;
 std::atomic<int> g_param_chunk{16};
-std::atomic<double> g_param_delta{0.001};
+std::atomic<double> g_param_delta{3e-5};
+std::atomic<double> g_param_delta16{1e-3};
 std::atomic<int> g_param_ns_sw{2};
 std::atomic<int> g_param_ns_wilson{1};
 std::atomic<int> g_param_graphs{1};
@@ -93,7 +94,7 @@ void prof_commit(bool keep) {
 }
 
 int param_chunk() { return g_param_chunk.load(); }
-double param_delta() { return g_param_delta.load(); }
+double param_delta(bool half) { return half ? g_param_delta16.load() : g_param_delta.load(); }
 int param_ns(int nc) { return nc == 3 ? g_param_ns_sw.load() : g_param_ns_wilson.load(); }
 bool param_graphs() { return g_param_graphs.load() != 0; }
 bool param_site_blocking() { return g_param_site_block.load() != 0; }
@@ -213,8 +214,9 @@ int sw_set_param(int key, double value) {
       g_param_chunk.store((int)value);
       return SW_OK;
     case SW_PARAM_RELIABLE_DELTA:
+    case SW_PARAM_RELIABLE_DELTA_F16:
       if (!(value > 0 && value < 1)) return SW_ERR_ARG;
-      g_param_delta.store(value);
+      (key == SW_PARAM_RELIABLE_DELTA ? g_param_delta : g_param_delta16).store(value);
       return SW_OK;
     case SW_PARAM_GRAPHS:
     case SW_PARAM_SITE_BLOCKING:
@@ -239,6 +241,7 @@ int sw_get_param(int key, double* value) {
   switch (key) {
     case SW_PARAM_CHUNK: *value = g_param_chunk.load(); return SW_OK;
     case SW_PARAM_RELIABLE_DELTA: *value = g_param_delta.load(); return SW_OK;
+    case SW_PARAM_RELIABLE_DELTA_F16: *value = g_param_delta16.load(); return SW_OK;
     case SW_PARAM_NS_SW: *value = g_param_ns_sw.load(); return SW_OK;
     case SW_PARAM_NS_WILSON: *value = g_param_ns_wilson.load(); return SW_OK;
     case SW_PARAM_GRAPHS: *value = g_param_graphs.load(); return SW_OK;

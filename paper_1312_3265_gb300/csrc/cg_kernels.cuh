@@ -185,7 +185,7 @@ __device__ __forceinline__ void st_site(const VecP16<NC>& v, int n, const CV<flo
   if (!(m > 1e-30f)) m = (m == m) ? 0.f : m;
   const float inv = m > 0.f ? 1.f / m : 0.f;
 #pragma unroll
-  for (int c = 0; c < NC; ++c) v.p[(size_t)c * v.V + n] = __floats2half2_rn(a.c[c].re * inv, a.c[c].im * inv);
+  for (int c = 0; c < NC; ++c) v.p[pk(n, NC, c)] = __floats2half2_rn(a.c[c].re * inv, a.c[c].im * inv);
   reinterpret_cast<float*>(v.p + (size_t)NC * v.V)[n] = m;
 }
 
@@ -193,7 +193,7 @@ template <int NC>
 __device__ __forceinline__ void st_site(const VecP32q<NC>& v, int n, const CV<float, NC>& a) {
 #pragma unroll
   for (int q = 0; q < NC / 2; ++q)
-    v.p[(size_t)q * v.V + n] = make_float4(a.c[2 * q].re, a.c[2 * q].im, a.c[2 * q + 1].re, a.c[2 * q + 1].im);
+    v.p[pk(n, NC / 2, q)] = make_float4(a.c[2 * q].re, a.c[2 * q].im, a.c[2 * q + 1].re, a.c[2 * q + 1].im);
 }
 
 // Per-system view of a batched vector: system `sys` starts `sys * sstride`
@@ -211,10 +211,13 @@ struct BatchParams {
 };
 
 // ---------------------------------------------------------------- plain apply (ABI)
+// out = (D+m) in, or (D+m)^+ in with dagger; with has_sub, out = sub - (D+m) in
+// (the FP64 residual chi - (D+m) x of a reliable update).
 template <typename T, typename Op>
 __global__ void __launch_bounds__(kTile) apply_kernel(Geom g, Op op, typename Op::Vec in, typename Op::Vec out,
                                                     double mass0, size_t sstride, double r, int dagger,
-                                                    const SysState* S, int only_status, int* nact = nullptr) {
+                                                    const SysState* S, int only_status, int* nact = nullptr,
+                                                    typename Op::Vec sub = {}, int has_sub = 0) {
   // mass: mass0, or each system's own mass when the launch is filtered by status;
   // nact (instrumentation, may be null) counts the systems computed
   const int sys = blockIdx.y;
@@ -222,11 +225,12 @@ __global__ void __launch_bounds__(kTile) apply_kernel(Geom g, Op op, typename Op
   if (nact && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nact, 1);
   in = sys_view(in, sys, sstride);
   out = sys_view(out, sys, sstride);
+  if (has_sub) sub = sys_view(sub, sys, sstride);
   const T m = (T)(S ? S[sys].mass : mass0);
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.V; n += gridDim.x * blockDim.x) {
     const CV<T, Op::NC> v = op.apply(g, n, in, m, (T)r, dagger != 0);
 #pragma unroll
-    for (int c = 0; c < Op::NC; ++c) out.st(n, c, v.c[c]);
+    for (int c = 0; c < Op::NC; ++c) out.st(n, c, has_sub ? sub.ld(n, c) - v.c[c] : v.c[c]);
   }
 }
 
@@ -444,18 +448,17 @@ __global__ void __launch_bounds__(256) cg_k3(int V, RVec r, PVec p, size_t rstri
 }
 
 // ---------------------------------------------------------------- FP64 residual (reliable update)
-// r64 = b - (D+m)^+ t64, |r64|^2, then the convergence decision.
+// r64 = (D+m)^+ t64 with t64 = chi - (D+m) x (apply_kernel's has_sub form), so
+// r64 = b - A x for b = (D+m)^+ chi; |r64|^2, then the convergence decision.
 template <typename Op>
-__global__ void __launch_bounds__(kTile) residual64(Geom g, Op op, typename Op::Vec t, typename Op::Vec b,
-                                                  typename Op::Vec r, BatchParams bp, SysState* S, RedBuf rb,
-                                                  int* nact = nullptr) {
+__global__ void __launch_bounds__(kTile) residual64(Geom g, Op op, typename Op::Vec t, typename Op::Vec r,
+                                                  BatchParams bp, SysState* S, RedBuf rb, int* nact = nullptr) {
   __shared__ double sm[32];
   __shared__ int last;
   const int sys = blockIdx.y;
   if (S[sys].status != ST_NEED_RU) return;
   if (nact && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nact, 1);
   t = sys_view(t, sys, bp.sstride64);
-  b = sys_view(b, sys, bp.sstride64);
   r = sys_view(r, sys, bp.sstride64);
   const double m = S[sys].mass;
   const int ntiles = (g.V + kTile - 1) / kTile;
@@ -466,9 +469,8 @@ __global__ void __launch_bounds__(kTile) residual64(Geom g, Op op, typename Op::
       const CV<double, Op::NC> at = op.apply(g, n, t, m, bp.r, true);
 #pragma unroll
       for (int c = 0; c < Op::NC; ++c) {
-        const cx<double> rc = b.ld(n, c) - at.c[c];
-        r.st(n, c, rc);
-        acc += norm2(rc);
+        r.st(n, c, at.c[c]);
+        acc += norm2(at.c[c]);
       }
     }
     put_tile(rb, sys, tile, block_sum(acc, sm));
@@ -493,6 +495,50 @@ __global__ void __launch_bounds__(kTile) residual64(Geom g, Op op, typename Op::
         s.status = ST_JUST_UPDATED;
       }
     }
+  }
+}
+
+// ---------------------------------------------------------------- inner-precision right-hand side
+// Admission in the mixed modes (systems in ST_ADMIT): b = (D+m)^+ chi with the
+// inner-precision operator on chi's inner-precision copy (in the stencil
+// storage), stored as the iterated residual r and as the first search
+// direction p (x0 = 0 gives r0 = p0 = b), and |b|^2 (FP64 accumulation) ->
+// S.b2.  b is needed only as the iteration's starting residual and for the
+// tolerance scale: every residual that decides convergence is recomputed in
+// FP64 from chi itself (residual64), so no FP64 copy of b exists.
+template <typename T, typename Op, typename RVec, typename GG>
+__global__ void __launch_bounds__(kTile) rhs_lo(GG g, Op op, typename Op::Vec chi, typename Op::Vec p, RVec r,
+                                              BatchParams bp, SysState* S, RedBuf rb, int* nact = nullptr) {
+  __shared__ double sm[32];
+  __shared__ int last;
+  const int sys = blockIdx.y;
+  if (S[sys].status != ST_ADMIT) return;
+  if (nact && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nact, 1);
+  chi = sys_view(chi, sys, bp.vstride);
+  p = sys_view(p, sys, bp.vstride);
+  r = sys_view(r, sys, bp.sstride);
+  const T m = (T)S[sys].mass;
+  const int ntiles = (g.V + kTile - 1) / kTile;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int n = tile * kTile + threadIdx.x;
+    double acc = 0.0;
+    if (n < g.V) {
+      CV<T, Op::NC> v;
+      op.template apply_multi<1, GG>(g, n, chi, bp.vstride, 1u, &m, (T)bp.r, true, &v);
+      T a = T(0);
+#pragma unroll
+      for (int c = 0; c < Op::NC; ++c) {
+        r.st(n, c, v.c[c]);
+        a += norm2(v.c[c]);
+      }
+      st_site(p, n, v);
+      acc = (double)a;
+    }
+    put_tile(rb, sys, tile, block_sum(acc, sm));
+  }
+  if (block_done(rb, sys, &last, gridDim.x)) {
+    const double b2 = finalize_sum(rb, sys, ntiles, sm);
+    if (threadIdx.x == 0) S[sys].b2 = b2;
   }
 }
 

@@ -4,9 +4,14 @@
 // Layouts
 //   canonical (the C ABI's, FP64): site-major arrays of complex128
 //     U[V][4][9], W[V][8][9], vectors [V][ncomp]
-//   planar (internal, FP32): component-major float2 planes, so that a warp
-//     reading one component of 32 consecutive sites touches 256 contiguous bytes
-//     U[4*9][V], W[8*9][V], vectors [ncomp][V]
+//   packed (internal, FP32 / FP16): sites in groups of 16, each group storing
+//     its sites' component planes one after another, element (site n, plane c)
+//     of a field of npl planes at ((n / 16) npl + c) 16 + n % 16 ("AoSoA-16").
+//     A warp reading one component of 16 consecutive sites touches one
+//     contiguous run of 16 units, and the planes of one site lie a
+//     compile-time distance apart, so a whole site is addressed from one base
+//     pointer.  Every lattice extent is even, so V is a multiple of 16.
+//     U: 4*9 planes, W: 8*9 planes, vectors: ncomp planes
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
@@ -109,7 +114,7 @@ struct Geom {
   int apbc;       // antiperiodic fermion BC in time
 };
 
-__device__ __forceinline__ void coords(const Geom& g, int n, int x[4]) {
+__host__ __device__ inline void coords(const Geom& g, int n, int x[4]) {
   x[0] = n % g.L[0];
   int q = n / g.L[0];
   x[1] = q % g.L[1];
@@ -119,7 +124,7 @@ __device__ __forceinline__ void coords(const Geom& g, int n, int x[4]) {
 }
 
 // neighbour index of n (coordinates x) one step `s` (+1/-1) along mu
-__device__ __forceinline__ int hop(const Geom& g, int n, const int x[4], int mu, int s) {
+__host__ __device__ inline int hop(const Geom& g, int n, const int x[4], int mu, int s) {
   if (s > 0) return (x[mu] == g.L[mu] - 1) ? n - (g.L[mu] - 1) * g.stride[mu] : n + g.stride[mu];
   return (x[mu] == 0) ? n + (g.L[mu] - 1) * g.stride[mu] : n - g.stride[mu];
 }
@@ -128,7 +133,7 @@ __device__ __forceinline__ bool bc_flip(const Geom& g, const int x[4], int s) {
   return g.apbc && ((s > 0) ? (x[3] == g.L[3] - 1) : (x[3] == 0));
 }
 
-// Blocked site order of the inner-precision (FP32/FP16) planar storage: the
+// Blocked site order of the inner-precision (FP32/FP16) packed storage: the
 // lattice is cut into blocks of B0 x B1 x B2 x B3 sites (powers of two up to
 // 4, 4, 4, 2), stored one after the other in lexicographic block order, the
 // sites of a block contiguous in lexicographic order inside it.  A 128-site
@@ -214,6 +219,20 @@ __device__ __forceinline__ bool bc_flip(const GeomBlk& g, const int x[4], int s)
   return g.apbc && ((s > 0) ? (x[3] == g.L[3] - 1) : (x[3] == 0));
 }
 
+// Neighbour offsets of site n: n + df[mu] is the forward and n + db[mu] the
+// backward neighbour along mu.  The site index is a sum of one term per
+// direction (lexicographic and blocked orders alike), so a hop along mu
+// changes only the mu-term and a diagonal neighbour -- a hypercube corner
+// x + s -- is n plus one offset per direction.
+template <typename GG>
+__host__ __device__ inline void hop_deltas(const GG& g, int n, const int x[4], int df[4], int db[4]) {
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    df[mu] = hop(g, n, x, mu, +1) - n;
+    db[mu] = hop(g, n, x, mu, -1) - n;
+  }
+}
+
 // lexicographic site index -> blocked index (host and device)
 __host__ __device__ inline int lex_to_blk(const GeomBlk& g, int n) {
   int x[4];
@@ -256,33 +275,38 @@ struct TransC64 {
   }
 };
 
-// Planar FP32: plane c of an object of `ncx` complex numbers per site at p[c*V + n]
+// Packed (AoSoA-16) addressing: unit (site n, plane c) of a field of npl
+// planes.  V is a multiple of 16 (even extents), so no group is partial.
+__host__ __device__ __forceinline__ size_t pk(int n, int npl, int c) {
+  return ((size_t)(n >> 4) * npl + c) * 16 + (n & 15);
+}
+
+// Packed FP32 links, 36 planes: plane mu*9 + 3i + j holds U_mu[i][j]
 struct GaugeP32 {
   static constexpr int kBytes = 4 * 9 * 8;
   static constexpr const char* kPrec = "f32";
   const float2* p;
-  int V;
   __device__ __forceinline__ M3<float> link(int n, int mu) const {
-    const float2* q = p + (size_t)mu * 9 * V + n;
+    const float2* q = p + pk(n, 36, mu * 9);
     M3<float> M;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) { float2 v = __ldg(q + (size_t)(i * 3 + j) * V); M.e[i][j] = {v.x, v.y}; }
+      for (int j = 0; j < 3; ++j) { float2 v = __ldg(q + (i * 3 + j) * 16); M.e[i][j] = {v.x, v.y}; }
     return M;
   }
 };
+// Packed FP32 transports, 72 planes: plane k*9 + 3i + j holds W(x, s_k)[i][j]
 struct TransP32 {
   static constexpr int kBytes = 8 * 9 * 8;
   const float2* p;
-  int V;
   __device__ __forceinline__ M3<float> mat(int n, int k) const {
-    const float2* q = p + (size_t)k * 9 * V + n;
+    const float2* q = p + pk(n, 72, k * 9);
     M3<float> M;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) { float2 v = __ldg(q + (size_t)(i * 3 + j) * V); M.e[i][j] = {v.x, v.y}; }
+      for (int j = 0; j < 3; ++j) { float2 v = __ldg(q + (i * 3 + j) * 16); M.e[i][j] = {v.x, v.y}; }
     return M;
   }
 };
@@ -295,41 +319,41 @@ template <int NC> struct VecC64 {  // canonical [V][NC] complex128
   __device__ __forceinline__ cx<double> ld(int n, int c) const { double2 v = __ldg(p + (size_t)n * NC + c); return {v.x, v.y}; }
   __device__ __forceinline__ void st(int n, int c, cx<double> a) const { p[(size_t)n * NC + c] = make_double2(a.re, a.im); }
 };
-template <int NC> struct VecP32 {  // planar [NC][V] float2
+template <int NC> struct VecP32 {  // packed, NC float2 planes
   using unit = float2;
   static size_t sys_units(int V) { return (size_t)V * NC; }
   float2* p;
-  int V;
-  __device__ __forceinline__ cx<float> ld(int n, int c) const { float2 v = __ldg(p + (size_t)c * V + n); return {v.x, v.y}; }
-  __device__ __forceinline__ void st(int n, int c, cx<float> a) const { p[(size_t)c * V + n] = make_float2(a.re, a.im); }
+  int V;  // volume (the packed addressing itself needs only n)
+  __device__ __forceinline__ cx<float> ld(int n, int c) const { float2 v = __ldg(p + pk(n, NC, c)); return {v.x, v.y}; }
+  __device__ __forceinline__ void st(int n, int c, cx<float> a) const { p[pk(n, NC, c)] = make_float2(a.re, a.im); }
 };
 
-// Planar FP32 with two complex components per 16-byte plane element:
-// [NC/2][V] float4 holding components (2k, 2k+1).  Whole-site loads and stores
+// Packed FP32 with two complex components per 16-byte unit: NC/2 float4
+// planes, plane k holding components (2k, 2k+1).  Whole-site loads and stores
 // use half as many, twice as wide, memory instructions (NC even).
 template <int NC> struct VecP32q {
   static_assert(NC % 2 == 0, "pairs of components");
   using unit = float4;
   static size_t sys_units(int V) { return (size_t)V * NC / 2; }
   float4* p;
-  int V;
+  int V;  // volume (the packed addressing itself needs only n)
   __device__ __forceinline__ cx<float> ld(int n, int c) const {
-    const float2 v = __ldg(reinterpret_cast<const float2*>(p + (size_t)(c >> 1) * V + n) + (c & 1));
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p + pk(n, NC / 2, c >> 1)) + (c & 1));
     return {v.x, v.y};
   }
   __device__ __forceinline__ void st(int n, int c, cx<float> a) const {
-    reinterpret_cast<float2*>(p + (size_t)(c >> 1) * V + n)[c & 1] = make_float2(a.re, a.im);
+    reinterpret_cast<float2*>(p + pk(n, NC / 2, c >> 1))[c & 1] = make_float2(a.re, a.im);
   }
 };
 
-// Planar FP16 storage (mixed precision "half" mode; arithmetic stays FP32).
-//   links: the first two rows only (12 reals) as 6 half2 planes per direction,
-//          U16[mu*6 + c][V]; the third row is rebuilt as conj(row0 x row1),
-//          exact for SU(3) links
-//   transports: all 9 entries, W16[k*9 + c][V] (not unitary: no compression)
-//   vectors: NC half2 planes holding psi/scale, one float scale per site
-//          (the largest |re|, |im| of the site), so every site keeps FP16's
-//          relative precision whatever its magnitude
+// Packed FP16 storage (mixed precision "half" mode; arithmetic stays FP32).
+//   links: the first two rows only (12 reals) as 6 half2 planes per direction
+//          (24 planes); the third row is rebuilt as conj(row0 x row1), exact
+//          for SU(3) links
+//   transports: all 9 entries, 72 half2 planes (not unitary: no compression)
+//   vectors: NC half2 planes holding psi/scale, then one float scale per site
+//          (the largest |re|, |im| of the site, site-major), so every site
+//          keeps FP16's relative precision whatever its magnitude
 __device__ __forceinline__ cx<float> h2c(__half2 h) {
   const float2 f = __half22float2(h);
   return {f.x, f.y};
@@ -339,14 +363,13 @@ struct GaugeP16 {
   static constexpr int kBytes = 4 * 6 * 4;
   static constexpr const char* kPrec = "f16";
   const __half2* p;
-  int V;
   __device__ __forceinline__ M3<float> link(int n, int mu) const {
-    const __half2* q = p + (size_t)mu * 6 * V + n;
+    const __half2* q = p + pk(n, 24, mu * 6);
     M3<float> M;
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) M.e[i][j] = h2c(__ldg(q + (size_t)(i * 3 + j) * V));
+      for (int j = 0; j < 3; ++j) M.e[i][j] = h2c(__ldg(q + (i * 3 + j) * 16));
     // row 2 = conj(row0 x row1)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -360,25 +383,24 @@ struct GaugeP16 {
 struct TransP16 {
   static constexpr int kBytes = 8 * 9 * 4;
   const __half2* p;
-  int V;
   __device__ __forceinline__ M3<float> mat(int n, int k) const {
-    const __half2* q = p + (size_t)k * 9 * V + n;
+    const __half2* q = p + pk(n, 72, k * 9);
     M3<float> M;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) M.e[i][j] = h2c(__ldg(q + (size_t)(i * 3 + j) * V));
+      for (int j = 0; j < 3; ++j) M.e[i][j] = h2c(__ldg(q + (i * 3 + j) * 16));
     return M;
   }
 };
-template <int NC> struct VecP16 {  // per system: [NC][V] half2 planes, then [V] float scales
+template <int NC> struct VecP16 {  // per system: NC packed half2 planes, then [V] float scales
   using unit = __half2;
   static size_t sys_units(int V) { return (size_t)V * (NC + 1); }
   __half2* p;
   int V;
   __device__ __forceinline__ const float* sc() const { return reinterpret_cast<const float*>(p + (size_t)NC * V); }
   __device__ __forceinline__ cx<float> ld(int n, int c) const {
-    const cx<float> v = h2c(__ldg(p + (size_t)c * V + n));
+    const cx<float> v = h2c(__ldg(p + pk(n, NC, c)));
     const float s = __ldg(sc() + n);
     return {v.re * s, v.im * s};
   }

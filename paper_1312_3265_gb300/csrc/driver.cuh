@@ -4,12 +4,13 @@
 //   F64    x, r, p, t in FP64 (canonical layout); the residual is replaced by
 //          the recomputed b - A x whenever the iterated one meets the
 //          tolerance, so convergence is always decided on a true residual.
-//   MIXED  inner iterations in FP32 on planar copies of links and vectors,
-//          with reliable updates (Sleijpen & van der Vorst 1996): when the
-//          iterated residual falls below delta times its maximum since the
-//          last update (or meets the tolerance), the FP32 correction is
-//          added to the FP64 solution and r = b - A x is recomputed in FP64.
-//          Dot products always accumulate in FP64.
+//   MIXED  inner iterations in FP32 (or on FP16 storage) on packed copies of
+//          links and vectors, with reliable updates (Sleijpen & van der Vorst
+//          1996): when the iterated residual falls below delta times its
+//          maximum since the last update (or meets the tolerance), the FP32
+//          correction is added to the FP64 solution and r = b - A x is
+//          recomputed in FP64 as (D+m)^+ (chi - (D+m) x).  Dot products
+//          always accumulate in FP64.
 //
 // The host launches iterations in chunks and reads the per-system status
 // words between chunks; iterations of systems that have stopped return at
@@ -29,25 +30,27 @@
 namespace swc {
 
 // Tunables (sw_set_param): iterations launched between status reads, and
-// the reliable-update trigger delta (update when |r| < delta max|r|).
+// the reliable-update trigger delta (update when |r| < delta max|r|) for FP32
+// or FP16 stencil storage.
 int param_chunk();
-double param_delta();
+double param_delta(bool half);
 int param_ns(int nc);  // systems per thread of the FP32 stencils (1, 2 or 4) for NC components
 bool param_site_blocking();  // blocked site order for the packed FP32/FP16 storage
 bool param_group_fast();     // system groups as the fastest grid dimension of the stencils
 bool param_graphs();   // replay chunks of iterations as captured CUDA graphs
 
-inline int grid_for(const void* kernel, int block, int V, int nsys, int cap) {
+inline int grid_for(const void* kernel, int block, int V, int nsys, int cap, size_t smem = 0) {
   static std::mutex mu;
-  static std::unordered_map<const void*, int> cache;
+  static std::unordered_map<const void*, std::unordered_map<size_t, int>> cache;
   int nb;
   {
     std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(kernel);
-    if (it == cache.end()) {
+    auto& per = cache[kernel];
+    auto it = per.find(smem);
+    if (it == per.end()) {
       nb = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, 0) != cudaSuccess || nb < 1) nb = 1;
-      cache[kernel] = nb;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem) != cudaSuccess || nb < 1) nb = 1;
+      per[smem] = nb;
     } else {
       nb = it->second;
     }
@@ -119,7 +122,7 @@ inline int status_to_code(int st) {
 
 // Device workspace of one batched solve, carved from a single block.
 struct Workspace {
-  double2 *b64, *r64, *t64;  // FP64 canonical
+  double2 *b64, *r64, *t64;  // FP64 canonical (b64: FP64 mode only)
   void *p_lo, *t_lo;         // stencil vectors p, t in the inner precision's storage
   float2 *r32, *x32;         // FP32 residual and correction (mixed precision only)
   SysState* S;
@@ -140,7 +143,7 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 inline size_t workspace_bytes_pt(int V, int NC, int nsys, bool mixed, size_t pt) {
   const size_t n = (size_t)V * NC * nsys;
   const size_t ntiles = (size_t)(V + kTile - 1) / kTile;
-  size_t b = 3 * align_up(sizeof(double2) * n);
+  size_t b = (mixed ? 2 : 3) * align_up(sizeof(double2) * n);  // b64 only in FP64 mode
   b += mixed ? 2 * align_up(pt * nsys) + 2 * align_up(sizeof(float2) * n) : align_up(pt * nsys);
   b += align_up(sizeof(SysState) * nsys) + align_up(sizeof(double) * 2 * ntiles * nsys) +
        align_up(sizeof(unsigned) * nsys) + align_up(sizeof(double) * nsys) +
@@ -165,7 +168,7 @@ inline Workspace carve_workspace_pt(void* base, int V, int NC, int nsys, bool mi
     return p;
   };
   Workspace w{};
-  w.b64 = (double2*)take(sizeof(double2) * n);
+  w.b64 = mixed ? nullptr : (double2*)take(sizeof(double2) * n);
   w.r64 = (double2*)take(sizeof(double2) * n);
   w.t64 = (double2*)take(sizeof(double2) * n);
   if (mixed) {
@@ -248,7 +251,10 @@ inline void ritz_extremes(const double* h, int k, double* lmin, double* lmax) {
 //
 // Admission runs on the device: p (and the FP32 correction) cleared,
 // b = (D+m)^+ chi, |b|^2 and |x0|^2, then b = 0 -> x = 0 (converged),
-// x0 = 0 -> r = b exactly, otherwise an FP64 residual b - A x0.
+// x0 = 0 -> r = b exactly, otherwise an FP64 residual b - A x0.  In the mixed
+// modes b is formed by the inner-precision operator (it only starts the
+// iteration and scales the tolerance); every residual that decides
+// convergence is r = (D+m)^+ (chi - (D+m) x) in FP64, from chi itself.
 //
 // OpD: FP64 operator on canonical storage.  OpF: the inner-iteration operator
 // (FP32 planar when MIXED, else the same as OpD).
@@ -288,6 +294,7 @@ class Engine {
     gR_ = grid_for((const void*)residual64<OpD>, kTile, g.V, cap, pstride_);
     gV_ = grid_for((const void*)cg_k3<TF, VR, VF, NC>, 256, g.V, cap, pstride_);
     gN_ = grid_for((const void*)norm_b<NC>, kTile, g.V, cap, pstride_);
+    if constexpr (MIXED) gH_ = grid_for((const void*)rhs_lo<TF, OpF, VR, GK>, kTile, g.V, cap, pstride_);
     g1_ = grid_for(k1_ptr(), kTile, g.V, ngrp_, pstride_);
     g2_ = grid_for(k2_ptr(), kTile, g.V, ngrp_, pstride_);
     if constexpr (MIXED) {
@@ -311,7 +318,7 @@ class Engine {
     cudaMemsetAsync(ws.pcount, 0, sizeof(int) * 2 * kProfSlots, st);
     cudaMemcpyAsync(ws.S, hr_, sizeof(SysState) * cap, cudaMemcpyHostToDevice, st);
     chunk_ = param_chunk();
-    delta_ = param_delta();
+    delta_ = param_delta(std::is_same<VF, VecP16<NC>>::value);
   }
 
   // FP64 matvec launches (right-hand side: 1 application; residual: 2) are
@@ -346,9 +353,13 @@ class Engine {
     const double rv = (double)sizeof(typename VR::unit) * n_;
     static const std::string c1 = std::string(OpF::kName) + ".k1." + OpF::kPrec;
     static const std::string c2 = std::string(OpF::kName) + ".k2." + OpF::kPrec;
+    // flops: the paper's count per site and application (Eq. 4) for every
+    // computed system (k2's x, r updates are not counted)
+    const double fl = OpF::kFlops * g_.V;
     for (size_t k = 0; k < samples_.size(); ++k) {
-      prof_push(c1.c_str(), samples_[k].e0, samples_[k].e1, gauge + cnt[2 * k] * 2.0 * pv);
-      prof_push(c2.c_str(), samples_[k].e1, samples_[k].e2, gauge + cnt[2 * k + 1] * (2.0 * pv + 4.0 * rv));
+      prof_push(c1.c_str(), samples_[k].e0, samples_[k].e1, gauge + cnt[2 * k] * 2.0 * pv, fl * cnt[2 * k]);
+      prof_push(c2.c_str(), samples_[k].e1, samples_[k].e2, gauge + cnt[2 * k + 1] * (2.0 * pv + 4.0 * rv),
+                fl * cnt[2 * k + 1]);
     }
     prof_commit(true);
     samples_.clear();
@@ -393,13 +404,22 @@ class Engine {
       using PU = typename VF::unit;
       admit_clear<PU><<<dim3(gV_, cap_), 256, 0, st_>>>(vunits_, static_cast<PU*>(ws_.p_lo), vunits_,
                                                          MIXED ? ws_.x32 : nullptr, MIXED ? n_ : 0, S);
-      FpSample* fs = fp_sample(1);
-      apply_kernel<double, OpD><<<dim3(gA_, cap_), kTile, 0, st_>>>(g_, opd_, V64{chi_}, V64{ws_.b64}, 0.0, n_,
-                                                                    r_, 1, S, ST_ADMIT, fs ? fs->cnt : nullptr);
-      if (fs) cudaEventRecord(fs->e1, st_);
-      norm_b<NC><<<dim3(gN_, cap_), kTile, 0, st_>>>(g_.V, ws_.b64, x_, n_, S, rb_);
-      admit_vectors<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, ws_.b64, n_, S);
-      admit_states<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S);
+      if constexpr (MIXED) {
+        // b = (D+m)^+ chi in the inner precision: r = p = b and |b|^2
+        demote_chi<NC, VF><<<dim3(gV_, cap_), 256, 0, st_>>>(gb_, chi_, ft_, n_, vunits_, S);
+        rhs_lo<TF, OpF, VR, GK><<<dim3(gH_, cap_), kTile, 0, st_>>>(gk_, opf_, ft_, fp_, fr_, bp_, S, rb_);
+        norm_b<NC><<<dim3(gN_, cap_), kTile, 0, st_>>>(g_.V, nullptr, x_, n_, S, rb_);
+        admit_vectors<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, nullptr, n_, S);
+        note_launches(1);
+      } else {
+        FpSample* fs = fp_sample(1);
+        apply_kernel<double, OpD><<<dim3(gA_, cap_), kTile, 0, st_>>>(g_, opd_, V64{chi_}, V64{ws_.b64}, 0.0, n_,
+                                                                      r_, 1, S, ST_ADMIT, fs ? fs->cnt : nullptr);
+        if (fs) cudaEventRecord(fs->e1, st_);
+        norm_b<NC><<<dim3(gN_, cap_), kTile, 0, st_>>>(g_.V, ws_.b64, x_, n_, S, rb_);
+        admit_vectors<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, ws_.b64, n_, S);
+      }
+      admit_states<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S, MIXED ? 1 : 0);
       note_launches(5);
       ru = true;
     }
@@ -477,10 +497,11 @@ class Engine {
     SysState* S = ws_.S;
     if constexpr (MIXED) accum_x<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(gb_, x_, ws_.x32, n_, n_, S);
     FpSample* fs = fp_sample(2);
+    // r = (D+m)^+ (chi - (D+m) x) = b - A x, all in FP64
     apply_kernel<double, OpD><<<dim3(gA_, cap_), kTile, 0, st_>>>(g_, opd_, V64{x_}, V64{ws_.t64}, 0.0, n_, r_, 0,
-                                                                  S, ST_NEED_RU, fs ? fs->cnt : nullptr);
-    residual64<OpD><<<dim3(gR_, cap_), kTile, 0, st_>>>(g_, opd_, V64{ws_.t64}, V64{ws_.b64}, V64{ws_.r64}, bp_, S,
-                                                        rb_);
+                                                                  S, ST_NEED_RU, fs ? fs->cnt : nullptr,
+                                                                  V64{chi_}, 1);
+    residual64<OpD><<<dim3(gR_, cap_), kTile, 0, st_>>>(g_, opd_, V64{ws_.t64}, V64{ws_.r64}, bp_, S, rb_);
     if (fs) cudaEventRecord(fs->e1, st_);
     if constexpr (MIXED) demote_r<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(gb_, ws_.r64, ws_.r32, n_, n_, S);
     cg_k3<TF, VR, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, vunits_, S, ST_JUST_UPDATED);
@@ -534,19 +555,21 @@ class Engine {
     cudaMemset(ws_.pcount + kProfSlots, 0, sizeof(int) * kProfSlots);
   }
 
+  // Register-blocking widths 2 and 4 exist for the inner-precision stencils
+  // only (the FP64 ones are ALU-bound and run one system per thread).
   const void* k1_ptr() const {
-    switch (ns_) {
-      case 2: return (const void*)cg_k1<TF, OpF, 2, GK>;
-      case 4: return (const void*)cg_k1<TF, OpF, 4, GK>;
-      default: return (const void*)cg_k1<TF, OpF, 1, GK>;
+    if constexpr (MIXED) {
+      if (ns_ == 2) return (const void*)cg_k1<TF, OpF, 2, GK>;
+      if (ns_ == 4) return (const void*)cg_k1<TF, OpF, 4, GK>;
     }
+    return (const void*)cg_k1<TF, OpF, 1, GK>;
   }
   const void* k2_ptr() const {
-    switch (ns_) {
-      case 2: return (const void*)cg_k2<TF, OpF, 2, VR, GK>;
-      case 4: return (const void*)cg_k2<TF, OpF, 4, VR, GK>;
-      default: return (const void*)cg_k2<TF, OpF, 1, VR, GK>;
+    if constexpr (MIXED) {
+      if (ns_ == 2) return (const void*)cg_k2<TF, OpF, 2, VR, GK>;
+      if (ns_ == 4) return (const void*)cg_k2<TF, OpF, 4, VR, GK>;
     }
+    return (const void*)cg_k2<TF, OpF, 1, VR, GK>;
   }
   template <int NS> void launch_k12(int* c) {
     SysState* S = ws_.S;
@@ -570,10 +593,12 @@ class Engine {
       c = ws_.pcount + 2 * (samples_.size() - 1);
       cudaEventRecord(samples_.back().e0, st_);
     }
-    switch (ns_) {
-      case 2: launch_k12<2>(c); break;
-      case 4: launch_k12<4>(c); break;
-      default: launch_k12<1>(c); break;
+    if constexpr (MIXED) {
+      if (ns_ == 2) launch_k12<2>(c);
+      else if (ns_ == 4) launch_k12<4>(c);
+      else launch_k12<1>(c);
+    } else {
+      launch_k12<1>(c);
     }
     if (sample) cudaEventRecord(samples_.back().e2, st_);
     cg_k3<TF, VR, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, vunits_, S, ST_RUNNING);
@@ -598,7 +623,7 @@ class Engine {
   cudaStream_t st_;
   cudaEvent_t ev_;
   size_t n_;
-  int pstride_ = 0, ngrp_ = 0, gA_ = 0, gR_ = 0, gV_ = 0, gN_ = 0, g1_ = 0, g2_ = 0;
+  int pstride_ = 0, ngrp_ = 0, gA_ = 0, gR_ = 0, gV_ = 0, gN_ = 0, gH_ = 0, g1_ = 0, g2_ = 0;
   RedBuf rb_{};
   BatchParams bp_{};
   VF fp_{}, ft_{};

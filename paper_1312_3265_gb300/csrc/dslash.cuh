@@ -28,25 +28,25 @@ template <typename T> __device__ __forceinline__ void neg3(V3<T>& v) {
   for (int i = 0; i < 3; ++i) v.c[i] = T(-1) * v.c[i];
 }
 
-// Hypercube corner of n displaced by s = (s0, s1, s2, s3), each +-1.
-template <typename GG>
-__device__ __forceinline__ int corner(const GG& g, int n, const int x[4], int s0, int s1, int s2, int s3) {
-  n = hop(g, n, x, 0, s0);
-  n = hop(g, n, x, 1, s1);
-  n = hop(g, n, x, 2, s2);
-  return hop(g, n, x, 3, s3);
+// Offsets of the two hypercube corners paired with stored transport k
+// (s_k = (s0, s1, s2, +1), bit mu of k set: s_mu = -1): the corner x + s_k,
+// and x - s_k, whose transport W(x - s_k, s_k) gives W(x, -s_k) = W(x - s_k, s_k)^+.
+__host__ __device__ inline void corner_offsets(int k, const int df[4], const int db[4], int& of, int& ob) {
+  of = ((k & 1) ? db[0] : df[0]) + ((k & 2) ? db[1] : df[1]) + ((k & 4) ? db[2] : df[2]) + df[3];
+  ob = ((k & 1) ? df[0] : db[0]) + ((k & 2) ? df[1] : db[1]) + ((k & 4) ? df[2] : db[2]) + db[3];
 }
 
 template <typename T, typename G, typename Wt, typename In>
 __device__ __forceinline__ V3<T> sw_site(const Geom& g, int n, const G& U, const Wt& W, const In& in,
                                          T mass, T r, bool dagger) {
-  int x[4];
+  int x[4], df[4], db[4];
   coords(g, n, x);
+  hop_deltas(g, n, x, df, db);
   V3<T> st = zero3<T>();
   int par = 0;
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
-    const int nf = hop(g, n, x, mu, +1), nb = hop(g, n, x, mu, -1);
+    const int nf = n + df[mu], nb = n + db[mu];
     V3<T> f = mv(U.link(n, mu), ld3<In, T>(in, nf));
     V3<T> b = mdv(U.link(nb, mu), ld3<In, T>(in, nb));
     if (mu == 3) {
@@ -62,9 +62,9 @@ __device__ __forceinline__ V3<T> sw_site(const Geom& g, int n, const G& U, const
   const bool fflip = bc_flip(g, x, +1), bflip = bc_flip(g, x, -1);
 #pragma unroll 2
   for (int k = 0; k < 8; ++k) {
-    const int s0 = (k & 1) ? -1 : 1, s1 = (k & 2) ? -1 : 1, s2 = (k & 4) ? -1 : 1;
-    const int yf = corner(g, n, x, s0, s1, s2, +1);
-    const int yb = corner(g, n, x, -s0, -s1, -s2, -1);
+    int of, ob;
+    corner_offsets(k, df, db, of, ob);
+    const int yf = n + of, yb = n + ob;
     V3<T> a = mv(W.mat(n, k), ld3<In, T>(in, yf));
     V3<T> b = mdv(W.mat(yb, k), ld3<In, T>(in, yb));
     if (fflip) neg3(a);
@@ -91,13 +91,14 @@ template <typename In, typename T> struct SpLoader {
     return p;
   }
 };
-// float4 planes: a spinor is 6 sixteen-byte loads
+// float4 planes: a spinor is 6 sixteen-byte loads from one base address
 template <> struct SpLoader<VecP32q<12>, float> {
   static __device__ __forceinline__ Sp<float> load(const VecP32q<12>& in, int n) {
     Sp<float> p;
+    const float4* b = in.p + pk(n, 6, 0);
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-      const float4 v = __ldg(in.p + (size_t)q * in.V + n);
+      const float4 v = __ldg(b + q * 16);
       const int c0 = 2 * q, c1 = 2 * q + 1;
       p.s[c0 / 3].c[c0 % 3] = {v.x, v.y};
       p.s[c1 / 3].c[c1 % 3] = {v.z, v.w};
@@ -162,15 +163,16 @@ __device__ __forceinline__ void wgeneral(int mu, T c, T r, const Sp<T>& f, Sp<T>
 template <typename T, bool R1, typename G, typename In>
 __device__ __forceinline__ Sp<T> wilson_site(const Geom& g, int n, const G& U, const In& in,
                                              T mass, T r, bool dagger) {
-  int x[4];
+  int x[4], df[4], db[4];
   coords(g, n, x);
+  hop_deltas(g, n, x, df, db);
   Sp<T> acc;
 #pragma unroll
   for (int s = 0; s < 4; ++s) acc.s[s] = zero3<T>();
   const T sg = dagger ? T(-1) : T(1);
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
-    const int nf = hop(g, n, x, mu, +1), nb = hop(g, n, x, mu, -1);
+    const int nf = n + df[mu], nb = n + db[mu];
     T bf = T(1), bb = T(1);
     if (mu == 3) {
       if (bc_flip(g, x, +1)) bf = T(-1);
@@ -239,8 +241,9 @@ template <typename T, int NS, typename G, typename Wt, typename In, typename GG>
 __device__ __forceinline__ void sw_site_multi(const GG& g, int n, const G& U, const Wt& W, const In& in,
                                               size_t stride, unsigned act, const T* mass, T r, bool dagger,
                                               V3<T>* out) {
-  int x[4];
+  int x[4], df[4], db[4];
   coords(g, n, x);
+  hop_deltas(g, n, x, df, db);
   V3<T> acc[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) acc[s] = zero3<T>();
@@ -248,7 +251,7 @@ __device__ __forceinline__ void sw_site_multi(const GG& g, int n, const G& U, co
   int par = 0;
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
-    const int nf = hop(g, n, x, mu, +1), nb = hop(g, n, x, mu, -1);
+    const int nf = n + df[mu], nb = n + db[mu];
     const T eta = (par & 1) ? -half : half;
     T cf = eta, cb = -eta;
     if (mu == 3) {
@@ -269,9 +272,9 @@ __device__ __forceinline__ void sw_site_multi(const GG& g, int n, const G& U, co
   const T hf = bc_flip(g, x, +1) ? -hs : hs, hb = bc_flip(g, x, -1) ? -hs : hs;
 #pragma unroll 1
   for (int k = 0; k < 8; ++k) {
-    const int s0 = (k & 1) ? -1 : 1, s1 = (k & 2) ? -1 : 1, s2 = (k & 4) ? -1 : 1;
-    const int yf = corner(g, n, x, s0, s1, s2, +1);
-    const int yb = corner(g, n, x, -s0, -s1, -s2, -1);
+    int of, ob;
+    corner_offsets(k, df, db, of, ob);
+    const int yf = n + of, yb = n + ob;
     const M3<T> Wf = W.mat(n, k);
 #pragma unroll
     for (int s = 0; s < NS; ++s)
@@ -293,6 +296,8 @@ __device__ __forceinline__ void sw_site_multi(const GG& g, int n, const G& U, co
 template <typename T, bool R1, int NS, typename G, typename In, typename GG>
 __device__ __forceinline__ void wilson_site_multi(const GG& g, int n, const G& U, const In& in, size_t stride,
                                                   unsigned act, const T* mass, T r, bool dagger, Sp<T>* out) {
+  // (neighbours computed where used: holding eight offsets costs the
+  // register-capped Wilson kernels more than the few integer operations)
   int x[4];
   coords(g, n, x);
   Sp<T> acc[NS];

@@ -4,7 +4,7 @@
 
 namespace swc {
 
-// canonical FP64 [V][nobj][9] -> planar FP32 [nobj*9][V], blocked site order
+// canonical FP64 [V][nobj][9] -> packed FP32 (nobj*9 planes), blocked site order
 static __global__ void pack_mats_p32(GeomBlk gb, int nobj, const double2* __restrict__ src,
                                      float2* __restrict__ dst) {
   const int V = gb.V;
@@ -13,22 +13,22 @@ static __global__ void pack_mats_p32(GeomBlk gb, int nobj, const double2* __rest
     const size_t n = i / ((size_t)nobj * 9);
     const size_t c = i - n * nobj * 9;
     const double2 v = src[i];
-    dst[c * V + lex_to_blk(gb, (int)n)] = make_float2((float)v.x, (float)v.y);
+    dst[pk(lex_to_blk(gb, (int)n), nobj * 9, (int)c)] = make_float2((float)v.x, (float)v.y);
   }
 }
 
-// canonical FP64 links [V][4][9] -> FP16 12-real planes [4*6][V] (rows 0, 1), blocked order
+// canonical FP64 links [V][4][9] -> packed FP16 12-real links (24 planes: rows 0, 1), blocked order
 static __global__ void pack_links_h12(GeomBlk gb, const double2* __restrict__ src, __half2* __restrict__ dst) {
   const int V = gb.V;
   const size_t total = (size_t)V * 4 * 6;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const size_t n = i / 24, r = i - n * 24, mu = r / 6, c = r - mu * 6;
     const double2 v = src[(n * 4 + mu) * 9 + c];
-    dst[(mu * 6 + c) * V + lex_to_blk(gb, (int)n)] = __floats2half2_rn((float)v.x, (float)v.y);
+    dst[pk(lex_to_blk(gb, (int)n), 24, (int)(mu * 6 + c))] = __floats2half2_rn((float)v.x, (float)v.y);
   }
 }
 
-// canonical FP64 [V][nobj][9] -> FP16 planes [nobj*9][V], blocked order
+// canonical FP64 [V][nobj][9] -> packed FP16 (nobj*9 planes), blocked order
 static __global__ void pack_mats_h(GeomBlk gb, int nobj, const double2* __restrict__ src,
                                    __half2* __restrict__ dst) {
   const int V = gb.V;
@@ -37,7 +37,7 @@ static __global__ void pack_mats_h(GeomBlk gb, int nobj, const double2* __restri
     const size_t n = i / ((size_t)nobj * 9);
     const size_t c = i - n * nobj * 9;
     const double2 v = src[i];
-    dst[c * V + lex_to_blk(gb, (int)n)] = __floats2half2_rn((float)v.x, (float)v.y);
+    dst[pk(lex_to_blk(gb, (int)n), nobj * 9, (int)c)] = __floats2half2_rn((float)v.x, (float)v.y);
   }
 }
 
@@ -77,7 +77,7 @@ static __global__ void su3_deviation(int V, const double2* __restrict__ U, unsig
   atomicMax(dev, __float_as_uint(worst));
 }
 
-// x64 (canonical) += x32 (planar, blocked order); x32 = 0   -- systems with status NEED_RU
+// x64 (canonical) += x32 (packed, blocked order); x32 = 0   -- systems with status NEED_RU
 template <int NC>
 __global__ void accum_x(GeomBlk gb, double2* x64, float2* x32, size_t s64, size_t s32, const SysState* S) {
   const int sys = blockIdx.y;
@@ -89,17 +89,17 @@ __global__ void accum_x(GeomBlk gb, double2* x64, float2* x32, size_t s64, size_
     const int nb = lex_to_blk(gb, n);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      const float2 a = x32[(size_t)c * V + nb];
+      const float2 a = x32[pk(nb, NC, c)];
       double2 b = x64[(size_t)n * NC + c];
       b.x += (double)a.x;
       b.y += (double)a.y;
       x64[(size_t)n * NC + c] = b;
-      x32[(size_t)c * V + nb] = make_float2(0.f, 0.f);
+      x32[pk(nb, NC, c)] = make_float2(0.f, 0.f);
     }
   }
 }
 
-// r32 (planar, blocked order) = (float) r64 (canonical)   -- systems with status JUST_UPDATED
+// r32 (packed, blocked order) = (float) r64 (canonical)   -- systems with status JUST_UPDATED
 template <int NC>
 __global__ void demote_r(GeomBlk gb, const double2* r64, float2* r32, size_t s64, size_t s32, const SysState* S) {
   const int sys = blockIdx.y;
@@ -112,7 +112,7 @@ __global__ void demote_r(GeomBlk gb, const double2* r64, float2* r32, size_t s64
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const double2 a = r64[(size_t)n * NC + c];
-      r32[(size_t)c * V + nb] = make_float2((float)a.x, (float)a.y);
+      r32[pk(nb, NC, c)] = make_float2((float)a.x, (float)a.y);
     }
   }
 }
@@ -133,7 +133,28 @@ __global__ void admit_clear(size_t units, TP* p, size_t pstride, float2* x32, si
   }
 }
 
-// Admission, step 3: |b|^2 and |x0|^2 of each admitted system -> S.b2, S.x02,
+// Admission (mixed modes), before rhs_lo: chi (canonical FP64) -> its
+// inner-precision copy in the stencil storage (blocked site order), for the
+// systems in ST_ADMIT.
+template <int NC, typename PVec>
+__global__ void demote_chi(GeomBlk gb, const double2* chi, PVec out, size_t s64, size_t sout, const SysState* S) {
+  const int sys = blockIdx.y;
+  if (S[sys].status != ST_ADMIT) return;
+  chi += sys * s64;
+  out = sys_view(out, sys, sout);
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gb.V; n += gridDim.x * blockDim.x) {
+    CV<float, NC> v;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const double2 a = chi[(size_t)n * NC + c];
+      v.c[c] = {(float)a.x, (float)a.y};
+    }
+    st_site(out, lex_to_blk(gb, n), v);
+  }
+}
+
+// Admission, step 3: |x0|^2 of each admitted system -> S.x02, and |b|^2 ->
+// S.b2 from b (FP64 mode; b == nullptr: S.b2 already holds it, from rhs_lo);
 // S.tol2 <- S.tol2 * |b|^2 (S.tol2 holds tol^2 on entry), and the system's
 // next state: b = 0 -> ST_ZERO_B, x0 = 0 -> ST_ZERO_GUESS, else ST_NEED_RU
 // (non-finite b -> ST_FAILED).
@@ -144,7 +165,7 @@ __global__ void __launch_bounds__(kTile) norm_b(int V, const double2* b, const d
   __shared__ int last;
   const int sys = blockIdx.y;
   if (S[sys].status != ST_ADMIT) return;
-  b += sys * s64;
+  if (b) b += sys * s64;
   x += sys * s64;
   const int ntiles = (V + kTile - 1) / kTile;
   RedBuf rx = rb;  // |x0|^2 tile sums go to the second half of the partials
@@ -155,10 +176,12 @@ __global__ void __launch_bounds__(kTile) norm_b(int V, const double2* b, const d
     if (n < V) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const double2 v = b[(size_t)n * NC + c];
         const double2 w = x[(size_t)n * NC + c];
-        acc[0] += v.x * v.x + v.y * v.y;
         acc[1] += w.x * w.x + w.y * w.y;
+        if (b) {
+          const double2 v = b[(size_t)n * NC + c];
+          acc[0] += v.x * v.x + v.y * v.y;
+        }
       }
     }
     block_sum_multi<2>(acc, sm);
@@ -166,27 +189,30 @@ __global__ void __launch_bounds__(kTile) norm_b(int V, const double2* b, const d
     put_tile(rx, sys, tile, acc[1]);
   }
   if (block_done(rb, sys, &last, gridDim.x)) {
-    const double s = finalize_sum(rb, sys, ntiles, sm);
+    const double s = b ? finalize_sum(rb, sys, ntiles, sm) : 0.0;
     const double sx = finalize_sum(rx, sys, ntiles, sm);
     if (threadIdx.x == 0) {
       SysState& st = S[sys];
-      st.b2 = s;
+      if (b) st.b2 = s;
+      const double b2 = st.b2;
       st.x02 = sx;
-      st.tol2 *= s;
-      if (!isfinite(s) || !isfinite(sx)) st.status = ST_FAILED;
-      else if (s == 0.0) st.status = ST_ZERO_B;
+      st.tol2 *= b2;
+      if (!isfinite(b2) || !isfinite(sx)) st.status = ST_FAILED;
+      else if (b2 == 0.0) st.status = ST_ZERO_B;
       else if (sx == 0.0) st.status = ST_ZERO_GUESS;
       else st.status = ST_NEED_RU;
     }
   }
 }
 
-// Admission, step 4: b = 0 -> x = 0;  x0 = 0 -> r = b (exact initial residual).
+// Admission, step 4: b = 0 -> x = 0;  x0 = 0 -> r = b (exact initial
+// residual; FP64 mode: r64 = b64, mixed modes: rhs_lo has already stored r
+// and p, b64 == nullptr).
 template <int NC>
 __global__ void admit_vectors(int V, double2* x, double2* r64, const double2* b64, size_t s64, const SysState* S) {
   const int sys = blockIdx.y;
   const int st = S[sys].status;
-  if (st != ST_ZERO_B && st != ST_ZERO_GUESS) return;
+  if (st != ST_ZERO_B && (st != ST_ZERO_GUESS || !b64)) return;
   const size_t n = (size_t)V * NC, off = sys * s64;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     if (st == ST_ZERO_B) x[off + i] = make_double2(0.0, 0.0);
@@ -194,8 +220,10 @@ __global__ void admit_vectors(int V, double2* x, double2* r64, const double2* b6
   }
 }
 
-// Admission, step 5: ST_ZERO_B -> converged; ST_ZERO_GUESS -> residual known.
-static __global__ void admit_states(int nsys, SysState* S) {
+// Admission, step 5: ST_ZERO_B -> converged; ST_ZERO_GUESS -> residual known:
+// FP64 mode: JUST_UPDATED (p = r still to set); mixed modes (p_set): rhs_lo
+// has set r = p = b, so the system runs at once.
+static __global__ void admit_states(int nsys, SysState* S, int p_set) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsys) return;
   SysState& s = S[i];
@@ -205,7 +233,7 @@ static __global__ void admit_states(int nsys, SysState* S) {
   } else if (s.status == ST_ZERO_GUESS) {
     s.rr = s.rr_true = s.rmax2 = s.b2;
     s.beta = 0.0;
-    s.status = ST_JUST_UPDATED;
+    s.status = p_set ? ST_RUNNING : ST_JUST_UPDATED;
   }
 }
 

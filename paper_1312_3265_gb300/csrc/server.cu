@@ -187,7 +187,7 @@ static int make_engine(const Geom& g, int op, const double2* U, double r, int pr
         pack_mats_h<<<gp, 256, 0, st>>>(make_blocked(g, param_site_blocking()), 8, Wr, w16);
         note_launches(2);
         *d = SW64{GaugeC64{Ur}, TransC64{Wr}};
-        *f = SW16{GaugeP16{u16, g.V}, TransP16{w16, g.V}};
+        *f = SW16{GaugeP16{u16}, TransP16{w16}};
         return (int)SW_OK;
       }, out);
     return build_engine<SW64, SW32, true>(g, cap, r, prec, [&](auto& owned, cudaStream_t st, SW64* d, SW32* f) {
@@ -200,7 +200,7 @@ static int make_engine(const Geom& g, int op, const double2* U, double r, int pr
       pack_mats_p32<<<gp, 256, 0, st>>>(make_blocked(g, param_site_blocking()), 8, Wr, w32);
       note_launches(2);
       *d = SW64{GaugeC64{Ur}, TransC64{Wr}};
-      *f = SW32{GaugeP32{u32, g.V}, TransP32{w32, g.V}};
+      *f = SW32{GaugeP32{u32}, TransP32{w32}};
       return (int)SW_OK;
     }, out);
   }
@@ -225,7 +225,7 @@ static int make_engine(const Geom& g, int op, const double2* U, double r, int pr
         pack_links_h12<<<gp, 256, 0, st>>>(make_blocked(g, param_site_blocking()), Ur, u16);
         note_launches(1);
         *d = W64<R1>{GaugeC64{Ur}};
-        *f = W16<R1>{GaugeP16{u16, g.V}};
+        *f = W16<R1>{GaugeP16{u16}};
         return (int)SW_OK;
       }, out);
     return build_engine<W64<R1>, W32<R1>, true>(g, cap, r, prec,
@@ -237,7 +237,7 @@ static int make_engine(const Geom& g, int op, const double2* U, double r, int pr
       pack_mats_p32<<<gp, 256, 0, st>>>(make_blocked(g, param_site_blocking()), 4, Ur, u32);
       note_launches(1);
       *d = W64<R1>{GaugeC64{Ur}};
-      *f = W32<R1>{GaugeP32{u32, g.V}};
+      *f = W32<R1>{GaugeP32{u32}};
       return (int)SW_OK;
     }, out);
   };

@@ -31,7 +31,7 @@ int sw_cgne(const Geom& g, const SolveArgs& a) {
     pack_mats_p32<<<gp, 256, 0, a.stream>>>(make_blocked(g, param_site_blocking()), 4, a.U, mu.as<float2>());
     pack_mats_p32<<<gp, 256, 0, a.stream>>>(make_blocked(g, param_site_blocking()), 8, a.W, mw.as<float2>());
     note_launches(2);
-    const SW32 opf{GaugeP32{mu.as<float2>(), g.V}, TransP32{mw.as<float2>(), g.V}};
+    const SW32 opf{GaugeP32{mu.as<float2>()}, TransP32{mw.as<float2>()}};
     return run_cgne<SW64, SW32, true>(g, opd, opf, a);
   }
   if (a.precision == SW_PREC_F16_RELIABLE) {
@@ -44,7 +44,7 @@ int sw_cgne(const Geom& g, const SolveArgs& a) {
     pack_links_h12<<<gp, 256, 0, a.stream>>>(make_blocked(g, param_site_blocking()), a.U, mu.as<__half2>());
     pack_mats_h<<<gp, 256, 0, a.stream>>>(make_blocked(g, param_site_blocking()), 8, a.W, mw.as<__half2>());
     note_launches(2);
-    const SW16 opf{GaugeP16{mu.as<__half2>(), g.V}, TransP16{mw.as<__half2>(), g.V}};
+    const SW16 opf{GaugeP16{mu.as<__half2>()}, TransP16{mw.as<__half2>()}};
     return run_cgne<SW64, SW16, true>(g, opd, opf, a);
   }
   return SW_ERR_ARG;

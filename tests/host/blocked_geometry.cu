@@ -1,12 +1,15 @@
-// Host-side check of the blocked site order used by the inner-precision
-// storage (GeomBlk in common.cuh): the order is a permutation of the sites,
-// coords() inverts blk_index(), and a hop in the blocked order lands on the
-// blocked index of the lexicographic neighbour, for every site, direction and
-// sign (periodic wrap included).  Prints "ok" or the first mismatch.
+// Host-side check of the site addressing used by the stencils (common.cuh,
+// dslash.cuh): the blocked site order is a permutation of the sites, coords()
+// inverts blk_index(), and a hop in the blocked order lands on the blocked
+// index of the lexicographic neighbour, for every site, direction and sign
+// (periodic wrap included); the per-site offsets reach all 16 hypercube
+// corners x +- s in both orders; the packed (AoSoA-16) unit index is a
+// bijection.  Prints "ok" or the first mismatch.
 #include <cstdio>
 #include <vector>
 
 #include "../../paper_1312_3265_gb300/csrc/common.cuh"
+#include "../../paper_1312_3265_gb300/csrc/dslash.cuh"
 
 using namespace swc;
 
@@ -33,6 +36,41 @@ static int check(int L0, int L1, int L2, int L3) {
         const int want = blk_index(b, z);
         const int got = hop(b, nb, x, mu, s);
         if (got != want) { printf("hop mismatch n=%d mu=%d s=%d (%dx%dx%dx%d)\n", n, mu, s, L0, L1, L2, L3); return 1; }
+      }
+  }
+  // hypercube corners from per-site offsets (lexicographic and blocked order)
+  for (int n = 0; n < g.V; ++n) {
+    int x[4] = {n % L0, (n / L0) % L1, (n / (L0 * L1)) % L2, n / (L0 * L1 * L2)};
+    const int nb = lex_to_blk(b, n);
+    int df[4], db[4], bf[4], bb[4];
+    hop_deltas(g, n, x, df, db);
+    hop_deltas(b, nb, x, bf, bb);
+    for (int k = 0; k < 8; ++k) {
+      int zf[4], zb[4];
+      for (int mu = 0; mu < 4; ++mu) {
+        const int s = (mu == 3) ? 1 : (((k >> mu) & 1) ? -1 : 1);
+        zf[mu] = (x[mu] + s + g.L[mu]) % g.L[mu];
+        zb[mu] = (x[mu] - s + g.L[mu]) % g.L[mu];
+      }
+      const int lf = zf[0] + L0 * (zf[1] + L1 * (zf[2] + L2 * zf[3]));
+      const int lb = zb[0] + L0 * (zb[1] + L1 * (zb[2] + L2 * zb[3]));
+      int of, ob;
+      corner_offsets(k, df, db, of, ob);
+      if (n + of != lf || n + ob != lb) { printf("corner mismatch n=%d k=%d (%dx%dx%dx%d)\n", n, k, L0, L1, L2, L3); return 1; }
+      corner_offsets(k, bf, bb, of, ob);
+      if (nb + of != blk_index(b, zf) || nb + ob != blk_index(b, zb)) {
+        printf("blocked corner mismatch n=%d k=%d (%dx%dx%dx%d)\n", n, k, L0, L1, L2, L3);
+        return 1;
+      }
+    }
+  }
+  // packed unit index: a bijection of (site, plane) onto [0, V npl)
+  for (int npl : {3, 6, 12, 24, 36, 72}) {
+    std::vector<char> hit((size_t)g.V * npl, 0);
+    for (int n = 0; n < g.V; ++n)
+      for (int c = 0; c < npl; ++c) {
+        const size_t i = pk(n, npl, c);
+        if (i >= hit.size() || hit[i]++) { printf("packed index clash npl=%d n=%d c=%d\n", npl, n, c); return 1; }
       }
   }
   return 0;

@@ -126,20 +126,24 @@ def test_wilson_general_r(sw):
 
 def test_edge_cases(sw):
     P = Problem(sw, (2, 2, 2, 2), sw.SW_OP_STAGGERED_WILSON, 1, 0.3, 0.1)
-    # zero source: x = 0 exactly, even from a non-zero guess
+    # zero source: x = 0 exactly, even from a non-zero guess (FP64 and the
+    # mixed modes, whose right-hand side comes from the inner-precision operator)
     zero = np.zeros(P.lat.volume * 3, dtype=np.complex128)
-    x, info = P.solve(sw, zero, 1e-8, 0, x0=np.ones_like(zero))
-    assert info.status == sw.SW_OK and np.all(x == 0)
+    for prec in (0, 1, 2):
+        x, info = P.solve(sw, zero, 1e-8, prec, x0=np.ones_like(zero))
+        assert info.status == sw.SW_OK and np.all(x == 0)
     # max_iter reached: status SW_NOT_CONVERGED, true residual reported
     P4 = Problem(sw, (4, 4, 4, 4), sw.SW_OP_WILSON, 0, 0.3, 0.01)
     chi = ls.point_source(P4.dims, 12, 0).reshape(-1)
     x, info = P4.solve(sw, chi, 1e-10, 0, max_iter=3)
     assert info.status == sw.SW_NOT_CONVERGED and info.iters == 3
     assert abs(info.true_rel_resid - P4.true_resid(chi, x)) < 1e-6
-    # the guess is used: starting from the solution needs no iteration
+    # the guess is used: starting from the solution needs no iteration (the
+    # FP64 residual of the guess decides, in every precision mode)
     xs, _ = P4.solve(sw, chi, 1e-9, 0)
-    _, info = P4.solve(sw, chi, 1e-8, 0, x0=xs)
-    assert info.status == sw.SW_OK and info.iters == 0
+    for prec in (0, 1, 2):
+        _, info = P4.solve(sw, chi, 1e-8, prec, x0=xs)
+        assert info.status == sw.SW_OK and info.iters == 0 and info.true_rel_resid <= 1e-8
     # a NaN source is reported, not iterated on
     bad = chi.copy()
     bad[5] = np.nan
