@@ -220,7 +220,11 @@ int sw_autotune(const sw_lattice* lat, int op, const void* U, const void* W, int
  * recomputation) and "<operator>.rhs.f64": they are bound by the FP64 units,
  * so they carry flops -- the paper's count per site and application (Eq. 4:
  * 1743 staggered Wilson, 1392 Wilson) times sites, applications and the
- * systems the launch computed -- and bytes 0.
+ * systems the launch computed -- and bytes 0.  The stencil classes carry the
+ * same flop count besides their bytes.  Every launch of a class while
+ * profiling is enabled -- timed or not, graph replays included -- is counted
+ * as "issued" (sw_profile_issued), so the time a class takes in a solve is
+ * its mean time per timed launch times its issued launches.
  * Process-wide and thread-safe; disabled by default. */
 int sw_profile_enable(int on);
 /* Total kernel launches this library has issued in the process (always on). */
@@ -232,6 +236,10 @@ int sw_profile_count(void);
  * HOST pointers (each may be NULL).  Returns SW_ERR_ARG for a bad index. */
 int sw_profile_entry(int i, char* name, int name_len, long long* launches, double* total_ms,
                      double* total_bytes, double* total_flops);
+/* Class i: launches issued while profiling was enabled (timed or not) into
+ * *issued (HOST).  Returns SW_ERR_ARG for a bad index, SW_ERR_NULL for a
+ * NULL pointer. */
+int sw_profile_issued(int i, long long* issued);
 
 /* ---- Continuous-batching solve server -------------------------------------
  * Serving counterpart of the batched solve: gauge fields stay resident on the

@@ -214,7 +214,8 @@ def sw_profile_reset():
 
 
 def sw_profile_read():
-    """{class: {"launches", "ms", "bytes", "flops"}} accumulated since the last reset."""
+    """{class: {"launches", "ms", "bytes", "flops", "issued"}} accumulated since the last reset
+    (launches, ms, bytes, flops: the timed launches; issued: every launch while enabled)."""
     out = {}
     L = lib()
     for i in range(L.sw_profile_count()):
@@ -222,7 +223,10 @@ def sw_profile_read():
         n, ms, by, fl = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(L.sw_profile_entry(i, name, 64, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by),
                                   ctypes.byref(fl)), "sw_profile_entry")
-        out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "bytes": by.value, "flops": fl.value}
+        iss = ctypes.c_longlong()
+        _check(L.sw_profile_issued(i, ctypes.byref(iss)), "sw_profile_issued")
+        out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "bytes": by.value, "flops": fl.value,
+                                    "issued": iss.value}
     return out
 
 

@@ -30,6 +30,7 @@ int sm_count() {
 namespace {
 struct ProfStat {
   long long launches = 0;
+  long long issued = 0;
   double ms = 0.0;
   double bytes = 0.0;
   double flops = 0.0;
@@ -86,6 +87,11 @@ cudaEvent_t prof_event() {
 
 void prof_push(const char* cls, cudaEvent_t a, cudaEvent_t b, double bytes, double flops) {
   t_staged.push_back(Pending{cls, a, b, bytes, flops});
+}
+
+void prof_count(const char* cls, long long n) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_prof_on) g_prof[cls].issued += n;
 }
 
 void prof_commit(bool keep) {
@@ -262,6 +268,16 @@ int sw_profile_enable(int on) {
 int sw_profile_reset(void) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   g_prof.clear();
+  return SW_OK;
+}
+
+int sw_profile_issued(int i, long long* issued) {
+  if (!issued) return SW_ERR_NULL;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (i < 0 || i >= (int)g_prof.size()) return SW_ERR_ARG;
+  auto it = g_prof.begin();
+  std::advance(it, i);
+  *issued = it->second.issued;
   return SW_OK;
 }
 

@@ -39,18 +39,17 @@ bool param_site_blocking();  // blocked site order for the packed FP32/FP16 stor
 bool param_group_fast();     // system groups as the fastest grid dimension of the stencils
 bool param_graphs();   // replay chunks of iterations as captured CUDA graphs
 
-inline int grid_for(const void* kernel, int block, int V, int nsys, int cap, size_t smem = 0) {
+inline int grid_for(const void* kernel, int block, int V, int nsys, int cap) {
   static std::mutex mu;
-  static std::unordered_map<const void*, std::unordered_map<size_t, int>> cache;
+  static std::unordered_map<const void*, int> cache;
   int nb;
   {
     std::lock_guard<std::mutex> lk(mu);
-    auto& per = cache[kernel];
-    auto it = per.find(smem);
-    if (it == per.end()) {
+    auto it = cache.find(kernel);
+    if (it == cache.end()) {
       nb = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem) != cudaSuccess || nb < 1) nb = 1;
-      per[smem] = nb;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, 0) != cudaSuccess || nb < 1) nb = 1;
+      cache[kernel] = nb;
     } else {
       nb = it->second;
     }
@@ -290,13 +289,7 @@ class Engine {
     bp_ = BatchParams{r, n_, n_, vunits_};
     ns_ = MIXED ? param_ns(NC) : 1;
     ngrp_ = (cap + ns_ - 1) / ns_;
-    gA_ = grid_for((const void*)apply_kernel<double, OpD>, kTile, g.V, cap, pstride_);
-    gR_ = grid_for((const void*)residual64<OpD>, kTile, g.V, cap, pstride_);
-    gV_ = grid_for((const void*)cg_k3<TF, VR, VF, NC>, 256, g.V, cap, pstride_);
-    gN_ = grid_for((const void*)norm_b<NC>, kTile, g.V, cap, pstride_);
-    if constexpr (MIXED) gH_ = grid_for((const void*)rhs_lo<TF, OpF, VR, GK>, kTile, g.V, cap, pstride_);
-    g1_ = grid_for(k1_ptr(), kTile, g.V, ngrp_, pstride_);
-    g2_ = grid_for(k2_ptr(), kTile, g.V, ngrp_, pstride_);
+    set_grids(ngrp_);
     if constexpr (MIXED) {
       fr_ = VR{ws.r32, g.V};
       fx_ = VR{ws.x32, g.V};
@@ -336,6 +329,24 @@ class Engine {
     return &fsamples_.back();
   }
 
+  // Profiler class names: "<operator>.<kernel>.<precision>".
+  static const char* cls_k1() {
+    static const std::string c = std::string(OpF::kName) + ".k1." + OpF::kPrec;
+    return c.c_str();
+  }
+  static const char* cls_k2() {
+    static const std::string c = std::string(OpF::kName) + ".k2." + OpF::kPrec;
+    return c.c_str();
+  }
+  static const char* cls_ru() {
+    static const std::string c = std::string(OpD::kName) + ".ru.f64";
+    return c.c_str();
+  }
+  static const char* cls_rhs() {
+    static const std::string c = std::string(OpD::kName) + ".rhs.f64";
+    return c.c_str();
+  }
+
   // Turn the sampled launches into profiler records (after the stream is idle).
   void flush_profile() {
     flush_fp_samples();
@@ -351,14 +362,12 @@ class Engine {
     const double gauge = (double)g_.V * OpF::kGaugeBytes;
     const double pv = (double)sizeof(typename VF::unit) * vunits_;
     const double rv = (double)sizeof(typename VR::unit) * n_;
-    static const std::string c1 = std::string(OpF::kName) + ".k1." + OpF::kPrec;
-    static const std::string c2 = std::string(OpF::kName) + ".k2." + OpF::kPrec;
     // flops: the paper's count per site and application (Eq. 4) for every
     // computed system (k2's x, r updates are not counted)
     const double fl = OpF::kFlops * g_.V;
     for (size_t k = 0; k < samples_.size(); ++k) {
-      prof_push(c1.c_str(), samples_[k].e0, samples_[k].e1, gauge + cnt[2 * k] * 2.0 * pv, fl * cnt[2 * k]);
-      prof_push(c2.c_str(), samples_[k].e1, samples_[k].e2, gauge + cnt[2 * k + 1] * (2.0 * pv + 4.0 * rv),
+      prof_push(cls_k1(), samples_[k].e0, samples_[k].e1, gauge + cnt[2 * k] * 2.0 * pv, fl * cnt[2 * k]);
+      prof_push(cls_k2(), samples_[k].e1, samples_[k].e2, gauge + cnt[2 * k + 1] * (2.0 * pv + 4.0 * rv),
                 fl * cnt[2 * k + 1]);
     }
     prof_commit(true);
@@ -367,7 +376,7 @@ class Engine {
   }
 
   ~Engine() {
-    if (gexec_) cudaGraphExecDestroy(gexec_);
+    for (auto& ge : gexecs_) cudaGraphExecDestroy(ge.second);
   }
   Engine(const Engine&) = delete;
   Engine& operator=(const Engine&) = delete;
@@ -399,34 +408,49 @@ class Engine {
   void issue() {
     SysState* S = ws_.S;
     bool ru = need_ru_;
+    // Grids of the launches that compute only some slots (admission, reliable
+    // updates) are sized for the slots they compute, not for the engine's
+    // capacity: the blocks of the other slots return at once, and a launch
+    // sized for all slots would leave the SMs nearly empty (the FP64
+    // matvecs need full occupancy to keep the FP64 pipe busy).
+    int n_ru = need_ru_ ? nneed_ : 0;
     if (!staged_.empty()) {
+      const int na = (int)staged_.size();
+      n_ru += na;  // admitted systems with a guess x0 != 0 take an FP64 residual now
       upload_staged();
       using PU = typename VF::unit;
-      admit_clear<PU><<<dim3(gV_, cap_), 256, 0, st_>>>(vunits_, static_cast<PU*>(ws_.p_lo), vunits_,
-                                                         MIXED ? ws_.x32 : nullptr, MIXED ? n_ : 0, S);
+      const int gv = grid_of((const void*)admit_clear<PU>, 256, na);
+      admit_clear<PU><<<dim3(gv, cap_), 256, 0, st_>>>(vunits_, static_cast<PU*>(ws_.p_lo), vunits_,
+                                                       MIXED ? ws_.x32 : nullptr, MIXED ? n_ : 0, S);
+      const int gn = grid_of((const void*)norm_b<NC>, kTile, na);
       if constexpr (MIXED) {
         // b = (D+m)^+ chi in the inner precision: r = p = b and |b|^2
-        demote_chi<NC, VF><<<dim3(gV_, cap_), 256, 0, st_>>>(gb_, chi_, ft_, n_, vunits_, S);
-        rhs_lo<TF, OpF, VR, GK><<<dim3(gH_, cap_), kTile, 0, st_>>>(gk_, opf_, ft_, fp_, fr_, bp_, S, rb_);
-        norm_b<NC><<<dim3(gN_, cap_), kTile, 0, st_>>>(g_.V, nullptr, x_, n_, S, rb_);
-        admit_vectors<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, nullptr, n_, S);
+        demote_chi<NC, VF><<<dim3(grid_of((const void*)demote_chi<NC, VF>, 256, na), cap_), 256, 0, st_>>>(
+            gb_, chi_, ft_, n_, vunits_, S);
+        rhs_lo<TF, OpF, VR, GK><<<dim3(grid_of((const void*)rhs_lo<TF, OpF, VR, GK>, kTile, na), cap_), kTile, 0,
+                                  st_>>>(gk_, opf_, ft_, fp_, fr_, bp_, S, rb_);
+        norm_b<NC><<<dim3(gn, cap_), kTile, 0, st_>>>(g_.V, nullptr, x_, n_, S, rb_);
+        admit_vectors<NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, nullptr, n_, S);
         note_launches(1);
       } else {
         FpSample* fs = fp_sample(1);
-        apply_kernel<double, OpD><<<dim3(gA_, cap_), kTile, 0, st_>>>(g_, opd_, V64{chi_}, V64{ws_.b64}, 0.0, n_,
-                                                                      r_, 1, S, ST_ADMIT, fs ? fs->cnt : nullptr);
+        if (prof_enabled()) prof_count(cls_rhs(), 1);
+        apply_kernel<double, OpD><<<dim3(grid_of((const void*)apply_kernel<double, OpD>, kTile, na), cap_), kTile,
+                                    0, st_>>>(g_, opd_, V64{chi_}, V64{ws_.b64}, 0.0, n_, r_, 1, S, ST_ADMIT,
+                                              fs ? fs->cnt : nullptr);
         if (fs) cudaEventRecord(fs->e1, st_);
-        norm_b<NC><<<dim3(gN_, cap_), kTile, 0, st_>>>(g_.V, ws_.b64, x_, n_, S, rb_);
-        admit_vectors<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, ws_.b64, n_, S);
+        norm_b<NC><<<dim3(gn, cap_), kTile, 0, st_>>>(g_.V, ws_.b64, x_, n_, S, rb_);
+        admit_vectors<NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, ws_.b64, n_, S);
       }
       admit_states<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S, MIXED ? 1 : 0);
       note_launches(5);
       ru = true;
     }
-    if (ru) reliable_update();
+    if (ru) reliable_update(n_ru);
     // After reliable updates with nothing known to be running, read the
     // statuses first rather than launch a chunk that may find nothing to do.
     if (!ru || nrun_ > 0) {
+      size_for_live();
       // every 4th chunk is timed when profiling, on its second iteration: by
       // then the queue is full, so the events time the kernels rather than the
       // host's launch latency
@@ -454,9 +478,11 @@ class Engine {
     if (const cudaError_t l = cudaGetLastError(); l != cudaSuccess) return cuda_fail(l);
     int active = 0, nrun = 0;
     need_ru_ = false;
+    nneed_ = 0;
     for (int i = 0; i < cap_; ++i) {
       const int s = hr_[i].status;
       need_ru_ |= (s == ST_NEED_RU);
+      nneed_ += (s == ST_NEED_RU);
       nrun += (s == ST_RUNNING);
       active += (s == ST_RUNNING || s == ST_NEED_RU || s == ST_JUST_UPDATED || s == ST_ADMIT ||
                  s == ST_ZERO_B || s == ST_ZERO_GUESS);
@@ -493,46 +519,89 @@ class Engine {
     staged_.clear();
   }
 
-  void reliable_update() {
+  // nsys: the slots (at most) that take the update this round, for the grids.
+  void reliable_update(int nsys) {
     SysState* S = ws_.S;
-    if constexpr (MIXED) accum_x<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(gb_, x_, ws_.x32, n_, n_, S);
+    const int gv = grid_of((const void*)cg_k3<TF, VR, VF, NC>, 256, nsys);
+    if constexpr (MIXED) accum_x<NC><<<dim3(gv, cap_), 256, 0, st_>>>(gb_, x_, ws_.x32, n_, n_, S);
     FpSample* fs = fp_sample(2);
+    if (prof_enabled()) prof_count(cls_ru(), 1);
     // r = (D+m)^+ (chi - (D+m) x) = b - A x, all in FP64
-    apply_kernel<double, OpD><<<dim3(gA_, cap_), kTile, 0, st_>>>(g_, opd_, V64{x_}, V64{ws_.t64}, 0.0, n_, r_, 0,
-                                                                  S, ST_NEED_RU, fs ? fs->cnt : nullptr,
-                                                                  V64{chi_}, 1);
-    residual64<OpD><<<dim3(gR_, cap_), kTile, 0, st_>>>(g_, opd_, V64{ws_.t64}, V64{ws_.r64}, bp_, S, rb_);
+    apply_kernel<double, OpD><<<dim3(grid_of((const void*)apply_kernel<double, OpD>, kTile, nsys), cap_), kTile, 0,
+                                st_>>>(g_, opd_, V64{x_}, V64{ws_.t64}, 0.0, n_, r_, 0, S, ST_NEED_RU,
+                                       fs ? fs->cnt : nullptr, V64{chi_}, 1);
+    residual64<OpD><<<dim3(grid_of((const void*)residual64<OpD>, kTile, nsys), cap_), kTile, 0, st_>>>(
+        g_, opd_, V64{ws_.t64}, V64{ws_.r64}, bp_, S, rb_);
     if (fs) cudaEventRecord(fs->e1, st_);
-    if constexpr (MIXED) demote_r<NC><<<dim3(gV_, cap_), 256, 0, st_>>>(gb_, ws_.r64, ws_.r32, n_, n_, S);
-    cg_k3<TF, VR, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, vunits_, S, ST_JUST_UPDATED);
+    if constexpr (MIXED) demote_r<NC><<<dim3(gv, cap_), 256, 0, st_>>>(gb_, ws_.r64, ws_.r32, n_, n_, S);
+    cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, vunits_, S, ST_JUST_UPDATED);
     commit_status<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S);
     note_launches(MIXED ? 6 : 4);
   }
 
   // One chunk of iterations as a CUDA graph, captured on first use: every
   // kernel argument is fixed for the engine's life, so the graph is replayed.
+  // One graph per grid class (see size_for_live), captured on first use.
   void launch_chunk_graph() {
-    if (!gexec_ && !graph_failed_) {
+    cudaGraphExec_t ge = nullptr;
+    for (auto& g : gexecs_)
+      if (g.first == cls_) ge = g.second;
+    if (!ge && !graph_failed_) {
       cudaGraph_t graph = nullptr;
       bool ok = cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
       if (ok) {
         for (int i = 0; i < chunk_; ++i) iterate(false, false);
         ok = cudaStreamEndCapture(st_, &graph) == cudaSuccess && graph;
       }
-      ok = ok && cudaGraphInstantiate(&gexec_, graph, 0) == cudaSuccess;
+      ok = ok && cudaGraphInstantiate(&ge, graph, 0) == cudaSuccess;
       if (graph) cudaGraphDestroy(graph);
       if (!ok) {
         cudaGetLastError();
-        gexec_ = nullptr;
+        ge = nullptr;
         graph_failed_ = true;
+      } else {
+        gexecs_.push_back({cls_, ge});
       }
     }
-    if (gexec_) {
-      cudaGraphLaunch(gexec_, st_);
+    if (ge) {
+      cudaGraphLaunch(ge, st_);
       note_launches(3 * chunk_);
+      if (prof_enabled()) {
+        prof_count(cls_k1(), chunk_);
+        prof_count(cls_k2(), chunk_);
+      }
     } else {
       for (int i = 0; i < chunk_; ++i) iterate(false);
     }
+  }
+
+  // Grids of the iteration kernels for `groups` groups of ns_ slots that may
+  // run (blocks of stopped slots return at once).
+  void set_grids(int groups) {
+    cls_ = groups;
+    g1_ = grid_for(k1_ptr(), kTile, g_.V, groups, pstride_);
+    g2_ = grid_for(k2_ptr(), kTile, g_.V, groups, pstride_);
+    gV_ = grid_for((const void*)cg_k3<TF, VR, VF, NC>, 256, g_.V, groups * ns_, pstride_);
+  }
+
+  // Size the iteration grids for the groups holding a slot that may run in
+  // the next chunk, rounded up to a power of two (at most the engine's
+  // groups): as systems converge, the remaining ones keep the SMs full.  A
+  // system's arithmetic and reduction order do not depend on the grid.
+  void size_for_live() {
+    int live = 0;
+    for (int gi = 0; gi < ngrp_; ++gi) {
+      bool any = false;
+      for (int i = gi * ns_; i < cap_ && i < (gi + 1) * ns_; ++i) {
+        const int s = hr_[i].status;
+        any |= (s == ST_RUNNING || s == ST_NEED_RU || s == ST_JUST_UPDATED || s == ST_ADMIT || s == ST_ZERO_GUESS);
+      }
+      live += any;
+    }
+    int cls = 1;
+    while (cls < live) cls *= 2;
+    if (cls > ngrp_) cls = ngrp_;
+    if (cls != cls_) set_grids(cls);
   }
 
   void flush_fp_samples() {
@@ -542,12 +611,10 @@ class Engine {
       cudaGetLastError();
       return;
     }
-    static const std::string cr = std::string(OpD::kName) + ".ru.f64";
-    static const std::string cb = std::string(OpD::kName) + ".rhs.f64";
     for (size_t k = 0; k < fsamples_.size(); ++k) {
       const FpSample& f = fsamples_[k];
       const int systems = cnt[2 * kProfSlots - 1 - k];
-      prof_push(f.apps == 2 ? cr.c_str() : cb.c_str(), f.e0, f.e1, 0.0,
+      prof_push(f.apps == 2 ? cls_ru() : cls_rhs(), f.e0, f.e1, 0.0,
                 OpD::kFlops * g_.V * f.apps * systems);
     }
     prof_commit(true);
@@ -602,7 +669,13 @@ class Engine {
     }
     if (sample) cudaEventRecord(samples_.back().e2, st_);
     cg_k3<TF, VR, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, vunits_, S, ST_RUNNING);
-    if (count) note_launches(3);
+    if (count) {
+      note_launches(3);
+      if (prof_enabled()) {
+        prof_count(cls_k1(), 1);
+        prof_count(cls_k2(), 1);
+      }
+    }
   }
 
   struct Sample {
@@ -623,7 +696,7 @@ class Engine {
   cudaStream_t st_;
   cudaEvent_t ev_;
   size_t n_;
-  int pstride_ = 0, ngrp_ = 0, gA_ = 0, gR_ = 0, gV_ = 0, gN_ = 0, gH_ = 0, g1_ = 0, g2_ = 0;
+  int pstride_ = 0, ngrp_ = 0, gV_ = 0, g1_ = 0, g2_ = 0;
   RedBuf rb_{};
   BatchParams bp_{};
   VF fp_{}, ft_{};
@@ -632,12 +705,19 @@ class Engine {
   int chunk_ = 16;
   double delta_ = 0.1;
   bool need_ru_ = false;
+  int nneed_ = 0;  // slots in NEED_RU at the last status read
+
+  // Blocks per slot of a launch that computes `nsys` of the engine's slots.
+  int grid_of(const void* kernel, int block, int nsys) const {
+    return grid_for(kernel, block, g_.V, nsys < 1 ? 1 : (nsys > cap_ ? cap_ : nsys), pstride_);
+  }
   int nrun_ = 0, ns_ = 1, gfast_ = 0;
   std::vector<Sample> samples_;
   std::vector<FpSample> fsamples_;
   long long rounds_ = 0, chunks_ = 0;
   bool use_graphs_ = true, graph_failed_ = false;
-  cudaGraphExec_t gexec_ = nullptr;
+  int cls_ = 0;  // groups the iteration grids are sized for
+  std::vector<std::pair<int, cudaGraphExec_t>> gexecs_;
   std::vector<int> staged_;
   std::vector<char> reported_;
 };

@@ -54,6 +54,8 @@ void prof_push(const char* cls, cudaEvent_t a, cudaEvent_t b, double bytes, doub
 void prof_flush();
 // Keep (or drop) the samples pushed since the last commit.
 void prof_commit(bool keep);
+// Count n launches of a class as issued (while profiling is enabled).
+void prof_count(const char* cls, long long n);
 // Kernel launches issued by the library (all entry points), for the caller's accounting.
 void note_launches(int k);
 // Record the CUDA error behind an SW_ERR_CUDA return (sw_last_cuda_error).
