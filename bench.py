@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -56,11 +57,11 @@ ITERS_TABLE = {"sw": {0.02: 41.0, 0.05: 39.0, 0.1: 36.9, 0.2: 32.0},
 # with the systems computed).  Entries are removed when the kernel changes.
 NCU_TRAFFIC = {
     # profiles/ncu_sw_k1k2_fp32_16x16x16x32_12sys.md
-    "sw.k1.f32": {"bytes": 209.9e6, "algorithmic": 188.7e6, "systems": 12},
-    "sw.k2.f32": {"bytes": 366.0e6, "algorithmic": 339.7e6, "systems": 12},
+    "sw.k1.f32": {"bytes": 198.4e6, "algorithmic": 188.7e6, "systems": 12},
+    "sw.k2.f32": {"bytes": 348.8e6, "algorithmic": 339.7e6, "systems": 12},
     # profiles/ncu_wilson_k1k2_fp32_16x16x16x32_12sys.md
-    "wilson.k1.f32": {"bytes": 325.4e6, "algorithmic": 339.7e6, "systems": 12},
-    "wilson.k2.f32": {"bytes": 945.1e6, "algorithmic": 943.7e6, "systems": 12},
+    "wilson.k1.f32": {"bytes": 319.5e6, "algorithmic": 339.7e6, "systems": 12},
+    "wilson.k2.f32": {"bytes": 939.8e6, "algorithmic": 943.7e6, "systems": 12},
 }
 
 # FP64 peak of a GB300 (nominal 1.25 TFLOP/s; not in the measured-peaks file):
@@ -92,6 +93,9 @@ def parse():
     ap.add_argument("--graphs", type=int, default=None, help="1/0: replay chunks as CUDA graphs (library default 1)")
     ap.add_argument("--site-blocking", type=int, default=None, help="1/0: blocked site order of packed fields")
     ap.add_argument("--group-fast", type=int, default=None, help="1/0: system groups fastest in the stencil grid")
+    ap.add_argument("--concurrent-ops", action="store_true",
+                    help="solve the staggered Wilson and Wilson batches at the same time, each on its own stream "
+                         "and host thread (the per-kernel event timings then include the other batch's kernels)")
     ap.add_argument("--ops", choices=["both", "sw", "wilson"], default="both",
                     help="operators of a step (the large-volume runs take one per lattice)")
     ap.add_argument("--sources", default="point",
@@ -314,18 +318,50 @@ def run_ours(args):
     x_w = torch.empty_like(chi_w)
     stream = torch.cuda.current_stream(dev)
 
+    # The staggered Wilson batch (its FP64 hypercube build and reliable
+    # updates are bound by the FP64 pipe) and the Wilson batch (bound by HBM)
+    # are independent.  By default they run one after the other, so that the
+    # kernel timings of the roofline report are those of each kernel alone;
+    # with --concurrent-ops they run at once, each on its own stream from its
+    # own host thread (the library's entry points are thread-safe).
+    stream_sw = torch.cuda.Stream(dev) if (args.ops == "both" and args.concurrent_ops) else stream
+    ev_start, ev_sw = torch.cuda.Event(), torch.cuda.Event()
+
     def step(seed, Ud, csw, cw, xsw, xw, precision=None):
         pr = prec if precision is None else precision
-        inf_sw, inf_w = [], []
+        res = {"sw": [], "w": []}
+
+        def solve_sw():
+            try:
+                stream_sw.wait_event(ev_start)
+                with torch.cuda.stream(stream_sw):
+                    sw.sw_hypercube_build(dims, Ud, W, stream=stream_sw)
+                    xsw.zero_()
+                    rc1, res["sw"] = sw.cgne_solve_batch(dims, sw.SW_OP_STAGGERED_WILSON, Ud, W, csw, xsw, m_sw,
+                                                         1.0, TOL, 100000, pr, stream=stream_sw)
+                ev_sw.record(stream_sw)
+            except BaseException as exc:  # re-raised by the caller after the join
+                res["err"] = exc
+
+        ev_start.record(stream)
+        th = None
         if args.ops in ("both", "sw"):
-            sw.sw_hypercube_build(dims, Ud, W, stream=stream)
-            xsw.zero_()
-            rc1, inf_sw = sw.cgne_solve_batch(dims, sw.SW_OP_STAGGERED_WILSON, Ud, W, csw, xsw, m_sw, 1.0, TOL,
-                                              100000, pr, stream=stream)
+            if stream_sw is stream:
+                solve_sw()
+            else:
+                th = threading.Thread(target=solve_sw)
+                th.start()
         if args.ops in ("both", "wilson"):
             xw.zero_()
-            rc2, inf_w = sw.cgne_solve_batch(dims, sw.SW_OP_WILSON, Ud, None, cw, xw, m_w, R_WILSON, TOL, 100000,
-                                             pr, stream=stream)
+            rc2, res["w"] = sw.cgne_solve_batch(dims, sw.SW_OP_WILSON, Ud, None, cw, xw, m_w, R_WILSON, TOL, 100000,
+                                                pr, stream=stream)
+        if th is not None:
+            th.join()
+        if "err" in res:
+            raise res["err"]
+        if args.ops in ("both", "sw"):
+            stream.wait_event(ev_sw)
+        inf_sw, inf_w = res["sw"], res["w"]
         for inf in inf_sw + inf_w:
             if inf.status != sw.SW_OK or not (inf.true_rel_resid <= TOL):
                 raise RuntimeError(f"solve failed: {inf}")
@@ -486,7 +522,9 @@ def run_ours(args):
                    "systems_per_thread": {"sw": int(sw.sw_get_param(sw.SW_PARAM_NS_SW)),
                                           "wilson": int(sw.sw_get_param(sw.SW_PARAM_NS_WILSON))},
                    "l2": "inputs larger than L2: a step touches ~10 GB and each step uses a new configuration",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "operator_batches": ("concurrent, one stream and host thread each"
+                                        if (args.concurrent_ops and args.ops == "both") else "one after the other")},
         "clocks": ck, "gpu_launches": int(launches), "roofline": roof, "roofline_hbm_top": roof_hbm,
         "kernels": kernels,
         "latency_ms": {"p50": round(float(np.percentile(lats, 50)), 2),

@@ -159,8 +159,10 @@ int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, const void*
 
 /* Solver tunables (process-wide, read at the start of each solve).
  * SW_PARAM_CHUNK: CG iterations launched between two reads of the per-system
- *   status words (1..4096, default 16).  Larger chunks mean fewer host
- *   synchronisations; converged systems idle for at most one chunk.
+ *   status words (1..4096, default 4).  Larger chunks mean fewer host
+ *   synchronisations; converged systems idle for at most one chunk, and a
+ *   system whose reliable update ran beside a chunk resumes at an iteration
+ *   boundary within it.
  * SW_PARAM_RELIABLE_DELTA: mixed precision only; the FP32 correction is
  *   folded into the FP64 solution and r = b - A x recomputed in FP64 when the
  *   iterated |r| falls below delta times its maximum since the last such

@@ -47,7 +47,7 @@ std::map<std::string, ProfStat> g_prof;
 std::vector<cudaEvent_t> g_pool;
 thread_local std::vector<Pending> t_pending;
 thread_local std::vector<Pending> t_staged;
-std::atomic<int> g_param_chunk{16};
+std::atomic<int> g_param_chunk{4};
 std::atomic<double> g_param_delta{3e-5};
 std::atomic<double> g_param_delta16{1e-3};
 std::atomic<int> g_param_ns_sw{2};

@@ -33,7 +33,9 @@ enum SysStatus : int {
   ST_IDLE = 6,          // slot without a system
   ST_ADMIT = 7,         // slot being set up: b = (D+m)^+ chi, norms
   ST_ZERO_B = 8,        // admitted with b = 0: solution x = 0
-  ST_ZERO_GUESS = 9     // admitted with x0 = 0: r = b, no matvec needed
+  ST_ZERO_GUESS = 9,    // admitted with x0 = 0: r = b, no matvec needed
+  ST_RU_PENDING = 10,   // taken into this round's reliable update (from NEED_RU)
+  ST_READY = 11         // residual replaced and p refreshed: runs from the next iteration
 };
 
 struct SysState {
@@ -448,6 +450,12 @@ __global__ void __launch_bounds__(256) cg_k3(int V, RVec r, PVec p, size_t rstri
 }
 
 // ---------------------------------------------------------------- FP64 residual (reliable update)
+// A reliable update acts on the systems in ST_RU_PENDING (marked from
+// ST_NEED_RU by the host's round, so that iterations running at the same time
+// on another stream -- which may move other systems to ST_NEED_RU -- cannot
+// change the set while the update's kernels run).  It ends in ST_READY;
+// commit_ready, launched on the iteration stream at an iteration boundary,
+// lets the system run again.
 // r64 = (D+m)^+ t64 with t64 = chi - (D+m) x (apply_kernel's has_sub form), so
 // r64 = b - A x for b = (D+m)^+ chi; |r64|^2, then the convergence decision.
 template <typename Op>
@@ -456,7 +464,7 @@ __global__ void __launch_bounds__(kTile) residual64(Geom g, Op op, typename Op::
   __shared__ double sm[32];
   __shared__ int last;
   const int sys = blockIdx.y;
-  if (S[sys].status != ST_NEED_RU) return;
+  if (S[sys].status != ST_RU_PENDING) return;
   if (nact && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nact, 1);
   t = sys_view(t, sys, bp.sstride64);
   r = sys_view(r, sys, bp.sstride64);

@@ -46,15 +46,34 @@ template <typename T> __device__ __forceinline__ V3<T> zero3() {
   return v;
 }
 
+// Complex multiply-accumulate a b into (re, im) with fused multiply-adds: 4
+// per complex product (written out because a product formed first and then
+// added costs 6: the compiler cannot fuse across the separate addition).
+template <typename T> __device__ __forceinline__ void cmac(T& re, T& im, cx<T> a, cx<T> b) {
+  re = fma(a.re, b.re, re);
+  re = fma(-a.im, b.im, re);
+  im = fma(a.re, b.im, im);
+  im = fma(a.im, b.re, im);
+}
+// conj(a) b accumulated
+template <typename T> __device__ __forceinline__ void cjmac(T& re, T& im, cx<T> a, cx<T> b) {
+  re = fma(a.re, b.re, re);
+  re = fma(a.im, b.im, re);
+  im = fma(a.re, b.im, im);
+  im = fma(-a.im, b.re, im);
+}
+
 // M v
 template <typename T> __device__ __forceinline__ V3<T> mv(const M3<T>& M, const V3<T>& v) {
   V3<T> o;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    cx<T> s = cmul(M.e[i][0], v.c[0]);
-    s = s + cmul(M.e[i][1], v.c[1]);
-    s = s + cmul(M.e[i][2], v.c[2]);
-    o.c[i] = s;
+    T re = M.e[i][0].re * v.c[0].re, im = M.e[i][0].re * v.c[0].im;
+    re = fma(-M.e[i][0].im, v.c[0].im, re);
+    im = fma(M.e[i][0].im, v.c[0].re, im);
+    cmac(re, im, M.e[i][1], v.c[1]);
+    cmac(re, im, M.e[i][2], v.c[2]);
+    o.c[i] = {re, im};
   }
   return o;
 }
@@ -63,10 +82,12 @@ template <typename T> __device__ __forceinline__ V3<T> mdv(const M3<T>& M, const
   V3<T> o;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    cx<T> s = cjmul(M.e[0][i], v.c[0]);
-    s = s + cjmul(M.e[1][i], v.c[1]);
-    s = s + cjmul(M.e[2][i], v.c[2]);
-    o.c[i] = s;
+    T re = M.e[0][i].re * v.c[0].re, im = M.e[0][i].re * v.c[0].im;
+    re = fma(M.e[0][i].im, v.c[0].im, re);
+    im = fma(-M.e[0][i].im, v.c[0].re, im);
+    cjmac(re, im, M.e[1][i], v.c[1]);
+    cjmac(re, im, M.e[2][i], v.c[2]);
+    o.c[i] = {re, im};
   }
   return o;
 }
@@ -84,10 +105,12 @@ template <typename T> __device__ __forceinline__ M3<T> mm(const M3<T>& A, const 
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      cx<T> s = cmul(A.e[i][0], B.e[0][j]);
-      s = s + cmul(A.e[i][1], B.e[1][j]);
-      s = s + cmul(A.e[i][2], B.e[2][j]);
-      C.e[i][j] = s;
+      T re = A.e[i][0].re * B.e[0][j].re, im = A.e[i][0].re * B.e[0][j].im;
+      re = fma(-A.e[i][0].im, B.e[0][j].im, re);
+      im = fma(A.e[i][0].im, B.e[0][j].re, im);
+      cmac(re, im, A.e[i][1], B.e[1][j]);
+      cmac(re, im, A.e[i][2], B.e[2][j]);
+      C.e[i][j] = {re, im};
     }
   return C;
 }
@@ -374,8 +397,15 @@ struct GaugeP16 {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const int a = (j + 1) % 3, b = (j + 2) % 3;
-      const cx<float> c = cmul(M.e[0][a], M.e[1][b]) - cmul(M.e[0][b], M.e[1][a]);
-      M.e[2][j] = {c.re, -c.im};
+      // c = row0_a row1_b - row0_b row1_a, as fused multiply-adds
+      float re = M.e[0][a].re * M.e[1][b].re, im = M.e[0][a].re * M.e[1][b].im;
+      re = fma(-M.e[0][a].im, M.e[1][b].im, re);
+      im = fma(M.e[0][a].im, M.e[1][b].re, im);
+      re = fma(-M.e[0][b].re, M.e[1][a].re, re);
+      re = fma(M.e[0][b].im, M.e[1][a].im, re);
+      im = fma(-M.e[0][b].re, M.e[1][a].im, im);
+      im = fma(-M.e[0][b].im, M.e[1][a].re, im);
+      M.e[2][j] = {re, -im};
     }
     return M;
   }

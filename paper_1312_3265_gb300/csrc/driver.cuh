@@ -126,7 +126,7 @@ struct Workspace {
   float2 *r32, *x32;         // FP32 residual and correction (mixed precision only)
   SysState* S;
   double* partials;
-  unsigned* tickets;
+  unsigned* tickets;  // [2 nsys]: iteration kernels, then reliable-update kernels
   double* mass;
   double* hist;  // CG coefficients, [nsys][kHist][2]
   int* pcount;   // systems computed per sampled launch, [kProfSlots][2]
@@ -145,7 +145,7 @@ inline size_t workspace_bytes_pt(int V, int NC, int nsys, bool mixed, size_t pt)
   size_t b = (mixed ? 2 : 3) * align_up(sizeof(double2) * n);  // b64 only in FP64 mode
   b += mixed ? 2 * align_up(pt * nsys) + 2 * align_up(sizeof(float2) * n) : align_up(pt * nsys);
   b += align_up(sizeof(SysState) * nsys) + align_up(sizeof(double) * 2 * ntiles * nsys) +
-       align_up(sizeof(unsigned) * nsys) + align_up(sizeof(double) * nsys) +
+       align_up(sizeof(unsigned) * 2 * nsys) + align_up(sizeof(double) * nsys) +
        align_up(sizeof(double) * 2 * kHist * nsys) + align_up(sizeof(int) * 2 * kProfSlots);
   return b;
 }
@@ -181,7 +181,7 @@ inline Workspace carve_workspace_pt(void* base, int V, int NC, int nsys, bool mi
   }
   w.S = (SysState*)take(sizeof(SysState) * nsys);
   w.partials = (double*)take(sizeof(double) * 2 * ntiles * nsys);  // 2nd half: norm_b's |x0|^2
-  w.tickets = (unsigned*)take(sizeof(unsigned) * nsys);
+  w.tickets = (unsigned*)take(sizeof(unsigned) * 2 * nsys);  // 2nd half: the reliable-update kernels
   w.mass = (double*)take(sizeof(double) * nsys);
   w.hist = (double*)take(sizeof(double) * 2 * kHist * nsys);
   w.pcount = (int*)take(sizeof(int) * 2 * kProfSlots);
@@ -285,6 +285,9 @@ class Engine {
     else gk_ = g;
     gfast_ = param_group_fast() ? 1 : 0;
     rb_ = RedBuf{ws.partials, ws.tickets, pstride_, ws.hist};
+    // the reliable-update kernels may run while iterations of other systems
+    // run on the side: their own block tickets (per system, not per group)
+    rbu_ = RedBuf{ws.partials, ws.tickets + cap, pstride_, ws.hist};
     vunits_ = VF::sys_units(g.V);
     bp_ = BatchParams{r, n_, n_, vunits_};
     ns_ = MIXED ? param_ns(NC) : 1;
@@ -307,7 +310,15 @@ class Engine {
       z.status = ST_IDLE;
       hr_[i] = z;
     }
-    cudaMemsetAsync(ws.tickets, 0, sizeof(unsigned) * cap, st);
+    cudaMemsetAsync(ws.tickets, 0, sizeof(unsigned) * 2 * cap, st);
+    if (use_graphs_) {  // callers that allow driver resources get the overlapped reliable update
+      if (cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        side_ = nullptr;
+      }
+    }
     cudaMemsetAsync(ws.pcount, 0, sizeof(int) * 2 * kProfSlots, st);
     cudaMemcpyAsync(ws.S, hr_, sizeof(SysState) * cap, cudaMemcpyHostToDevice, st);
     chunk_ = param_chunk();
@@ -321,10 +332,10 @@ class Engine {
     int* cnt;
     int apps;
   };
-  FpSample* fp_sample(int apps) {
+  FpSample* fp_sample(int apps, cudaStream_t sx) {
     if (!prof_enabled() || fsamples_.size() >= (size_t)kProfSlots / 2) return nullptr;
     FpSample f{prof_event(), prof_event(), ws_.pcount + 2 * kProfSlots - 1 - fsamples_.size(), apps};
-    cudaEventRecord(f.e0, st_);
+    cudaEventRecord(f.e0, sx);
     fsamples_.push_back(f);
     return &fsamples_.back();
   }
@@ -377,6 +388,12 @@ class Engine {
 
   ~Engine() {
     for (auto& ge : gexecs_) cudaGraphExecDestroy(ge.second);
+    if (side_) {
+      cudaStreamSynchronize(side_);
+      cudaStreamDestroy(side_);
+    }
+    if (ev_fork_) cudaEventDestroy(ev_fork_);
+    if (ev_join_) cudaEventDestroy(ev_join_);
   }
   Engine(const Engine&) = delete;
   Engine& operator=(const Engine&) = delete;
@@ -433,7 +450,7 @@ class Engine {
         admit_vectors<NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, nullptr, n_, S);
         note_launches(1);
       } else {
-        FpSample* fs = fp_sample(1);
+        FpSample* fs = fp_sample(1, st_);
         if (prof_enabled()) prof_count(cls_rhs(), 1);
         apply_kernel<double, OpD><<<dim3(grid_of((const void*)apply_kernel<double, OpD>, kTile, na), cap_), kTile,
                                     0, st_>>>(g_, opd_, V64{chi_}, V64{ws_.b64}, 0.0, n_, r_, 1, S, ST_ADMIT,
@@ -446,16 +463,34 @@ class Engine {
       note_launches(5);
       ru = true;
     }
-    if (ru) reliable_update(n_ru);
     // After reliable updates with nothing known to be running, read the
     // statuses first rather than launch a chunk that may find nothing to do.
-    if (!ru || nrun_ > 0) {
+    const bool run = !ru || nrun_ > 0;
+    // The reliable update (FP64, bound by the FP64 pipe) runs on the side
+    // stream while the chunk of iterations of the other systems (FP32, bound
+    // by memory) runs on the engine's stream: they act on disjoint systems.
+    const bool overlap = ru && run && side_ != nullptr;
+    if (ru) {
+      mark_ru<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S);
+      note_launches(1);
+      if (overlap) {
+        cudaEventRecord(ev_fork_, st_);
+        cudaStreamWaitEvent(side_, ev_fork_, 0);
+        reliable_update(n_ru, side_);
+        cudaEventRecord(ev_join_, side_);
+      } else {
+        reliable_update(n_ru, st_);
+      }
+    }
+    if (run) {
       size_for_live();
       // every 4th chunk is timed when profiling, on its second iteration: by
       // then the queue is full, so the events time the kernels rather than the
       // host's launch latency
+      // (never in a round whose reliable update runs alongside: the events
+      // would time the two streams' kernels sharing the GPU)
       const bool prof = prof_enabled() && chunk_ > 1 && samples_.size() < (size_t)kProfSlots / 2 &&
-                        (chunks_ % 4 == 0);
+                        (chunks_ % 4 == 0) && !overlap;
       ++chunks_;
       if (!prof && use_graphs_ && chunks_ > 1) {
         launch_chunk_graph();
@@ -463,6 +498,7 @@ class Engine {
         for (int i = 0; i < chunk_; ++i) iterate(prof && i == 1);
       }
     }
+    if (overlap) cudaStreamWaitEvent(st_, ev_join_, 0);
     cudaMemcpyAsync(hr_, S, sizeof(SysState) * cap_, cudaMemcpyDeviceToHost, st_);
     if (ev_) cudaEventRecord(ev_, st_);
   }
@@ -485,7 +521,7 @@ class Engine {
       nneed_ += (s == ST_NEED_RU);
       nrun += (s == ST_RUNNING);
       active += (s == ST_RUNNING || s == ST_NEED_RU || s == ST_JUST_UPDATED || s == ST_ADMIT ||
-                 s == ST_ZERO_B || s == ST_ZERO_GUESS);
+                 s == ST_ZERO_B || s == ST_ZERO_GUESS || s == ST_RU_PENDING || s == ST_READY);
     }
     nrun_ = nrun;
     ++rounds_;
@@ -519,28 +555,27 @@ class Engine {
     staged_.clear();
   }
 
+  // The reliable update of the systems in RU_PENDING, on stream `sx`.
   // nsys: the slots (at most) that take the update this round, for the grids.
-  void reliable_update(int nsys) {
+  void reliable_update(int nsys, cudaStream_t sx) {
     SysState* S = ws_.S;
     const int gv = grid_of((const void*)cg_k3<TF, VR, VF, NC>, 256, nsys);
-    if constexpr (MIXED) accum_x<NC><<<dim3(gv, cap_), 256, 0, st_>>>(gb_, x_, ws_.x32, n_, n_, S);
-    FpSample* fs = fp_sample(2);
+    if constexpr (MIXED) accum_x<NC><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, x_, ws_.x32, n_, n_, S);
+    FpSample* fs = fp_sample(2, sx);
     if (prof_enabled()) prof_count(cls_ru(), 1);
     // r = (D+m)^+ (chi - (D+m) x) = b - A x, all in FP64
     apply_kernel<double, OpD><<<dim3(grid_of((const void*)apply_kernel<double, OpD>, kTile, nsys), cap_), kTile, 0,
-                                st_>>>(g_, opd_, V64{x_}, V64{ws_.t64}, 0.0, n_, r_, 0, S, ST_NEED_RU,
-                                       fs ? fs->cnt : nullptr, V64{chi_}, 1);
-    residual64<OpD><<<dim3(grid_of((const void*)residual64<OpD>, kTile, nsys), cap_), kTile, 0, st_>>>(
-        g_, opd_, V64{ws_.t64}, V64{ws_.r64}, bp_, S, rb_);
-    if (fs) cudaEventRecord(fs->e1, st_);
-    if constexpr (MIXED) demote_r<NC><<<dim3(gv, cap_), 256, 0, st_>>>(gb_, ws_.r64, ws_.r32, n_, n_, S);
-    cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, vunits_, S, ST_JUST_UPDATED);
-    commit_status<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S);
+                                sx>>>(g_, opd_, V64{x_}, V64{ws_.t64}, 0.0, n_, r_, 0, S, ST_RU_PENDING,
+                                      fs ? fs->cnt : nullptr, V64{chi_}, 1);
+    residual64<OpD><<<dim3(grid_of((const void*)residual64<OpD>, kTile, nsys), cap_), kTile, 0, sx>>>(
+        g_, opd_, V64{ws_.t64}, V64{ws_.r64}, bp_, S, rbu_);
+    if (fs) cudaEventRecord(fs->e1, sx);
+    if constexpr (MIXED) demote_r<NC><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, ws_.r64, ws_.r32, n_, n_, S);
+    cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, sx>>>(g_.V, fr_, fp_, n_, vunits_, S, ST_JUST_UPDATED);
+    mark_ready<<<(cap_ + 127) / 128, 128, 0, sx>>>(cap_, S);
     note_launches(MIXED ? 6 : 4);
   }
 
-  // One chunk of iterations as a CUDA graph, captured on first use: every
-  // kernel argument is fixed for the engine's life, so the graph is replayed.
   // One graph per grid class (see size_for_live), captured on first use.
   void launch_chunk_graph() {
     cudaGraphExec_t ge = nullptr;
@@ -565,7 +600,7 @@ class Engine {
     }
     if (ge) {
       cudaGraphLaunch(ge, st_);
-      note_launches(3 * chunk_);
+      note_launches(4 * chunk_);
       if (prof_enabled()) {
         prof_count(cls_k1(), chunk_);
         prof_count(cls_k2(), chunk_);
@@ -594,7 +629,8 @@ class Engine {
       bool any = false;
       for (int i = gi * ns_; i < cap_ && i < (gi + 1) * ns_; ++i) {
         const int s = hr_[i].status;
-        any |= (s == ST_RUNNING || s == ST_NEED_RU || s == ST_JUST_UPDATED || s == ST_ADMIT || s == ST_ZERO_GUESS);
+        any |= (s == ST_RUNNING || s == ST_NEED_RU || s == ST_JUST_UPDATED || s == ST_ADMIT || s == ST_ZERO_GUESS ||
+                s == ST_READY);
       }
       live += any;
     }
@@ -660,6 +696,7 @@ class Engine {
       c = ws_.pcount + 2 * (samples_.size() - 1);
       cudaEventRecord(samples_.back().e0, st_);
     }
+    commit_ready<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S);
     if constexpr (MIXED) {
       if (ns_ == 2) launch_k12<2>(c);
       else if (ns_ == 4) launch_k12<4>(c);
@@ -670,7 +707,7 @@ class Engine {
     if (sample) cudaEventRecord(samples_.back().e2, st_);
     cg_k3<TF, VR, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, vunits_, S, ST_RUNNING);
     if (count) {
-      note_launches(3);
+      note_launches(4);
       if (prof_enabled()) {
         prof_count(cls_k1(), 1);
         prof_count(cls_k2(), 1);
@@ -697,7 +734,9 @@ class Engine {
   cudaEvent_t ev_;
   size_t n_;
   int pstride_ = 0, ngrp_ = 0, gV_ = 0, g1_ = 0, g2_ = 0;
-  RedBuf rb_{};
+  RedBuf rb_{}, rbu_{};
+  cudaStream_t side_ = nullptr;  // reliable updates overlapped with iterations
+  cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
   BatchParams bp_{};
   VF fp_{}, ft_{};
   VR fr_{}, fx_{};

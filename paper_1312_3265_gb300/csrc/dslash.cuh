@@ -36,41 +36,75 @@ __host__ __device__ inline void corner_offsets(int k, const int df[4], const int
   ob = ((k & 1) ? df[0] : db[0]) + ((k & 2) ? df[1] : db[1]) + ((k & 4) ? df[2] : db[2]) + db[3];
 }
 
+// acc += M v, acc += M^+ v, acc -= M^+ v: the accumulation runs through the
+// fused multiply-adds of the product, so no separate additions are needed
+// (the one-system operator of the FP64 residuals, bound by the FP64 pipe).
+template <typename T> __device__ __forceinline__ void mv_acc(V3<T>& acc, const M3<T>& M, const V3<T>& v) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      acc.c[i].re = fma(M.e[i][j].re, v.c[j].re, acc.c[i].re);
+      acc.c[i].re = fma(-M.e[i][j].im, v.c[j].im, acc.c[i].re);
+      acc.c[i].im = fma(M.e[i][j].re, v.c[j].im, acc.c[i].im);
+      acc.c[i].im = fma(M.e[i][j].im, v.c[j].re, acc.c[i].im);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void mdv_acc(V3<T>& acc, const M3<T>& M, const V3<T>& v, T sign) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const T mr = sign * M.e[j][i].re, mi = sign * M.e[j][i].im;  // sign is +-1: exact
+      acc.c[i].re = fma(mr, v.c[j].re, acc.c[i].re);
+      acc.c[i].re = fma(mi, v.c[j].im, acc.c[i].re);
+      acc.c[i].im = fma(mr, v.c[j].im, acc.c[i].im);
+      acc.c[i].im = fma(-mi, v.c[j].re, acc.c[i].im);
+    }
+}
+
 template <typename T, typename G, typename Wt, typename In>
 __device__ __forceinline__ V3<T> sw_site(const Geom& g, int n, const G& U, const Wt& W, const In& in,
                                          T mass, T r, bool dagger) {
   int x[4], df[4], db[4];
   coords(g, n, x);
   hop_deltas(g, n, x, df, db);
+  // st = sum_mu eta_mu [U_mu(x) psi(x+mu) - U_mu(x-mu)^+ psi(x-mu)]
   V3<T> st = zero3<T>();
   int par = 0;
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
-    const int nf = n + df[mu], nb = n + db[mu];
-    V3<T> f = mv(U.link(n, mu), ld3<In, T>(in, nf));
-    V3<T> b = mdv(U.link(nb, mu), ld3<In, T>(in, nb));
+    V3<T> pf = ld3<In, T>(in, n + df[mu]), pb = ld3<In, T>(in, n + db[mu]);
     if (mu == 3) {
-      if (bc_flip(g, x, +1)) neg3(f);
-      if (bc_flip(g, x, -1)) neg3(b);
+      if (bc_flip(g, x, +1)) neg3(pf);
+      if (bc_flip(g, x, -1)) neg3(pb);
     }
-    const T eta = (par & 1) ? T(-1) : T(1);
+    if (mu == 0) {  // eta_0 = +1
+      mv_acc(st, U.link(n, mu), pf);
+      mdv_acc(st, U.link(n + db[mu], mu), pb, T(-1));
+    } else {
+      V3<T> d = zero3<T>();
+      mv_acc(d, U.link(n, mu), pf);
+      mdv_acc(d, U.link(n + db[mu], mu), pb, T(-1));
+      const T eta = (par & 1) ? T(-1) : T(1);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) st.c[i] = st.c[i] + eta * (f.c[i] - b.c[i]);
+      for (int i = 0; i < 3; ++i) st.c[i] = st.c[i] + eta * d.c[i];
+    }
     par += x[mu];
   }
+  // h = sum over the 16 corners of W(x,s) psi(x+s)
   V3<T> h = zero3<T>();
   const bool fflip = bc_flip(g, x, +1), bflip = bc_flip(g, x, -1);
 #pragma unroll 2
   for (int k = 0; k < 8; ++k) {
     int of, ob;
     corner_offsets(k, df, db, of, ob);
-    const int yf = n + of, yb = n + ob;
-    V3<T> a = mv(W.mat(n, k), ld3<In, T>(in, yf));
-    V3<T> b = mdv(W.mat(yb, k), ld3<In, T>(in, yb));
-    if (fflip) neg3(a);
-    if (bflip) neg3(b);
-    acc3(h, a);
-    acc3(h, b);
+    V3<T> pf = ld3<In, T>(in, n + of), pb = ld3<In, T>(in, n + ob);
+    if (fflip) neg3(pf);
+    if (bflip) neg3(pb);
+    mv_acc(h, W.mat(n, k), pf);
+    mdv_acc(h, W.mat(n + ob, k), pb, T(1));
   }
   const T hs = (eps_eta5_neg(x) ? r : -r) * T(0.0625);
   const T ss = dagger ? T(-0.5) : T(0.5);

@@ -77,11 +77,11 @@ static __global__ void su3_deviation(int V, const double2* __restrict__ U, unsig
   atomicMax(dev, __float_as_uint(worst));
 }
 
-// x64 (canonical) += x32 (packed, blocked order); x32 = 0   -- systems with status NEED_RU
+// x64 (canonical) += x32 (packed, blocked order); x32 = 0   -- systems with status RU_PENDING
 template <int NC>
 __global__ void accum_x(GeomBlk gb, double2* x64, float2* x32, size_t s64, size_t s32, const SysState* S) {
   const int sys = blockIdx.y;
-  if (S[sys].status != ST_NEED_RU) return;
+  if (S[sys].status != ST_RU_PENDING) return;
   const int V = gb.V;
   x64 += sys * s64;
   x32 += sys * s32;
@@ -237,10 +237,26 @@ static __global__ void admit_states(int nsys, SysState* S, int p_set) {
   }
 }
 
-// JUST_UPDATED -> RUNNING after the post-update p refresh
-static __global__ void commit_status(int nsys, SysState* S) {
+// Start of a reliable update: NEED_RU -> RU_PENDING (the update's set).
+static __global__ void mark_ru(int nsys, SysState* S) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nsys && S[i].status == ST_JUST_UPDATED) S[i].status = ST_RUNNING;
+  if (i < nsys && S[i].status == ST_NEED_RU) S[i].status = ST_RU_PENDING;
+}
+
+// End of a reliable update, after the p refresh: JUST_UPDATED -> READY.
+static __global__ void mark_ready(int nsys, SysState* S) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nsys && S[i].status == ST_JUST_UPDATED) S[i].status = ST_READY;
+}
+
+// First launch of every CG iteration, on the iteration stream: READY ->
+// RUNNING.  A reliable update running concurrently on another stream marks
+// its systems READY only after all its writes (x, r, p) are complete, and the
+// switch happens between iterations, so every kernel of an iteration sees the
+// same set of running systems.
+static __global__ void commit_ready(int nsys, SysState* S) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nsys && S[i].status == ST_READY) S[i].status = ST_RUNNING;
 }
 
 }  // namespace swc

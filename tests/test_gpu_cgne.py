@@ -277,8 +277,11 @@ def test_half_precision_needs_su3_links(sw):
 
 
 def test_graph_replay_is_bitwise_launches(sw):
-    """Chunks of iterations replayed as a captured CUDA graph give exactly the
-    results of launching the kernels one by one."""
+    """Chunks of iterations replayed as a captured CUDA graph, with the FP64
+    reliable updates of some systems running on a side stream while the others
+    iterate, give exactly the results of launching the kernels one by one on
+    one stream (three masses: the systems reach their updates in different
+    rounds)."""
     import torch
     P = Problem(sw, (6, 4, 4, 6), sw.SW_OP_WILSON, 9, ls.PLAQ_EPS, 0.05)
     chis = np.stack([ls.gaussian_source(P.dims, 12, 60 + i).reshape(-1, 4, 3) for i in range(3)])
