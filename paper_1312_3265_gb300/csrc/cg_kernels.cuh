@@ -62,7 +62,7 @@ constexpr int kTile = 128;  // sites per reduction tile == threads per stencil b
 struct RedBuf {
   double* partials;   // [nsys][pstride] tile sums
   unsigned* tickets;  // [nsys], zero between launches
-  int pstride;        // >= number of tiles
+  int pstride;        // >= kWarps x number of tiles (the iteration kernels' warp sums)
   double* hist;       // [nsys][kHist][2]: (alpha_k, beta_k) of every iteration, for Ritz values
 };
 
@@ -259,6 +259,23 @@ template <int NS> __device__ __forceinline__ void block_sum_multi(double* v, dou
   }
 }
 
+// The iteration kernels reduce without a block barrier per tile: each warp
+// sums its 32 sites (FP64 shuffle tree) and lane 0 stores the warp sum at
+// slot kWarps*tile + warp of the system's partials; the last block adds all
+// kWarps*ntiles slots in slot order.  The order depends only on the volume,
+// so a system's sums are the same whatever the grid or the batch.
+constexpr int kWarps = kTile / 32;
+template <int NS>
+__device__ __forceinline__ void put_warp_sums(const RedBuf& rb, int sys0, unsigned act, int tile, double* v) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[s] += __shfl_down_sync(0xffffffffu, v[s], o);
+    if (lane == 0 && (act & (1u << s))) rb.partials[(size_t)(sys0 + s) * rb.pstride + kWarps * tile + w] = v[s];
+  }
+}
+
 // Systems of group blockIdx.y that are RUNNING, as a bit mask, and their masses.
 template <typename T, int NS>
 __device__ __forceinline__ unsigned running_mask(const SysState* S, int sys0, int nsys, T* m) {
@@ -328,16 +345,14 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k1(GG g
         acc[s] = (double)a;
       }
     }
-    block_sum_multi<NS>(acc, sm);
-#pragma unroll
-    for (int s = 0; s < NS; ++s)
-      if (act & (1u << s)) put_tile(rb, sys0 + s, tile, acc[s]);
+    put_warp_sums<NS>(rb, sys0, act, tile, acc);
   }
+  __threadfence();  // every warp's partials, before the block's ticket
   if (block_done(rb, grp, &last, nbt)) {
 #pragma unroll 1
     for (int s = 0; s < NS; ++s) {
       if (!(act & (1u << s))) continue;
-      const double pAp = finalize_sum(rb, sys0 + s, ntiles, sm);
+      const double pAp = finalize_sum(rb, sys0 + s, kWarps * ntiles, sm);
       if (threadIdx.x == 0) {
         SysState& st = S[sys0 + s];
         st.pAp = pAp;
@@ -404,16 +419,14 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(GG g
         acc[s] = (double)a;
       }
     }
-    block_sum_multi<NS>(acc, sm);
-#pragma unroll
-    for (int s = 0; s < NS; ++s)
-      if (act & (1u << s)) put_tile(rb, sys0 + s, tile, acc[s]);
+    put_warp_sums<NS>(rb, sys0, act, tile, acc);
   }
+  __threadfence();  // every warp's partials, before the block's ticket
   if (block_done(rb, grp, &last, nbt)) {
 #pragma unroll 1
     for (int s = 0; s < NS; ++s) {
       if (!(act & (1u << s))) continue;
-      const double rr = finalize_sum(rb, sys0 + s, ntiles, sm);
+      const double rr = finalize_sum(rb, sys0 + s, kWarps * ntiles, sm);
       if (threadIdx.x == 0) {
         SysState& st = S[sys0 + s];
         st.iter += 1;

@@ -144,7 +144,7 @@ inline size_t workspace_bytes_pt(int V, int NC, int nsys, bool mixed, size_t pt)
   const size_t ntiles = (size_t)(V + kTile - 1) / kTile;
   size_t b = (mixed ? 2 : 3) * align_up(sizeof(double2) * n);  // b64 only in FP64 mode
   b += mixed ? 2 * align_up(pt * nsys) + 2 * align_up(sizeof(float2) * n) : align_up(pt * nsys);
-  b += align_up(sizeof(SysState) * nsys) + align_up(sizeof(double) * 2 * ntiles * nsys) +
+  b += align_up(sizeof(SysState) * nsys) + align_up(sizeof(double) * 2 * kWarps * ntiles * nsys) +
        align_up(sizeof(unsigned) * 2 * nsys) + align_up(sizeof(double) * nsys) +
        align_up(sizeof(double) * 2 * kHist * nsys) + align_up(sizeof(int) * 2 * kProfSlots);
   return b;
@@ -180,7 +180,7 @@ inline Workspace carve_workspace_pt(void* base, int V, int NC, int nsys, bool mi
     w.t_lo = w.t64;
   }
   w.S = (SysState*)take(sizeof(SysState) * nsys);
-  w.partials = (double*)take(sizeof(double) * 2 * ntiles * nsys);  // 2nd half: norm_b's |x0|^2
+  w.partials = (double*)take(sizeof(double) * 2 * kWarps * ntiles * nsys);  // 2nd half: norm_b's |x0|^2
   w.tickets = (unsigned*)take(sizeof(unsigned) * 2 * nsys);  // 2nd half: the reliable-update kernels
   w.mass = (double*)take(sizeof(double) * nsys);
   w.hist = (double*)take(sizeof(double) * 2 * kHist * nsys);
@@ -279,7 +279,8 @@ class Engine {
          bool use_graphs = true)
       : g_(g), opd_(opd), opf_(opf), r_(r), cap_(cap), chi_(chi), x_(x), ws_(ws), hr_(hs_read), hst_(hs_stage),
         st_(st), ev_(ev), n_((size_t)g.V * NC), use_graphs_(use_graphs && param_graphs()) {
-    pstride_ = (g.V + kTile - 1) / kTile;
+    ntiles_ = (g.V + kTile - 1) / kTile;
+    pstride_ = kWarps * ntiles_;
     gb_ = make_blocked(g, param_site_blocking());
     if constexpr (MIXED) gk_ = gb_;
     else gk_ = g;
@@ -614,9 +615,9 @@ class Engine {
   // run (blocks of stopped slots return at once).
   void set_grids(int groups) {
     cls_ = groups;
-    g1_ = grid_for(k1_ptr(), kTile, g_.V, groups, pstride_);
-    g2_ = grid_for(k2_ptr(), kTile, g_.V, groups, pstride_);
-    gV_ = grid_for((const void*)cg_k3<TF, VR, VF, NC>, 256, g_.V, groups * ns_, pstride_);
+    g1_ = grid_for(k1_ptr(), kTile, g_.V, groups, ntiles_);
+    g2_ = grid_for(k2_ptr(), kTile, g_.V, groups, ntiles_);
+    gV_ = grid_for((const void*)cg_k3<TF, VR, VF, NC>, 256, g_.V, groups * ns_, ntiles_);
   }
 
   // Size the iteration grids for the groups holding a slot that may run in
@@ -733,7 +734,7 @@ class Engine {
   cudaStream_t st_;
   cudaEvent_t ev_;
   size_t n_;
-  int pstride_ = 0, ngrp_ = 0, gV_ = 0, g1_ = 0, g2_ = 0;
+  int ntiles_ = 0, pstride_ = 0, ngrp_ = 0, gV_ = 0, g1_ = 0, g2_ = 0;
   RedBuf rb_{}, rbu_{};
   cudaStream_t side_ = nullptr;  // reliable updates overlapped with iterations
   cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
@@ -748,7 +749,7 @@ class Engine {
 
   // Blocks per slot of a launch that computes `nsys` of the engine's slots.
   int grid_of(const void* kernel, int block, int nsys) const {
-    return grid_for(kernel, block, g_.V, nsys < 1 ? 1 : (nsys > cap_ ? cap_ : nsys), pstride_);
+    return grid_for(kernel, block, g_.V, nsys < 1 ? 1 : (nsys > cap_ ? cap_ : nsys), ntiles_);
   }
   int nrun_ = 0, ns_ = 1, gfast_ = 0;
   std::vector<Sample> samples_;
