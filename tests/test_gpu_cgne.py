@@ -344,3 +344,38 @@ def test_site_order_and_grid_order(sw, blocking, gfast):
         sw.sw_set_param(sw.SW_PARAM_GROUP_FAST, old[1])
     for prec in (sw.SW_PREC_F32_RELIABLE, sw.SW_PREC_F16_RELIABLE):
         assert np.array_equal(outs[(0, prec)], outs[(1, prec)])
+
+
+def test_concurrent_solves_from_two_threads(sw):
+    """Two host threads solving a staggered Wilson and a Wilson batch at the same
+    time, each on its own stream, get bit-identical results to solving them one
+    after the other (the entry points are thread-safe; every solve owns its
+    workspace, status buffers and side stream)."""
+    import threading
+    import torch
+    dims = (6, 4, 4, 6)
+    Ps = Problem(sw, dims, sw.SW_OP_STAGGERED_WILSON, 11, ls.PLAQ_EPS, 0.1, apbc=True)
+    Pw = Problem(sw, dims, sw.SW_OP_WILSON, 11, ls.PLAQ_EPS, 0.1, apbc=True)
+    ms, mw = [0.05, 0.1, 0.2], [0.05, 0.1, 0.2, 0.07]
+    chs = dev(np.stack([ls.gaussian_source(dims, 3, 80 + i).reshape(-1, 3) for i in range(3)]))
+    chw = dev(np.stack([ls.gaussian_source(dims, 12, 90 + i).reshape(-1, 4, 3) for i in range(4)]))
+
+    def run(P, ch, masses, stream):
+        with torch.cuda.stream(stream):
+            x = torch.zeros_like(ch)
+            rc, infos = sw.cgne_solve_batch(dims, P.op, P.U, P.W, ch, x, masses, 1.0, 1e-9, 10000,
+                                            sw.SW_PREC_F32_RELIABLE, True, stream=stream)
+        stream.synchronize()
+        return rc, infos, x.cpu().numpy()
+
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    ref_s, ref_w = run(Ps, chs, ms, s1), run(Pw, chw, mw, s2)
+    out = {}
+    th = threading.Thread(target=lambda: out.__setitem__("s", run(Ps, chs, ms, s1)))
+    th.start()
+    out["w"] = run(Pw, chw, mw, s2)
+    th.join()
+    for ref, got in ((ref_s, out["s"]), (ref_w, out["w"])):
+        assert ref[0] == sw.SW_OK and got[0] == sw.SW_OK
+        assert [i.iters for i in ref[1]] == [i.iters for i in got[1]]
+        assert np.array_equal(ref[2], got[2])
