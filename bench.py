@@ -57,11 +57,11 @@ ITERS_TABLE = {"sw": {0.02: 41.0, 0.05: 39.0, 0.1: 36.9, 0.2: 32.0},
 # with the systems computed).  Entries are removed when the kernel changes.
 NCU_TRAFFIC = {
     # profiles/ncu_sw_k1k2_fp32_16x16x16x32_12sys.md
-    "sw.k1.f32": {"bytes": 198.9e6, "algorithmic": 188.7e6, "systems": 12},
-    "sw.k2.f32": {"bytes": 346.2e6, "algorithmic": 339.7e6, "systems": 12},
-    # profiles/ncu_wilson_k1k2_fp32_16x16x16x32_12sys.md
-    "wilson.k1.f32": {"bytes": 323.8e6, "algorithmic": 339.7e6, "systems": 12},
-    "wilson.k2.f32": {"bytes": 950.1e6, "algorithmic": 943.7e6, "systems": 12},
+    "sw.k1.f32": {"bytes": 199.6e6, "algorithmic": 188.7e6, "systems": 12},
+    "sw.k2.f32": {"bytes": 230.5e6, "algorithmic": 226.5e6, "systems": 12},
+    # profiles/ncu_wilson_k1k2k3_fp32_16x16x16x32_12sys.md
+    "wilson.k1.f32": {"bytes": 323.7e6, "algorithmic": 339.7e6, "systems": 12},
+    "wilson.k2.f32": {"bytes": 475.9e6, "algorithmic": 490.7e6, "systems": 12},
 }
 
 # FP64 peak of a GB300 (nominal 1.25 TFLOP/s; not in the measured-peaks file):
@@ -266,6 +266,16 @@ def classify_kernels(prof, hbm_peak, peak_kind):
 
     top = max(cand, default=None)
     top_hbm = max((c for c in cand if c[2][0] == "hbm"), default=None)
+    # one whole inner-precision CG iteration (k1 + k2 + k3) of each operator:
+    # the algorithmic bytes of the three launches over their summed time
+    for op in ("wilson", "sw"):
+        ks = [k for k in prof if k.startswith(op + ".k") and prof[k]["launches"]]
+        if len(ks) == 3:
+            ms = sum(prof[k]["ms"] / prof[k]["launches"] for k in ks)
+            by = sum(prof[k]["bytes"] / prof[k]["launches"] for k in ks)
+            gbs = by / (ms / 1e3) / 1e9
+            kernels[op + ".iteration"] = {"kernels": sorted(ks), "ms": round(ms, 4), "GB/s": round(gbs, 1),
+                                          "frac_hbm": round(gbs / hbm_peak, 4)}
     return kernels, (roof_of(top) if top else None), (roof_of(top_hbm) if top_hbm else None)
 
 

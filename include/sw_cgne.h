@@ -209,14 +209,16 @@ int sw_autotune(const sw_lattice* lat, int op, const void* U, const void* W, int
 
 /* Kernel timing.  Instrumentation with no counterpart in the paper.  While
  * enabled, the second iteration of every chunk of CG iterations has its two
- * stencil launches (k1: t = (D+m) p with |t|^2; k2: (D+m)^+ t with the x, r
- * updates and |r|^2) bracketed by CUDA events on the solve's stream.  After
+ * stencil launches (k1: t = (D+m) p with |t|^2; k2: (D+m)^+ t with the r
+ * update and |r|^2) and its vector update (k3: x += alpha p, p = r + beta p)
+ * bracketed by CUDA events on the solve's stream.  After
  * each solve completes, the per-class totals grow by: launches, event time
  * (ms), and the algorithmic bytes of those launches (links and transports
  * once per launch, plus each running system's vectors read and written).
  * The stencil kernels of a sampled iteration count the systems they compute
  * on the device, so the byte count matches the work done.
- * Classes are named "<operator>.<kernel>.<precision>", e.g. "sw.k1.f32".
+ * Classes are named "<operator>.<kernel>.<precision>", e.g. "sw.k1.f32"
+ * (k3 carries bytes only).
  * The FP64 matvecs of the reliable updates and of the right-hand side are
  * timed as class "<operator>.ru.f64" (the two launches of a residual
  * recomputation) and "<operator>.rhs.f64": they are bound by the FP64 units,

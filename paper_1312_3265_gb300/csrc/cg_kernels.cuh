@@ -2,9 +2,11 @@
 //
 // One iteration of textbook CG on A = (D+m)^+(D+m) takes three launches:
 //   k1  t = (D+m) p,  pAp = <p, A p> = |t|^2,  alpha = |r|^2 / pAp
-//   k2  Ap = (D+m)^+ t (never stored), x += alpha p, r -= alpha Ap,
+//   k2  Ap = (D+m)^+ t (never stored), r -= alpha Ap,
 //       |r|^2, beta = |r_new|^2 / |r_old|^2, status decisions
-//   k3  p = r + beta p
+//   k3  x += alpha p, then p = r + beta p (one read of the old p serves both)
+// A system that k2 stops (for a reliable update) skips k3: its last
+// x += alpha p is applied at the start of the update (k3 in its x-only form).
 // Every launch covers a batch of independent systems (blockIdx.y = system)
 // that share the gauge field; blocks of a system whose status is not RUNNING
 // return at once, so converged systems cost nothing.  Scalars live in device
@@ -369,8 +371,8 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k1(GG g
 
 // ---------------------------------------------------------------- k2: Ap = D^+ t; x, r update; |r|^2
 template <typename T, typename Op, int NS, typename RVec, typename GG>
-__global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(GG g, Op op, typename Op::Vec t, typename Op::Vec p, RVec r,
-                                               RVec x, BatchParams bp, int nsys, SysState* S, RedBuf rb,
+__global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(GG g, Op op, typename Op::Vec t, RVec r,
+                                               BatchParams bp, int nsys, SysState* S, RedBuf rb,
                                                int* nact, int gfast) {
   __shared__ double sm[NS * 32];
   __shared__ int last;
@@ -388,9 +390,7 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(GG g
 #pragma unroll
   for (int s = 0; s < NS; ++s) alpha[s] = (act & (1u << s)) ? (T)S[sys0 + s].alpha : T(0);
   t = sys_view(t, sys0, bp.vstride);
-  p = sys_view(p, sys0, bp.vstride);
   r = sys_view(r, sys0, bp.sstride);
-  x = sys_view(x, sys0, bp.sstride);
   const int ntiles = (g.V + kTile - 1) / kTile;
   // grid-stride over tiles: the blocks resident at a time cover neighbouring
   // tiles, which keeps their neighbour reads together in L2 (measured faster
@@ -406,12 +406,10 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(GG g
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         if (!(act & (1u << s))) continue;
-        const typename Op::Vec ps = sys_at(p, s, bp.vstride);
-        const RVec rs = sys_at(r, s, bp.sstride), xs = sys_at(x, s, bp.sstride);
+        const RVec rs = sys_at(r, s, bp.sstride);
         T a = T(0);
 #pragma unroll
         for (int c = 0; c < Op::NC; ++c) {
-          xs.st(n, c, xs.ld(n, c) + alpha[s] * ps.ld(n, c));
           const cx<T> rc = rs.ld(n, c) - alpha[s] * ap[s].c[c];
           rs.st(n, c, rc);
           a += norm2(rc);
@@ -445,20 +443,35 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(GG g
   }
 }
 
-// ---------------------------------------------------------------- k3: p = r + beta p
+// ---------------------------------------------------------------- k3: x += alpha p, p = r + beta p
+// mode bit 1: x += alpha p (the iteration's solution update, deferred from
+// k2 so that one read of p serves it and the new direction); bit 2:
+// p = r + beta p.  Systems in ST_RUNNING take both, a reliable update takes
+// the x part first (systems in ST_RU_PENDING) and the p part last (ST_JUST_UPDATED).
 template <typename T, typename RVec, typename PVec, int NC>
-__global__ void __launch_bounds__(256) cg_k3(int V, RVec r, PVec p, size_t rstride, size_t pstride,
-                                             const SysState* S, int only_status) {
+__global__ void __launch_bounds__(256) cg_k3(int V, RVec r, PVec p, RVec x, size_t rstride, size_t pstride,
+                                             const SysState* S, int only_status, int mode, int* nact = nullptr) {
   const int sys = blockIdx.y;
   if (S[sys].status != only_status) return;
+  if (nact && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nact, 1);
   r = sys_view(r, sys, rstride);
   p = sys_view(p, sys, pstride);
-  const T beta = (T)S[sys].beta;
+  x = sys_view(x, sys, rstride);
+  const T beta = (T)S[sys].beta, alpha = (T)S[sys].alpha;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < V; n += gridDim.x * blockDim.x) {
-    CV<T, NC> v;
+    CV<T, NC> po;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) v.c[c] = r.ld(n, c) + beta * p.ld(n, c);
-    st_site(p, n, v);
+    for (int c = 0; c < NC; ++c) po.c[c] = p.ld(n, c);
+    if (mode & 1) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) x.st(n, c, x.ld(n, c) + alpha * po.c[c]);
+    }
+    if (mode & 2) {
+      CV<T, NC> v;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) v.c[c] = r.ld(n, c) + beta * po.c[c];
+      st_site(p, n, v);
+    }
   }
 }
 

@@ -129,7 +129,7 @@ struct Workspace {
   unsigned* tickets;  // [2 nsys]: iteration kernels, then reliable-update kernels
   double* mass;
   double* hist;  // CG coefficients, [nsys][kHist][2]
-  int* pcount;   // systems computed per sampled launch, [kProfSlots][2]
+  int* pcount;   // systems computed per sampled launch: [kProfSlots/2][3] (k1, k2, k3), then the FP64 samples
 };
 
 constexpr int kProfSlots = 1024;  // sampled iterations per solve
@@ -350,6 +350,10 @@ class Engine {
     static const std::string c = std::string(OpF::kName) + ".k2." + OpF::kPrec;
     return c.c_str();
   }
+  static const char* cls_k3() {
+    static const std::string c = std::string(OpF::kName) + ".k3." + OpF::kPrec;
+    return c.c_str();
+  }
   static const char* cls_ru() {
     static const std::string c = std::string(OpD::kName) + ".ru.f64";
     return c.c_str();
@@ -363,7 +367,7 @@ class Engine {
   void flush_profile() {
     flush_fp_samples();
     if (samples_.empty()) return;
-    std::vector<int> cnt(2 * samples_.size());
+    std::vector<int> cnt(3 * samples_.size());
     if (cnt.empty() ||
         cudaMemcpy(cnt.data(), ws_.pcount, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
       cudaGetLastError();
@@ -375,16 +379,18 @@ class Engine {
     const double pv = (double)sizeof(typename VF::unit) * vunits_;
     const double rv = (double)sizeof(typename VR::unit) * n_;
     // flops: the paper's count per site and application (Eq. 4) for every
-    // computed system (k2's x, r updates are not counted)
+    // computed system (k2's r update is not counted)
     const double fl = OpF::kFlops * g_.V;
+    // k3: r, p, x read, p and x written (a streaming kernel: no flops counted)
     for (size_t k = 0; k < samples_.size(); ++k) {
-      prof_push(cls_k1(), samples_[k].e0, samples_[k].e1, gauge + cnt[2 * k] * 2.0 * pv, fl * cnt[2 * k]);
-      prof_push(cls_k2(), samples_[k].e1, samples_[k].e2, gauge + cnt[2 * k + 1] * (2.0 * pv + 4.0 * rv),
-                fl * cnt[2 * k + 1]);
+      prof_push(cls_k1(), samples_[k].e0, samples_[k].e1, gauge + cnt[3 * k] * 2.0 * pv, fl * cnt[3 * k]);
+      prof_push(cls_k2(), samples_[k].e1, samples_[k].e2, gauge + cnt[3 * k + 1] * (pv + 2.0 * rv),
+                fl * cnt[3 * k + 1]);
+      prof_push(cls_k3(), samples_[k].e2, samples_[k].e3, cnt[3 * k + 2] * (2.0 * pv + 3.0 * rv));
     }
     prof_commit(true);
     samples_.clear();
-    cudaMemset(ws_.pcount, 0, sizeof(int) * kProfSlots);
+    cudaMemset(ws_.pcount, 0, sizeof(int) * 3 * kProfSlots / 2);
   }
 
   ~Engine() {
@@ -561,6 +567,8 @@ class Engine {
   void reliable_update(int nsys, cudaStream_t sx) {
     SysState* S = ws_.S;
     const int gv = grid_of((const void*)cg_k3<TF, VR, VF, NC>, 256, nsys);
+    // the last x += alpha p of each system (k2 stopped it before k3)
+    cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, sx>>>(g_.V, fr_, fp_, fx_, n_, vunits_, S, ST_RU_PENDING, 1);
     if constexpr (MIXED) accum_x<NC><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, x_, ws_.x32, n_, n_, S);
     FpSample* fs = fp_sample(2, sx);
     if (prof_enabled()) prof_count(cls_ru(), 1);
@@ -572,9 +580,9 @@ class Engine {
         g_, opd_, V64{ws_.t64}, V64{ws_.r64}, bp_, S, rbu_);
     if (fs) cudaEventRecord(fs->e1, sx);
     if constexpr (MIXED) demote_r<NC><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, ws_.r64, ws_.r32, n_, n_, S);
-    cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, sx>>>(g_.V, fr_, fp_, n_, vunits_, S, ST_JUST_UPDATED);
+    cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, sx>>>(g_.V, fr_, fp_, fx_, n_, vunits_, S, ST_JUST_UPDATED, 2);
     mark_ready<<<(cap_ + 127) / 128, 128, 0, sx>>>(cap_, S);
-    note_launches(MIXED ? 6 : 4);
+    note_launches(MIXED ? 7 : 5);
   }
 
   // One graph per grid class (see size_for_live), captured on first use.
@@ -605,6 +613,7 @@ class Engine {
       if (prof_enabled()) {
         prof_count(cls_k1(), chunk_);
         prof_count(cls_k2(), chunk_);
+        prof_count(cls_k3(), chunk_);
       }
     } else {
       for (int i = 0; i < chunk_; ++i) iterate(false);
@@ -656,7 +665,7 @@ class Engine {
     }
     prof_commit(true);
     fsamples_.clear();
-    cudaMemset(ws_.pcount + kProfSlots, 0, sizeof(int) * kProfSlots);
+    cudaMemset(ws_.pcount + 3 * kProfSlots / 2, 0, sizeof(int) * kProfSlots / 2);
   }
 
   // Register-blocking widths 2 and 4 exist for the inner-precision stencils
@@ -680,7 +689,7 @@ class Engine {
     const dim3 grid1 = gfast_ ? dim3(ngrp_, g1_) : dim3(g1_, ngrp_), grid2 = gfast_ ? dim3(ngrp_, g2_) : dim3(g2_, ngrp_);
     cg_k1<TF, OpF, NS, GK><<<grid1, kTile, 0, st_>>>(gk_, opf_, fp_, ft_, bp_, cap_, S, rb_, c, gfast_);
     if (c) cudaEventRecord(samples_.back().e1, st_);
-    cg_k2<TF, OpF, NS, VR, GK><<<grid2, kTile, 0, st_>>>(gk_, opf_, ft_, fp_, fr_, fx_, bp_, cap_, S, rb_,
+    cg_k2<TF, OpF, NS, VR, GK><<<grid2, kTile, 0, st_>>>(gk_, opf_, ft_, fr_, bp_, cap_, S, rb_,
                                                          c ? c + 1 : nullptr, gfast_);
   }
 
@@ -688,13 +697,13 @@ class Engine {
   // events, and its stencil kernels count the systems they compute; the
   // algorithmic bytes of a launch (every stored element touched once) are the
   // links (and transports) once plus, per computed system, the vectors read
-  // and written: k1 p read, t written; k2 t, p read and x, r read and written.
+  // and written: k1 p read, t written; k2 t read, r read and written.
   void iterate(bool sample, bool count = true) {
     SysState* S = ws_.S;
     int* c = nullptr;
     if (sample) {
-      samples_.push_back(Sample{prof_event(), prof_event(), prof_event()});
-      c = ws_.pcount + 2 * (samples_.size() - 1);
+      samples_.push_back(Sample{prof_event(), prof_event(), prof_event(), prof_event()});
+      c = ws_.pcount + 3 * (samples_.size() - 1);
       cudaEventRecord(samples_.back().e0, st_);
     }
     commit_ready<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S);
@@ -706,18 +715,21 @@ class Engine {
       launch_k12<1>(c);
     }
     if (sample) cudaEventRecord(samples_.back().e2, st_);
-    cg_k3<TF, VR, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, n_, vunits_, S, ST_RUNNING);
+    cg_k3<TF, VR, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, fx_, n_, vunits_, S, ST_RUNNING, 3,
+                                                            c ? c + 2 : nullptr);
+    if (sample) cudaEventRecord(samples_.back().e3, st_);
     if (count) {
       note_launches(4);
       if (prof_enabled()) {
         prof_count(cls_k1(), 1);
         prof_count(cls_k2(), 1);
+        prof_count(cls_k3(), 1);
       }
     }
   }
 
   struct Sample {
-    cudaEvent_t e0, e1, e2;
+    cudaEvent_t e0, e1, e2, e3;
   };
   Geom g_;
   GK gk_;
