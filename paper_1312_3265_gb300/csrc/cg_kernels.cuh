@@ -301,10 +301,10 @@ __device__ __forceinline__ unsigned running_mask(const SysState* S, int sys0, in
 // Minimum resident blocks per SM requested from the compiler for the
 // inner-precision stencil kernels (caps their registers): they are
 // latency-bound, so more resident warps hide more of the L2 latency
-// (staggered Wilson 8 blocks = 64 registers, Wilson 6 = 80, chosen from the
+// (staggered Wilson 8 blocks = 64 registers, Wilson 7 = 72, chosen from the
 // spill counts of ptxas and GB300 timings).  FP64 kernels are ALU-bound: no cap.
 template <typename T, typename Op> constexpr int stencil_min_blocks() {
-  return sizeof(T) == 4 ? (Op::NC == 3 ? 8 : 6) : 1;
+  return sizeof(T) == 4 ? (Op::NC == 3 ? 8 : 7) : 1;
 }
 
 template <typename T, typename Op, int NS, typename GG>

@@ -173,3 +173,45 @@ def test_large_lattice_sampled_sites(sw):
         assert np.abs(a[n] - want).max() < TOL * np.abs(want).max() * 10
         want = site.wilson_dslash_site(Uh, spn_h, dims, n, 0.05, 1.0, True, False)
         assert np.abs(b[n] - want).max() < TOL * np.abs(want).max() * 10
+
+
+def test_largest_lattices_sampled_sites(sw):
+    """The large-volume workloads' lattices: 48^3x96 staggered Wilson (10.6 M
+    sites, periodic) and 32^3x64 Wilson (antiperiodic): sampled output sites of
+    the FP64 operators -- the ones that decide convergence -- against the
+    one-site oracle, including the first and last sites and both time
+    boundaries (complex-element indices beyond 2^24)."""
+    import torch
+    for dims, op in (((48, 48, 48, 96), "sw"), ((32, 32, 32, 64), "wilson")):
+        V = ls.volume(dims)
+        Uh = ls.su3_links(dims, 2, ls.PLAQ_EPS, processes=16)
+        U = dev(Uh)
+        rng = np.random.default_rng(3)
+        slab = dims[0] * dims[1] * dims[2]
+        sites = np.concatenate([[0, V - 1, slab - 1, V - slab, (V // 2) | 1], rng.integers(0, V, 10)])
+        if op == "sw":
+            W = torch.empty((V, 8, 3, 3), dtype=torch.complex128, device="cuda")
+            sw.sw_hypercube_build(dims, U, W)
+            psi_h = rand_vec(V, 3, 27)
+            psi = dev(psi_h)
+            out = torch.empty_like(psi)
+            sw.sw_dslash_apply(dims, U, W, psi, out, 0.01, 1.0, False)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            del W, out
+            for n in sites:
+                want = site.sw_dslash_site(Uh, psi_h, dims, int(n), 0.01, 1.0, False, False)
+                assert np.abs(got[int(n)] - want).max() < TOL * np.abs(want).max() * 10
+        else:
+            spn_h = rand_vec(V, 12, 28).reshape(V, 4, 3)
+            spn = dev(spn_h)
+            out = torch.empty_like(spn)
+            sw.wilson_dslash_apply(dims, U, spn, out, 0.01, 1.0, True, True)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            del out
+            for n in sites:
+                want = site.wilson_dslash_site(Uh, spn_h, dims, int(n), 0.01, 1.0, True, True)
+                assert np.abs(got[int(n)] - want).max() < TOL * np.abs(want).max() * 10
+        del U
+        torch.cuda.empty_cache()
