@@ -60,8 +60,8 @@ NCU_TRAFFIC = {
     "sw.k1.f32": {"bytes": 199.6e6, "algorithmic": 188.7e6, "systems": 12},
     "sw.k2.f32": {"bytes": 230.5e6, "algorithmic": 226.5e6, "systems": 12},
     # profiles/ncu_wilson_k1k2k3_fp32_16x16x16x32_12sys.md
-    "wilson.k1.f32": {"bytes": 323.7e6, "algorithmic": 339.7e6, "systems": 12},
-    "wilson.k2.f32": {"bytes": 475.9e6, "algorithmic": 490.7e6, "systems": 12},
+    "wilson.k1.f32": {"bytes": 323.9e6, "algorithmic": 339.7e6, "systems": 12},
+    "wilson.k2.f32": {"bytes": 475.4e6, "algorithmic": 490.7e6, "systems": 12},
 }
 
 # FP64 peak of a GB300 (nominal 1.25 TFLOP/s; not in the measured-peaks file):
@@ -93,6 +93,9 @@ def parse():
     ap.add_argument("--graphs", type=int, default=None, help="1/0: replay chunks as CUDA graphs (library default 1)")
     ap.add_argument("--site-blocking", type=int, default=None, help="1/0: blocked site order of packed fields")
     ap.add_argument("--group-fast", type=int, default=None, help="1/0: system groups fastest in the stencil grid")
+    ap.add_argument("--autotune", action="store_true",
+                    help="before the warm-up, pick each operator's systems per thread and the shared site order "
+                         "with the library's width x site-order autotuner (overrides --ns-* / --site-blocking)")
     ap.add_argument("--concurrent-ops", action="store_true",
                     help="solve the staggered Wilson and Wilson batches at the same time, each on its own stream "
                          "and host thread (the per-kernel event timings then include the other batch's kernels)")
@@ -280,6 +283,31 @@ def classify_kernels(prof, hbm_peak, peak_kind):
 
 
 # ------------------------------------------------------------------ our arm
+def autotune_layout(sw, dims, Ud, W, prec, n_sw, n_w, stream, iters=48):
+    """Width x site order for this step's batches: sw_autotune_layout per
+    operator on the first configuration, then the site order (one setting for
+    both operators) with the smaller sum of the operators' best times, and per
+    operator the fastest width under that order."""
+    if prec == sw.SW_PREC_F64:
+        return {"skipped": "the FP64 path has one layout"}
+    times = {}
+    if n_sw:
+        sw.sw_hypercube_build(dims, Ud, W, stream=stream)
+        _, times["sw"] = sw.sw_autotune_layout(dims, sw.SW_OP_STAGGERED_WILSON, Ud, W, n_sw, prec, 1.0, iters,
+                                               stream=stream)
+    if n_w:
+        _, times["wilson"] = sw.sw_autotune_layout(dims, sw.SW_OP_WILSON, Ud, None, n_w, prec, R_WILSON, iters,
+                                                   stream=stream)
+    total = {b: sum(min(t[(w, b)] for w in (1, 2, 4)) for t in times.values()) for b in (0, 1)}
+    blk = min(total, key=total.get)
+    sw.sw_set_param(sw.SW_PARAM_SITE_BLOCKING, blk)
+    keys = {"sw": sw.SW_PARAM_NS_SW, "wilson": sw.SW_PARAM_NS_WILSON}
+    for op, t in times.items():
+        sw.sw_set_param(keys[op], min((1, 2, 4), key=lambda w: t[(w, blk)]))
+    return {"iters": iters, "site_blocking": blk,
+            "ms": {op: {f"ns{w}_blk{b}": round(v, 2) for (w, b), v in sorted(t.items())} for op, t in times.items()}}
+
+
 def run_ours(args):
     import torch
     import paper_1312_3265_gb300 as sw
@@ -327,6 +355,8 @@ def run_ours(args):
     x_sw = torch.empty_like(chi_sw)
     x_w = torch.empty_like(chi_w)
     stream = torch.cuda.current_stream(dev)
+    tune = (autotune_layout(sw, dims, U[seeds[0]], W, prec, len(m_sw), len(m_w), stream)
+            if args.autotune else None)
 
     # The staggered Wilson batch (its FP64 hypercube build and reliable
     # updates are bound by the FP64 pipe) and the Wilson batch (bound by HBM)
@@ -529,6 +559,7 @@ def run_ours(args):
                    "graphs": int(sw.sw_get_param(sw.SW_PARAM_GRAPHS)),
                    "site_blocking": int(sw.sw_get_param(sw.SW_PARAM_SITE_BLOCKING)),
                    "group_fast": int(sw.sw_get_param(sw.SW_PARAM_GROUP_FAST)),
+                   "autotune": tune,
                    "systems_per_thread": {"sw": int(sw.sw_get_param(sw.SW_PARAM_NS_SW)),
                                           "wilson": int(sw.sw_get_param(sw.SW_PARAM_NS_WILSON))},
                    "l2": "inputs larger than L2: a step touches ~10 GB and each step uses a new configuration",

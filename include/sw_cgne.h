@@ -207,6 +207,16 @@ int sw_get_param(int key, double* value);
 int sw_autotune(const sw_lattice* lat, int op, const void* U, const void* W, int nsys, int precision,
                 double r, int iters, double* ms, int* best, void* stream);
 
+/* Autotuner for width x site order (no counterpart in the paper): as
+ * sw_autotune, over the six pairs (NS in {1, 2, 4}) x (SW_PARAM_SITE_BLOCKING
+ * in {0, 1}), and sets the fastest pair: the operator's width and the
+ * process-wide site order of the packed fields.  ms (HOST [6], may be NULL)
+ * receives the times in ms at index 2 k + blocking for the k-th width;
+ * best_ns, best_blocking (HOST, may be NULL) the chosen pair.  On an error
+ * the previous settings are restored. */
+int sw_autotune_layout(const sw_lattice* lat, int op, const void* U, const void* W, int nsys, int precision,
+                       double r, int iters, double* ms, int* best_ns, int* best_blocking, void* stream);
+
 /* Kernel timing.  Instrumentation with no counterpart in the paper.  While
  * enabled, the second iteration of every chunk of CG iterations has its two
  * stencil launches (k1: t = (D+m) p with |t|^2; k2: (D+m)^+ t with the r

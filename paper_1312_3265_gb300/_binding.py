@@ -103,6 +103,9 @@ def lib():
             getattr(L, f).restype = i
         L.sw_autotune.argtypes = [lat, i, vp, vp, i, i, d, i, ctypes.POINTER(d), ctypes.POINTER(i), vp]
         L.sw_autotune.restype = i
+        L.sw_autotune_layout.argtypes = [lat, i, vp, vp, i, i, d, i, ctypes.POINTER(d), ctypes.POINTER(i),
+                                         ctypes.POINTER(i), vp]
+        L.sw_autotune_layout.restype = i
         L.sw_set_param.argtypes = [i, d]
         L.sw_get_param.argtypes = [i, ctypes.POINTER(d)]
         L.sw_set_param.restype = i
@@ -325,3 +328,15 @@ def sw_autotune(dims, op, U, W, nsys, precision=SW_PREC_F32_RELIABLE, r=1.0, ite
     _check(lib().sw_autotune(_lat(dims, t_antiperiodic), int(op), _ptr(U), _ptr(W), int(nsys), int(precision),
                              float(r), int(iters), ms, ctypes.byref(best), _stream(stream)), "sw_autotune")
     return best.value, {1: ms[0], 2: ms[1], 4: ms[2]}
+
+
+def sw_autotune_layout(dims, op, U, W, nsys, precision=SW_PREC_F32_RELIABLE, r=1.0, iters=48,
+                       t_antiperiodic=False, stream=None):
+    """Time register-blocking widths 1, 2, 4 x site orders (lexicographic,
+    blocked) and keep the fastest pair; returns ((ns, blocking), {(ns, blocking): ms})."""
+    ms = (ctypes.c_double * 6)()
+    bns, bblk = ctypes.c_int(), ctypes.c_int()
+    _check(lib().sw_autotune_layout(_lat(dims, t_antiperiodic), int(op), _ptr(U), _ptr(W), int(nsys),
+                                    int(precision), float(r), int(iters), ms, ctypes.byref(bns),
+                                    ctypes.byref(bblk), _stream(stream)), "sw_autotune_layout")
+    return (bns.value, bblk.value), {(w, b): ms[2 * k + b] for k, w in enumerate((1, 2, 4)) for b in (0, 1)}

@@ -1,11 +1,14 @@
-// Autotuner for the register-blocking width of the inner-precision stencils.
+// Autotuners for the layout of the inner-precision stencils.
 //
-// For one operator, precision, lattice and batch size it runs the batched
-// solve with each width NS in {1, 2, 4} for a fixed number of iterations
-// (the tolerance is unreachable, so every candidate does the same work:
-// admission, reliable updates, SW_PARAM_CHUNK-sized chunks of CG iterations)
-// and keeps the fastest as SW_PARAM_NS_SW or SW_PARAM_NS_WILSON.
+// For one operator, precision, lattice and batch size they run the batched
+// solve for a fixed number of iterations (the tolerance is unreachable, so
+// every candidate does the same work: admission, reliable updates,
+// SW_PARAM_CHUNK-sized chunks of CG iterations) with each candidate and keep
+// the fastest: sw_autotune over the register-blocking width NS in {1, 2, 4}
+// (SW_PARAM_NS_SW or SW_PARAM_NS_WILSON), sw_autotune_layout over width x site
+// order (SW_PARAM_SITE_BLOCKING: lexicographic, or 4x4x4x2 blocks).
 #include <chrono>
+#include <vector>
 
 #include "driver.cuh"
 
@@ -28,55 +31,119 @@ static __global__ void fill_hash(double2* p, size_t n, unsigned long long seed) 
 
 using namespace swc;
 
-extern "C" int sw_autotune(const sw_lattice* lat, int op, const void* U, const void* W, int nsys, int precision,
-                           double r, int iters, double* ms, int* best, void* stream) {
-  Geom g;
-  if (int e = make_geom(lat, &g)) return e;
+namespace {
+
+// Best of two timed batched solves of `iters` iterations each (the tolerance
+// is unreachable, so every candidate does the same work), in ms; negative
+// SW_ERR_* code on failure.
+double time_batch(const Geom& g, int op, const void* U, const void* W, int nsys, int precision, double r,
+                  int iters, const std::vector<double>& masses, DevMem& chi, DevMem& x, size_t n, cudaStream_t st) {
+  double tmin = 1e300;
+  for (int rep = 0; rep < 2; ++rep) {
+    cudaMemsetAsync(x.p, 0, sizeof(double2) * n, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
+    const auto t0 = std::chrono::steady_clock::now();
+    SolveArgs a{static_cast<const double2*>(U), static_cast<const double2*>(W), chi.as<double2>(),
+                x.as<double2>(), nsys, masses.data(), r, 1e-30, iters, precision, nullptr, st};
+    const int rc = op == SW_OP_WILSON ? wilson_cgne(g, a) : sw_cgne(g, a);
+    const double t = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (rc < 0) return rc;
+    if (t < tmin) tmin = t;
+  }
+  return tmin;
+}
+
+// Argument checks and the synthetic batch shared by the autotuners.
+int tune_setup(const sw_lattice* lat, int op, const void* U, const void* W, int nsys, int precision, double r,
+               int iters, Geom* g, DevMem& chi, DevMem& x, std::vector<double>& masses, size_t* n,
+               cudaStream_t st) {
+  if (int e = make_geom(lat, g)) return e;
   if (op != SW_OP_STAGGERED_WILSON && op != SW_OP_WILSON) return SW_ERR_ARG;
   if (precision != SW_PREC_F32_RELIABLE && precision != SW_PREC_F16_RELIABLE) return SW_ERR_ARG;
   if (nsys < 1 || nsys > 65535 || iters < 1 || !(r == r)) return SW_ERR_ARG;
-  if (int e = check_buf(U, (size_t)g.V * 576)) return e;
+  if (int e = check_buf(U, (size_t)g->V * 576)) return e;
   if (op == SW_OP_STAGGERED_WILSON)
-    if (int e = check_buf(W, (size_t)g.V * 1152)) return e;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (int e = check_buf(W, (size_t)g->V * 1152)) return e;
   const int nc = op == SW_OP_WILSON ? 12 : 3;
-  const size_t n = (size_t)g.V * nc * nsys;
-  DevMem chi, x;
-  if (!chi.alloc(sizeof(double2) * n, st) || !x.alloc(sizeof(double2) * n, st)) return SW_ERR_OOM;
-  fill_hash<<<sm_count() * 4, 256, 0, st>>>(chi.as<double2>(), n, 12345ull);
+  *n = (size_t)g->V * nc * nsys;
+  if (!chi.alloc(sizeof(double2) * *n, st) || !x.alloc(sizeof(double2) * *n, st)) return SW_ERR_OOM;
+  fill_hash<<<sm_count() * 4, 256, 0, st>>>(chi.as<double2>(), *n, 12345ull);
   note_launches(1);
-  std::vector<double> masses(nsys);
+  masses.resize(nsys);
   for (int i = 0; i < nsys; ++i) masses[i] = 0.05 + 0.1 * (i % 4) / 4.0;
+  return SW_OK;
+}
+
+const int kWidths[3] = {1, 2, 4};
+
+}  // namespace
+
+extern "C" int sw_autotune(const sw_lattice* lat, int op, const void* U, const void* W, int nsys, int precision,
+                           double r, int iters, double* ms, int* best, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Geom g;
+  DevMem chi, x;
+  std::vector<double> masses;
+  size_t n = 0;
+  if (int e = tune_setup(lat, op, U, W, nsys, precision, r, iters, &g, chi, x, masses, &n, st)) return e;
   const int key = op == SW_OP_WILSON ? SW_PARAM_NS_WILSON : SW_PARAM_NS_SW;
   double keep = 0;
   sw_get_param(key, &keep);
-  const int widths[3] = {1, 2, 4};
   double best_ms = 1e300;
   int best_ns = (int)keep;
   for (int k = 0; k < 3; ++k) {
-    sw_set_param(key, widths[k]);
-    double tmin = 1e300;
-    for (int rep = 0; rep < 2; ++rep) {
-      cudaMemsetAsync(x.p, 0, sizeof(double2) * n, st);
-      if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
-      const auto t0 = std::chrono::steady_clock::now();
-      SolveArgs a{static_cast<const double2*>(U), static_cast<const double2*>(W), chi.as<double2>(),
-                  x.as<double2>(), nsys, masses.data(), r, 1e-30, iters, precision, nullptr, st};
-      const int rc = op == SW_OP_WILSON ? wilson_cgne(g, a) : sw_cgne(g, a);
-      const double t = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-      if (rc < 0) {
-        sw_set_param(key, keep);
-        return rc;
-      }
-      if (t < tmin) tmin = t;
+    sw_set_param(key, kWidths[k]);
+    const double t = time_batch(g, op, U, W, nsys, precision, r, iters, masses, chi, x, n, st);
+    if (t < 0) {
+      sw_set_param(key, keep);
+      return (int)t;
     }
-    if (ms) ms[k] = tmin;
-    if (tmin < best_ms) {
-      best_ms = tmin;
-      best_ns = widths[k];
+    if (ms) ms[k] = t;
+    if (t < best_ms) {
+      best_ms = t;
+      best_ns = kWidths[k];
     }
   }
   sw_set_param(key, best_ns);
   if (best) *best = best_ns;
+  return SW_OK;
+}
+
+extern "C" int sw_autotune_layout(const sw_lattice* lat, int op, const void* U, const void* W, int nsys,
+                                  int precision, double r, int iters, double* ms, int* best_ns,
+                                  int* best_blocking, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Geom g;
+  DevMem chi, x;
+  std::vector<double> masses;
+  size_t n = 0;
+  if (int e = tune_setup(lat, op, U, W, nsys, precision, r, iters, &g, chi, x, masses, &n, st)) return e;
+  const int key = op == SW_OP_WILSON ? SW_PARAM_NS_WILSON : SW_PARAM_NS_SW;
+  double keep_ns = 0, keep_blk = 0;
+  sw_get_param(key, &keep_ns);
+  sw_get_param(SW_PARAM_SITE_BLOCKING, &keep_blk);
+  double best_ms = 1e300;
+  int bns = (int)keep_ns, bblk = (int)keep_blk;
+  for (int k = 0; k < 3; ++k)
+    for (int blk = 0; blk < 2; ++blk) {
+      sw_set_param(key, kWidths[k]);
+      sw_set_param(SW_PARAM_SITE_BLOCKING, blk);
+      const double t = time_batch(g, op, U, W, nsys, precision, r, iters, masses, chi, x, n, st);
+      if (t < 0) {
+        sw_set_param(key, keep_ns);
+        sw_set_param(SW_PARAM_SITE_BLOCKING, keep_blk);
+        return (int)t;
+      }
+      if (ms) ms[2 * k + blk] = t;
+      if (t < best_ms) {
+        best_ms = t;
+        bns = kWidths[k];
+        bblk = blk;
+      }
+    }
+  sw_set_param(key, bns);
+  sw_set_param(SW_PARAM_SITE_BLOCKING, bblk);
+  if (best_ns) *best_ns = bns;
+  if (best_blocking) *best_blocking = bblk;
   return SW_OK;
 }
