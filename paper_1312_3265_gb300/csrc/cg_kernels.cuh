@@ -40,6 +40,7 @@ enum SysStatus : int {
   ST_READY = 11         // residual replaced and p refreshed: runs from the next iteration
 };
 
+// Plain data of 8-byte words (moved between device and host as such).
 struct SysState {
   double rr;       // |r|^2 of the iterated residual
   double rr_old;   // previous |r|^2
@@ -58,6 +59,7 @@ struct SysState {
   int status;
   int n_ru;
 };
+static_assert(sizeof(SysState) % 8 == 0, "SysState moves as 8-byte words");
 
 constexpr int kTile = 128;  // sites per reduction tile == threads per stencil block
 

@@ -321,7 +321,9 @@ class Engine {
       }
     }
     cudaMemsetAsync(ws.pcount, 0, sizeof(int) * 2 * kProfSlots, st);
-    cudaMemcpyAsync(ws.S, hr_, sizeof(SysState) * cap, cudaMemcpyHostToDevice, st);
+    hrd_ = mapped_alias(hr_);
+    hstd_ = mapped_alias(hst_);
+    move_states(ws.S, hr_, hrd_, cap, cudaMemcpyHostToDevice);
     chunk_ = param_chunk();
     delta_ = param_delta(std::is_same<VF, VecP16<NC>>::value);
   }
@@ -506,7 +508,7 @@ class Engine {
       }
     }
     if (overlap) cudaStreamWaitEvent(st_, ev_join_, 0);
-    cudaMemcpyAsync(hr_, S, sizeof(SysState) * cap_, cudaMemcpyDeviceToHost, st_);
+    move_states(hr_, S, hrd_, cap_, cudaMemcpyDeviceToHost);
     if (ev_) cudaEventRecord(ev_, st_);
   }
 
@@ -549,14 +551,44 @@ class Engine {
   long long rounds() const { return rounds_; }
 
  private:
+  // Device address of a host status buffer that is pinned and mapped, else
+  // nullptr (ordinary host memory, e.g. the allocation-free entry's).
+  static SysState* mapped_alias(SysState* h) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost && at.devicePointer ? static_cast<SysState*>(at.devicePointer) : nullptr;
+  }
+
+  // n status words between the device and the host buffer `h` (device alias
+  // `hd`), in stream order on the engine's stream: by kernel when the host
+  // buffer is mapped, so the transfer does not wait behind copies the caller
+  // has queued on the copy engines, else by cudaMemcpyAsync.
+  void move_states(SysState* dst, const SysState* src, SysState* hd, int n, cudaMemcpyKind kind) {
+    if (n <= 0) return;
+    if (hd) {
+      const size_t words = sizeof(SysState) / 8 * (size_t)n;
+      const SysState* from = kind == cudaMemcpyHostToDevice ? hd : src;
+      SysState* to = kind == cudaMemcpyHostToDevice ? dst : hd;
+      const int blocks = (int)std::min<size_t>((words + 255) / 256, (size_t)sm_count());
+      copy_words<<<blocks, 256, 0, st_>>>(reinterpret_cast<const unsigned long long*>(from),
+                                          reinterpret_cast<unsigned long long*>(to), words);
+      note_launches(1);
+    } else {
+      cudaMemcpyAsync(dst, src, sizeof(SysState) * n, kind, st_);
+    }
+  }
+
   void upload_staged() {
     std::sort(staged_.begin(), staged_.end());
     size_t a = 0;
     while (a < staged_.size()) {  // one copy per run of consecutive slots
       size_t b = a + 1;
       while (b < staged_.size() && staged_[b] == staged_[b - 1] + 1) ++b;
-      cudaMemcpyAsync(ws_.S + staged_[a], hst_ + staged_[a], sizeof(SysState) * (b - a), cudaMemcpyHostToDevice,
-                      st_);
+      move_states(ws_.S + staged_[a], hst_ + staged_[a], hstd_ ? hstd_ + staged_[a] : nullptr, (int)(b - a),
+                  cudaMemcpyHostToDevice);
       a = b;
     }
     staged_.clear();
@@ -743,6 +775,8 @@ class Engine {
   Workspace ws_;
   SysState* hr_;
   SysState* hst_;
+  SysState* hrd_ = nullptr;   // device alias of hr_ when mapped
+  SysState* hstd_ = nullptr;  // device alias of hst_ when mapped
   cudaStream_t st_;
   cudaEvent_t ev_;
   size_t n_;

@@ -259,4 +259,14 @@ static __global__ void commit_ready(int nsys, SysState* S) {
   if (i < nsys && S[i].status == ST_READY) S[i].status = ST_RUNNING;
 }
 
+// n 8-byte words from src to dst.  Moves the solver's status words between
+// the device and mapped pinned host memory: the kernel's loads and stores
+// cross the host link directly, so these small transfers never queue behind
+// the caller's bulk copies on a copy engine.
+static __global__ void copy_words(const unsigned long long* __restrict__ src, unsigned long long* __restrict__ dst,
+                                  size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
 }  // namespace swc
