@@ -91,7 +91,8 @@ def parse():
     ap.add_argument("--w-sources", type=int, default=12, help="Wilson spin-colour sources per mass (<= 12)")
     ap.add_argument("--dims", default="16x16x16x32", help="lattice L0xL1xL2xL3 (L3 = time)")
     ap.add_argument("--graphs", type=int, default=None, help="1/0: replay chunks as CUDA graphs (library default 1)")
-    ap.add_argument("--site-blocking", type=int, default=None, help="1/0: blocked site order of packed fields")
+    ap.add_argument("--site-blocking", type=int, default=None,
+                    help="site order of the packed fields: 0 lexicographic, 1-5 site-block shapes")
     ap.add_argument("--group-fast", type=int, default=None, help="1/0: system groups fastest in the stencil grid")
     ap.add_argument("--autotune", action="store_true",
                     help="before the warm-up, pick each operator's systems per thread and the shared site order "
@@ -286,8 +287,9 @@ def classify_kernels(prof, hbm_peak, peak_kind):
 def autotune_layout(sw, dims, Ud, W, prec, n_sw, n_w, stream, iters=48):
     """Width x site order for this step's batches: sw_autotune_layout per
     operator on the first configuration, then the site order (one setting for
-    both operators) with the smaller sum of the operators' best times, and per
-    operator the fastest width under that order."""
+    both operators: lexicographic or a site-block shape) with the smallest sum
+    of the operators' best times, and per operator the fastest width under
+    that order."""
     if prec == sw.SW_PREC_F64:
         return {"skipped": "the FP64 path has one layout"}
     times = {}
@@ -298,14 +300,15 @@ def autotune_layout(sw, dims, Ud, W, prec, n_sw, n_w, stream, iters=48):
     if n_w:
         _, times["wilson"] = sw.sw_autotune_layout(dims, sw.SW_OP_WILSON, Ud, None, n_w, prec, R_WILSON, iters,
                                                    stream=stream)
-    total = {b: sum(min(t[(w, b)] for w in (1, 2, 4)) for t in times.values()) for b in (0, 1)}
+    shapes = range(sw.SW_SITE_SHAPES)
+    total = {b: sum(min(t[(w, b)] for w in (1, 2, 4)) for t in times.values()) for b in shapes}
     blk = min(total, key=total.get)
     sw.sw_set_param(sw.SW_PARAM_SITE_BLOCKING, blk)
     keys = {"sw": sw.SW_PARAM_NS_SW, "wilson": sw.SW_PARAM_NS_WILSON}
     for op, t in times.items():
         sw.sw_set_param(keys[op], min((1, 2, 4), key=lambda w: t[(w, blk)]))
     return {"iters": iters, "site_blocking": blk,
-            "ms": {op: {f"ns{w}_blk{b}": round(v, 2) for (w, b), v in sorted(t.items())} for op, t in times.items()}}
+            "ms": {op: {f"ns{w}_shape{b}": round(v, 2) for (w, b), v in sorted(t.items())} for op, t in times.items()}}
 
 
 def run_ours(args):

@@ -180,9 +180,12 @@ int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, const void*
  *   graph captured once per solve or server engine (one launch instead of
  *   3 per iteration); 0 launches the kernels one by one.  cgne_solve_noalloc
  *   never uses graphs.
- * SW_PARAM_SITE_BLOCKING: 1 stores the packed FP32/FP16 fields in blocks of
- *   up to 4x4x4x2 sites (each block contiguous), 0 (default) in lexicographic
- *   order.
+ * SW_PARAM_SITE_BLOCKING: site order of the packed FP32/FP16 fields: 0
+ *   (default) lexicographic; 1..SW_SITE_SHAPES-1 store them in blocks of sites,
+ *   each block contiguous, of at most 1: 4x4x4x2, 2: 8x4x2x2, 3: 8x8x2x1,
+ *   4: 2x4x4x4, 5: 4x4x2x4 sites (x0 x x1 x x2 x x3; in each direction the
+ *   largest power of two up to that extent dividing the lattice extent).  A
+ *   call takes the value current when it starts.
  * SW_PARAM_GROUP_FAST: 1 makes the system groups the fastest grid dimension
  *   of the stencil kernels, 0 (default) the tiles.
  * None of these changes what a solve converges to: convergence is always
@@ -191,6 +194,7 @@ int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, const void*
 enum { SW_PARAM_CHUNK = 0, SW_PARAM_RELIABLE_DELTA = 1, SW_PARAM_NS_SW = 2, SW_PARAM_NS_WILSON = 3,
        SW_PARAM_GRAPHS = 4, SW_PARAM_SITE_BLOCKING = 5, SW_PARAM_GROUP_FAST = 6,
        SW_PARAM_RELIABLE_DELTA_F16 = 9 };
+enum { SW_SITE_SHAPES = 6 };
 int sw_set_param(int key, double value);
 int sw_get_param(int key, double* value);
 
@@ -208,14 +212,15 @@ int sw_autotune(const sw_lattice* lat, int op, const void* U, const void* W, int
                 double r, int iters, double* ms, int* best, void* stream);
 
 /* Autotuner for width x site order (no counterpart in the paper): as
- * sw_autotune, over the six pairs (NS in {1, 2, 4}) x (SW_PARAM_SITE_BLOCKING
- * in {0, 1}), and sets the fastest pair: the operator's width and the
- * process-wide site order of the packed fields.  ms (HOST [6], may be NULL)
- * receives the times in ms at index 2 k + blocking for the k-th width;
- * best_ns, best_blocking (HOST, may be NULL) the chosen pair.  On an error
- * the previous settings are restored. */
+ * sw_autotune, over the 3 x SW_SITE_SHAPES pairs (NS in {1, 2, 4}) x
+ * (SW_PARAM_SITE_BLOCKING in 0..SW_SITE_SHAPES-1), and sets the fastest pair:
+ * the operator's width and the process-wide site order of the packed fields.
+ * ms (HOST [3 SW_SITE_SHAPES], may be NULL) receives the times in ms at index
+ * k SW_SITE_SHAPES + shape for the k-th width; best_ns, best_shape (HOST, may
+ * be NULL) the chosen pair.  On an error the width is restored and the site
+ * order left unchanged. */
 int sw_autotune_layout(const sw_lattice* lat, int op, const void* U, const void* W, int nsys, int precision,
-                       double r, int iters, double* ms, int* best_ns, int* best_blocking, void* stream);
+                       double r, int iters, double* ms, int* best_ns, int* best_shape, void* stream);
 
 /* Kernel timing.  Instrumentation with no counterpart in the paper.  While
  * enabled, the second iteration of every chunk of CG iterations has its two

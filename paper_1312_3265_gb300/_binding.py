@@ -22,6 +22,7 @@ SW_PARAM_GRAPHS = 4
 SW_PARAM_SITE_BLOCKING = 5
 SW_PARAM_GROUP_FAST = 6
 SW_PARAM_RELIABLE_DELTA_F16 = 9
+SW_SITE_SHAPES = 6  # SW_PARAM_SITE_BLOCKING values: 0 lexicographic, 1..5 site-block shapes
 
 
 class Lattice(ctypes.Structure):
@@ -332,11 +333,13 @@ def sw_autotune(dims, op, U, W, nsys, precision=SW_PREC_F32_RELIABLE, r=1.0, ite
 
 def sw_autotune_layout(dims, op, U, W, nsys, precision=SW_PREC_F32_RELIABLE, r=1.0, iters=48,
                        t_antiperiodic=False, stream=None):
-    """Time register-blocking widths 1, 2, 4 x site orders (lexicographic,
-    blocked) and keep the fastest pair; returns ((ns, blocking), {(ns, blocking): ms})."""
-    ms = (ctypes.c_double * 6)()
-    bns, bblk = ctypes.c_int(), ctypes.c_int()
+    """Time register-blocking widths 1, 2, 4 x site orders 0..SW_SITE_SHAPES-1
+    (lexicographic, then the site-block shapes) and keep the fastest pair;
+    returns ((ns, shape), {(ns, shape): ms})."""
+    ms = (ctypes.c_double * (3 * SW_SITE_SHAPES))()
+    bns, bshape = ctypes.c_int(), ctypes.c_int()
     _check(lib().sw_autotune_layout(_lat(dims, t_antiperiodic), int(op), _ptr(U), _ptr(W), int(nsys),
                                     int(precision), float(r), int(iters), ms, ctypes.byref(bns),
-                                    ctypes.byref(bblk), _stream(stream)), "sw_autotune_layout")
-    return (bns.value, bblk.value), {(w, b): ms[2 * k + b] for k, w in enumerate((1, 2, 4)) for b in (0, 1)}
+                                    ctypes.byref(bshape), _stream(stream)), "sw_autotune_layout")
+    return (bns.value, bshape.value), {(w, b): ms[k * SW_SITE_SHAPES + b] for k, w in enumerate((1, 2, 4))
+                                        for b in range(SW_SITE_SHAPES)}

@@ -103,7 +103,7 @@ int param_chunk() { return g_param_chunk.load(); }
 double param_delta(bool half) { return half ? g_param_delta16.load() : g_param_delta.load(); }
 int param_ns(int nc) { return nc == 3 ? g_param_ns_sw.load() : g_param_ns_wilson.load(); }
 bool param_graphs() { return g_param_graphs.load() != 0; }
-bool param_site_blocking() { return g_param_site_block.load() != 0; }
+int param_site_shape() { return g_param_site_block.load(); }
 bool param_group_fast() { return g_param_group_fast.load() != 0; }
 
 void prof_flush() {
@@ -140,6 +140,7 @@ int make_geom(const sw_lattice* lat, Geom* g) {
   for (int mu = 1; mu < 4; ++mu) g->stride[mu] = g->stride[mu - 1] * g->L[mu - 1];
   g->V = (int)V;
   g->apbc = lat->t_antiperiodic ? 1 : 0;
+  g->shape = param_site_shape();
   return SW_OK;
 }
 
@@ -225,12 +226,13 @@ int sw_set_param(int key, double value) {
       (key == SW_PARAM_RELIABLE_DELTA ? g_param_delta : g_param_delta16).store(value);
       return SW_OK;
     case SW_PARAM_GRAPHS:
-    case SW_PARAM_SITE_BLOCKING:
     case SW_PARAM_GROUP_FAST:
       if (!(value == 0 || value == 1)) return SW_ERR_ARG;
-      (key == SW_PARAM_GRAPHS ? g_param_graphs
-                              : key == SW_PARAM_SITE_BLOCKING ? g_param_site_block : g_param_group_fast)
-          .store((int)value);
+      (key == SW_PARAM_GRAPHS ? g_param_graphs : g_param_group_fast).store((int)value);
+      return SW_OK;
+    case SW_PARAM_SITE_BLOCKING:
+      if (!(value >= 0 && value < SW_SITE_SHAPES && value == (int)value)) return SW_ERR_ARG;
+      g_param_site_block.store((int)value);
       return SW_OK;
     case SW_PARAM_NS_SW:
     case SW_PARAM_NS_WILSON:

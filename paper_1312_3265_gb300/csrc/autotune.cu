@@ -6,7 +6,7 @@
 // SW_PARAM_CHUNK-sized chunks of CG iterations) with each candidate and keep
 // the fastest: sw_autotune over the register-blocking width NS in {1, 2, 4}
 // (SW_PARAM_NS_SW or SW_PARAM_NS_WILSON), sw_autotune_layout over width x site
-// order (SW_PARAM_SITE_BLOCKING: lexicographic, or 4x4x4x2 blocks).
+// order (SW_PARAM_SITE_BLOCKING: lexicographic or one of the site-block shapes).
 #include <chrono>
 #include <vector>
 
@@ -75,6 +75,7 @@ int tune_setup(const sw_lattice* lat, int op, const void* U, const void* W, int 
 }
 
 const int kWidths[3] = {1, 2, 4};
+static_assert(kSiteShapes == SW_SITE_SHAPES, "site-shape menu of the C ABI");
 
 }  // namespace
 
@@ -111,7 +112,7 @@ extern "C" int sw_autotune(const sw_lattice* lat, int op, const void* U, const v
 
 extern "C" int sw_autotune_layout(const sw_lattice* lat, int op, const void* U, const void* W, int nsys,
                                   int precision, double r, int iters, double* ms, int* best_ns,
-                                  int* best_blocking, void* stream) {
+                                  int* best_shape, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Geom g;
   DevMem chi, x;
@@ -119,31 +120,31 @@ extern "C" int sw_autotune_layout(const sw_lattice* lat, int op, const void* U, 
   size_t n = 0;
   if (int e = tune_setup(lat, op, U, W, nsys, precision, r, iters, &g, chi, x, masses, &n, st)) return e;
   const int key = op == SW_OP_WILSON ? SW_PARAM_NS_WILSON : SW_PARAM_NS_SW;
-  double keep_ns = 0, keep_blk = 0;
+  double keep_ns = 0, keep_shape = 0;
   sw_get_param(key, &keep_ns);
-  sw_get_param(SW_PARAM_SITE_BLOCKING, &keep_blk);
+  sw_get_param(SW_PARAM_SITE_BLOCKING, &keep_shape);
   double best_ms = 1e300;
-  int bns = (int)keep_ns, bblk = (int)keep_blk;
+  int bns = (int)keep_ns, bshape = (int)keep_shape;
   for (int k = 0; k < 3; ++k)
-    for (int blk = 0; blk < 2; ++blk) {
+    for (int shape = 0; shape < SW_SITE_SHAPES; ++shape) {
       sw_set_param(key, kWidths[k]);
-      sw_set_param(SW_PARAM_SITE_BLOCKING, blk);
-      const double t = time_batch(g, op, U, W, nsys, precision, r, iters, masses, chi, x, n, st);
+      Geom gs = g;  // the candidate's site order (a solve takes it from its Geom)
+      gs.shape = shape;
+      const double t = time_batch(gs, op, U, W, nsys, precision, r, iters, masses, chi, x, n, st);
       if (t < 0) {
         sw_set_param(key, keep_ns);
-        sw_set_param(SW_PARAM_SITE_BLOCKING, keep_blk);
         return (int)t;
       }
-      if (ms) ms[2 * k + blk] = t;
+      if (ms) ms[k * SW_SITE_SHAPES + shape] = t;
       if (t < best_ms) {
         best_ms = t;
         bns = kWidths[k];
-        bblk = blk;
+        bshape = shape;
       }
     }
   sw_set_param(key, bns);
-  sw_set_param(SW_PARAM_SITE_BLOCKING, bblk);
+  sw_set_param(SW_PARAM_SITE_BLOCKING, bshape);
   if (best_ns) *best_ns = bns;
-  if (best_blocking) *best_blocking = bblk;
+  if (best_shape) *best_shape = bshape;
   return SW_OK;
 }

@@ -135,6 +135,7 @@ struct Geom {
   int stride[4];  // 1, L0, L0 L1, L0 L1 L2
   int V;
   int apbc;       // antiperiodic fermion BC in time
+  int shape;      // site-block shape of the packed inner-precision fields (see site_shape), fixed per call
 };
 
 __host__ __device__ inline void coords(const Geom& g, int n, int x[4]) {
@@ -157,12 +158,12 @@ __device__ __forceinline__ bool bc_flip(const Geom& g, const int x[4], int s) {
 }
 
 // Blocked site order of the inner-precision (FP32/FP16) packed storage: the
-// lattice is cut into blocks of B0 x B1 x B2 x B3 sites (powers of two up to
-// 4, 4, 4, 2), stored one after the other in lexicographic block order, the
-// sites of a block contiguous in lexicographic order inside it.  A 128-site
-// tile then covers a compact 4-D region, so most of a site's neighbours lie
-// in the tile its block has just loaded.  The index is a sum of one term per
-// direction, so a hop changes one term: n = sum_mu (b_mu bs_mu + l_mu ls_mu).
+// lattice is cut into blocks of B0 x B1 x B2 x B3 sites (powers of two),
+// stored one after the other in lexicographic block order, the sites of a
+// block contiguous in lexicographic order inside it.  A 128-site tile then
+// covers a compact 4-D region, so more of a site's neighbours lie in the tile
+// its block has just loaded.  The index is a sum of one term per direction,
+// so a hop changes one term: n = sum_mu (b_mu bs_mu + l_mu ls_mu).
 struct GeomBlk {
   int L[4];
   int lb[4];     // log2 B_mu
@@ -173,10 +174,23 @@ struct GeomBlk {
   int apbc;
 };
 
-// blocking = false gives B = 1 everywhere, i.e. the lexicographic order.
-__host__ __device__ inline GeomBlk make_blocked(const Geom& g, bool blocking = true) {
+// Site-block shapes (largest extents B0 x B1 x B2 x B3; shape 0 is the
+// lexicographic order).  Each 128-site shape fills one reduction tile.
+constexpr int kSiteShapes = 6;
+__host__ __device__ inline void site_shape(int shape, int B[4]) {
+  constexpr int kShapes[kSiteShapes][4] = {{1, 1, 1, 1}, {4, 4, 4, 2}, {8, 4, 2, 2},
+                                           {8, 8, 2, 1}, {2, 4, 4, 4}, {4, 4, 2, 4}};
+  const int k = (shape >= 0 && shape < kSiteShapes) ? shape : 0;
+  for (int mu = 0; mu < 4; ++mu) B[mu] = kShapes[k][mu];
+}
+
+// Blocked geometry of `shape`: in each direction the block extent is the
+// largest power of two up to the shape's that divides the lattice extent.
+// shape 0 gives B = 1 everywhere, i.e. the lexicographic order.
+__host__ __device__ inline GeomBlk make_blocked(const Geom& g, int shape) {
   GeomBlk b;
-  const int cap[4] = {blocking ? 4 : 1, blocking ? 4 : 1, blocking ? 4 : 1, blocking ? 2 : 1};
+  int cap[4];
+  site_shape(shape, cap);
   int bsz = 1;
   for (int mu = 0; mu < 4; ++mu) {
     int B = 1, lg = 0;

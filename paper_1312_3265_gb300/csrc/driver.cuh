@@ -35,7 +35,6 @@ namespace swc {
 int param_chunk();
 double param_delta(bool half);
 int param_ns(int nc);  // systems per thread of the FP32 stencils (1, 2 or 4) for NC components
-bool param_site_blocking();  // blocked site order for the packed FP32/FP16 storage
 bool param_group_fast();     // system groups as the fastest grid dimension of the stencils
 bool param_graphs();   // replay chunks of iterations as captured CUDA graphs
 
@@ -281,7 +280,7 @@ class Engine {
         st_(st), ev_(ev), n_((size_t)g.V * NC), use_graphs_(use_graphs && param_graphs()) {
     ntiles_ = (g.V + kTile - 1) / kTile;
     pstride_ = kWarps * ntiles_;
-    gb_ = make_blocked(g, param_site_blocking());
+    gb_ = make_blocked(g, g.shape);
     if constexpr (MIXED) gk_ = gb_;
     else gk_ = g;
     gfast_ = param_group_fast() ? 1 : 0;

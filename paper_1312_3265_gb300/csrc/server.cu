@@ -183,8 +183,8 @@ static int make_engine(const Geom& g, int op, const double2* U, double r, int pr
         __half2* u16 = (__half2*)own(owned, V * 96, st);
         __half2* w16 = (__half2*)own(owned, V * 288, st);
         if (!u16 || !w16) return (int)SW_ERR_OOM;
-        pack_links_h12<<<gp, 256, 0, st>>>(make_blocked(g, param_site_blocking()), Ur, u16);
-        pack_mats_h<<<gp, 256, 0, st>>>(make_blocked(g, param_site_blocking()), 8, Wr, w16);
+        pack_links_h12<<<gp, 256, 0, st>>>(make_blocked(g, g.shape), Ur, u16);
+        pack_mats_h<<<gp, 256, 0, st>>>(make_blocked(g, g.shape), 8, Wr, w16);
         note_launches(2);
         *d = SW64{GaugeC64{Ur}, TransC64{Wr}};
         *f = SW16{GaugeP16{u16}, TransP16{w16}};
@@ -196,8 +196,8 @@ static int make_engine(const Geom& g, int op, const double2* U, double r, int pr
       float2* u32 = (float2*)own(owned, V * 288, st);
       float2* w32 = (float2*)own(owned, V * 576, st);
       if (!u32 || !w32) return (int)SW_ERR_OOM;
-      pack_mats_p32<<<gp, 256, 0, st>>>(make_blocked(g, param_site_blocking()), 4, Ur, u32);
-      pack_mats_p32<<<gp, 256, 0, st>>>(make_blocked(g, param_site_blocking()), 8, Wr, w32);
+      pack_mats_p32<<<gp, 256, 0, st>>>(make_blocked(g, g.shape), 4, Ur, u32);
+      pack_mats_p32<<<gp, 256, 0, st>>>(make_blocked(g, g.shape), 8, Wr, w32);
       note_launches(2);
       *d = SW64{GaugeC64{Ur}, TransC64{Wr}};
       *f = SW32{GaugeP32{u32}, TransP32{w32}};
@@ -222,7 +222,7 @@ static int make_engine(const Geom& g, int op, const double2* U, double r, int pr
         if (int e = check_su3(g, Ur, st)) return e;
         __half2* u16 = (__half2*)own(owned, V * 96, st);
         if (!u16) return (int)SW_ERR_OOM;
-        pack_links_h12<<<gp, 256, 0, st>>>(make_blocked(g, param_site_blocking()), Ur, u16);
+        pack_links_h12<<<gp, 256, 0, st>>>(make_blocked(g, g.shape), Ur, u16);
         note_launches(1);
         *d = W64<R1>{GaugeC64{Ur}};
         *f = W16<R1>{GaugeP16{u16}};
@@ -234,7 +234,7 @@ static int make_engine(const Geom& g, int op, const double2* U, double r, int pr
       if (int e = copy_links(owned, st, &Ur)) return e;
       float2* u32 = (float2*)own(owned, V * 288, st);
       if (!u32) return (int)SW_ERR_OOM;
-      pack_mats_p32<<<gp, 256, 0, st>>>(make_blocked(g, param_site_blocking()), 4, Ur, u32);
+      pack_mats_p32<<<gp, 256, 0, st>>>(make_blocked(g, g.shape), 4, Ur, u32);
       note_launches(1);
       *d = W64<R1>{GaugeC64{Ur}};
       *f = W32<R1>{GaugeP32{u32}};

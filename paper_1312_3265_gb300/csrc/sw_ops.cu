@@ -28,8 +28,8 @@ int sw_cgne(const Geom& g, const SolveArgs& a) {
         !mw.alloc(sizeof(float2) * 72 * (size_t)g.V, a.stream))
       return SW_ERR_OOM;
     const int gp = sm_count() * 8;
-    pack_mats_p32<<<gp, 256, 0, a.stream>>>(make_blocked(g, param_site_blocking()), 4, a.U, mu.as<float2>());
-    pack_mats_p32<<<gp, 256, 0, a.stream>>>(make_blocked(g, param_site_blocking()), 8, a.W, mw.as<float2>());
+    pack_mats_p32<<<gp, 256, 0, a.stream>>>(make_blocked(g, g.shape), 4, a.U, mu.as<float2>());
+    pack_mats_p32<<<gp, 256, 0, a.stream>>>(make_blocked(g, g.shape), 8, a.W, mw.as<float2>());
     note_launches(2);
     const SW32 opf{GaugeP32{mu.as<float2>()}, TransP32{mw.as<float2>()}};
     return run_cgne<SW64, SW32, true>(g, opd, opf, a);
@@ -41,8 +41,8 @@ int sw_cgne(const Geom& g, const SolveArgs& a) {
         !mw.alloc(sizeof(__half2) * 72 * (size_t)g.V, a.stream))
       return SW_ERR_OOM;
     const int gp = sm_count() * 8;
-    pack_links_h12<<<gp, 256, 0, a.stream>>>(make_blocked(g, param_site_blocking()), a.U, mu.as<__half2>());
-    pack_mats_h<<<gp, 256, 0, a.stream>>>(make_blocked(g, param_site_blocking()), 8, a.W, mw.as<__half2>());
+    pack_links_h12<<<gp, 256, 0, a.stream>>>(make_blocked(g, g.shape), a.U, mu.as<__half2>());
+    pack_mats_h<<<gp, 256, 0, a.stream>>>(make_blocked(g, g.shape), 8, a.W, mw.as<__half2>());
     note_launches(2);
     const SW16 opf{GaugeP16{mu.as<__half2>()}, TransP16{mw.as<__half2>()}};
     return run_cgne<SW64, SW16, true>(g, opd, opf, a);

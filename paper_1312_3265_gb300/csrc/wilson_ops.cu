@@ -34,7 +34,7 @@ static int cgne_impl(const Geom& g, const SolveArgs& a) {
   if (a.precision == SW_PREC_F32_RELIABLE) {
     DevMem mu;
     if (!mu.alloc(sizeof(float2) * 36 * (size_t)g.V, a.stream)) return SW_ERR_OOM;
-    pack_mats_p32<<<sm_count() * 8, 256, 0, a.stream>>>(make_blocked(g, param_site_blocking()), 4, a.U, mu.as<float2>());
+    pack_mats_p32<<<sm_count() * 8, 256, 0, a.stream>>>(make_blocked(g, g.shape), 4, a.U, mu.as<float2>());
     note_launches(1);
     const W32<R1> opf{GaugeP32{mu.as<float2>()}};
     return run_cgne<W64<R1>, W32<R1>, true>(g, opd, opf, a);
@@ -43,7 +43,7 @@ static int cgne_impl(const Geom& g, const SolveArgs& a) {
     if (int e = check_su3(g, a.U, a.stream)) return e;
     DevMem mu;
     if (!mu.alloc(sizeof(__half2) * 24 * (size_t)g.V, a.stream)) return SW_ERR_OOM;
-    pack_links_h12<<<sm_count() * 8, 256, 0, a.stream>>>(make_blocked(g, param_site_blocking()), a.U, mu.as<__half2>());
+    pack_links_h12<<<sm_count() * 8, 256, 0, a.stream>>>(make_blocked(g, g.shape), a.U, mu.as<__half2>());
     note_launches(1);
     const W16<R1> opf{GaugeP16{mu.as<__half2>()}};
     return run_cgne<W64<R1>, W16<R1>, true>(g, opd, opf, a);

@@ -4,7 +4,8 @@
 // index of the lexicographic neighbour, for every site, direction and sign
 // (periodic wrap included); the per-site offsets reach all 16 hypercube
 // corners x +- s in both orders; the packed (AoSoA-16) unit index is a
-// bijection.  Prints "ok" or the first mismatch.
+// bijection.  Every site-block shape of the menu, on lattices whose extents
+// the shapes divide and do not divide.  Prints "ok" or the first mismatch.
 #include <cstdio>
 #include <vector>
 
@@ -13,13 +14,14 @@
 
 using namespace swc;
 
-static int check(int L0, int L1, int L2, int L3) {
+static int check(int L0, int L1, int L2, int L3, int shape) {
   Geom g;
   g.L[0] = L0; g.L[1] = L1; g.L[2] = L2; g.L[3] = L3;
   g.stride[0] = 1; g.stride[1] = L0; g.stride[2] = L0 * L1; g.stride[3] = L0 * L1 * L2;
   g.V = L0 * L1 * L2 * L3;
   g.apbc = 0;
-  const GeomBlk b = make_blocked(g);
+  g.shape = shape;
+  const GeomBlk b = make_blocked(g, shape);
   std::vector<int> seen(g.V, 0);
   for (int n = 0; n < g.V; ++n) {
     int x[4] = {n % L0, (n / L0) % L1, (n / (L0 * L1)) % L2, n / (L0 * L1 * L2)};
@@ -64,6 +66,7 @@ static int check(int L0, int L1, int L2, int L3) {
       }
     }
   }
+  if (shape != 1) return 0;
   // packed unit index: a bijection of (site, plane) onto [0, V npl)
   for (int npl : {3, 6, 12, 24, 36, 72}) {
     std::vector<char> hit((size_t)g.V * npl, 0);
@@ -80,7 +83,11 @@ int main() {
   const int dims[][4] = {{2, 2, 2, 2}, {4, 4, 4, 4}, {6, 6, 4, 6}, {16, 16, 16, 32}, {2, 4, 6, 2}, {10, 4, 6, 10},
                          {24, 24, 24, 48}, {12, 12, 12, 24}, {8, 8, 8, 8}};
   for (auto& d : dims)
-    if (check(d[0], d[1], d[2], d[3])) return 1;
+    for (int shape = 0; shape < kSiteShapes; ++shape)
+      if (check(d[0], d[1], d[2], d[3], shape)) {
+        printf("(site-block shape %d)\n", shape);
+        return 1;
+      }
   printf("ok\n");
   return 0;
 }

@@ -317,15 +317,16 @@ def test_autotune_picks_a_width_and_solves(sw):
 
 @pytest.mark.parametrize("op", ["sw", "wilson"])
 def test_autotune_layout_picks_width_and_site_order(sw, op):
-    """The width x site-order autotuner times all six pairs, sets the
-    fastest, and the solver then converges with that layout."""
+    """The width x site-order autotuner times every pair (3 widths x the
+    lexicographic order and the site-block shapes), sets the fastest, and the
+    solver then converges with that layout."""
     P = (Problem(sw, (8, 8, 8, 8), sw.SW_OP_STAGGERED_WILSON, 4, ls.PLAQ_EPS, 0.1) if op == "sw"
          else Problem(sw, (8, 8, 8, 8), sw.SW_OP_WILSON, 4, ls.PLAQ_EPS, 0.1))
     key = sw.SW_PARAM_NS_SW if op == "sw" else sw.SW_PARAM_NS_WILSON
     old = (sw.sw_get_param(key), sw.sw_get_param(sw.SW_PARAM_SITE_BLOCKING))
     try:
         best, times = sw.sw_autotune_layout(P.dims, P.op, P.U, P.W, 5, sw.SW_PREC_F32_RELIABLE, iters=24)
-        assert set(times) == {(w, b) for w in (1, 2, 4) for b in (0, 1)}
+        assert set(times) == {(w, b) for w in (1, 2, 4) for b in range(sw.SW_SITE_SHAPES)}
         assert best in times and times[best] == min(times.values()) and all(t > 0 for t in times.values())
         assert (sw.sw_get_param(key), sw.sw_get_param(sw.SW_PARAM_SITE_BLOCKING)) == best
         nc = 3 if op == "sw" else 12
@@ -336,12 +337,12 @@ def test_autotune_layout_picks_width_and_site_order(sw, op):
         sw.sw_set_param(sw.SW_PARAM_SITE_BLOCKING, old[1])
 
 
-@pytest.mark.parametrize("blocking", [0, 1])
+@pytest.mark.parametrize("blocking", range(6))
 @pytest.mark.parametrize("gfast", [0, 1])
 def test_site_order_and_grid_order(sw, blocking, gfast):
-    """The packed fields' site order (blocked or lexicographic) and the stencil
-    grid order solve the same systems; the grid order does not even change a
-    bit (the reductions go over the same site tiles)."""
+    """The packed fields' site order (lexicographic or any site-block shape)
+    and the stencil grid order solve the same systems; the grid order does not
+    even change a bit (the reductions go over the same site tiles)."""
     import torch
     P = Problem(sw, (8, 4, 6, 8), sw.SW_OP_STAGGERED_WILSON, 6, ls.PLAQ_EPS, 0.07, apbc=True)
     chis = np.stack([ls.gaussian_source(P.dims, 3, 70 + i) for i in range(5)])
