@@ -248,6 +248,18 @@ int sw_autotune_layout(const sw_lattice* lat, int op, const void* U, const void*
 int sw_profile_enable(int on);
 /* Total kernel launches this library has issued in the process (always on). */
 long long sw_kernel_launches(void);
+
+/* Device workspace cache (no counterpart in the paper).  The solves, the
+ * server and the autotuners take their device workspace from one
+ * stream-ordered memory pool per device, which keeps freed blocks for the
+ * next call (so a solve does not map its workspace anew).
+ * sw_workspace_reserved: device bytes the pool of the current device holds,
+ * in use or cached, into *bytes (HOST).  sw_trim_workspace: hands the cached,
+ * unused bytes of that pool back to the driver; blocks still in use (a solve
+ * in flight, a server's engines) stay.  Both return SW_OK, SW_ERR_NULL or
+ * SW_ERR_CUDA. */
+int sw_workspace_reserved(unsigned long long* bytes);
+int sw_trim_workspace(void);
 int sw_profile_reset(void);
 /* Number of classes recorded so far. */
 int sw_profile_count(void);

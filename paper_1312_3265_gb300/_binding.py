@@ -113,6 +113,10 @@ def lib():
         L.sw_get_param.restype = i
         L.sw_kernel_launches.argtypes = []
         L.sw_kernel_launches.restype = ctypes.c_longlong
+        L.sw_workspace_reserved.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
+        L.sw_workspace_reserved.restype = i
+        L.sw_trim_workspace.argtypes = []
+        L.sw_trim_workspace.restype = i
         L.sw_profile_enable.argtypes = [i]
         L.sw_profile_reset.argtypes = []
         L.sw_profile_count.argtypes = []
@@ -236,6 +240,18 @@ def sw_profile_read():
 
 def sw_kernel_launches():
     return int(lib().sw_kernel_launches())
+
+
+def sw_workspace_reserved():
+    """Device bytes the library's workspace pool on the current device holds (in use or cached)."""
+    v = ctypes.c_ulonglong()
+    _check(lib().sw_workspace_reserved(ctypes.byref(v)), "sw_workspace_reserved")
+    return int(v.value)
+
+
+def sw_trim_workspace():
+    """Hand the cached, unused device workspace of the current device back to the driver."""
+    _check(lib().sw_trim_workspace(), "sw_trim_workspace")
 
 
 def cgne_solve_noalloc(dims, op, U, W, chi, x, mass, r=1.0, tol=1e-8, max_iter=100000, t_antiperiodic=False,

@@ -13,6 +13,31 @@
 
 namespace swc {
 
+
+cudaMemPool_t lib_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    unsigned long long keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pool;
+  }
+  return pools[dev];
+}
+
 int sm_count() {
   static int cached[64] = {0};
   int dev = 0;
@@ -260,6 +285,24 @@ int sw_get_param(int key, double* value) {
 }
 
 long long sw_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int sw_trim_workspace(void) {
+  cudaMemPool_t pool = lib_pool();
+  if (!pool) return SW_ERR_CUDA;
+  if (const cudaError_t e = cudaMemPoolTrimTo(pool, 0); e != cudaSuccess) return cuda_fail(e);
+  return SW_OK;
+}
+
+int sw_workspace_reserved(unsigned long long* bytes) {
+  if (!bytes) return SW_ERR_NULL;
+  cudaMemPool_t pool = lib_pool();
+  if (!pool) return SW_ERR_CUDA;
+  unsigned long long v = 0;
+  if (const cudaError_t e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v); e != cudaSuccess)
+    return cuda_fail(e);
+  *bytes = (unsigned long long)v;
+  return SW_OK;
+}
 
 int sw_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -73,7 +73,9 @@ struct DevMem {
   }
   bool alloc(size_t bytes, cudaStream_t st) {
     s = st;
-    return cudaMallocAsync(&p, bytes ? bytes : 16, st) == cudaSuccess;
+    cudaMemPool_t pool = lib_pool();
+    if (!pool) return false;
+    return cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, pool, st) == cudaSuccess;
   }
   template <typename T> T* as() const { return static_cast<T*>(p); }
 };
@@ -107,6 +109,26 @@ inline int pinned_states(int nsys, SysState** out) {
   }
   *out = buf;
   return SW_OK;
+}
+
+// Pinned, mapped host buffer for the CG coefficient histories of one solve
+// (per host thread, grown as needed; nullptr above 256 MB: such batches read
+// them into ordinary host memory).
+inline double* pinned_hist(size_t n) {
+  thread_local double* buf = nullptr;
+  thread_local size_t cap = 0;
+  if (n * sizeof(double) > (256u << 20)) return nullptr;
+  if (n > cap) {
+    if (buf) cudaFreeHost(buf);
+    buf = nullptr;
+    cap = 0;
+    if (cudaMallocHost((void**)&buf, sizeof(double) * n) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    cap = n;
+  }
+  return buf;
 }
 
 inline int status_to_code(int st) {
@@ -834,7 +856,7 @@ inline int worst_code(int worst, int code) {
 // staging).
 template <class OpD, class OpF, bool MIXED>
 int run_cgne_ws(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a, const Workspace& ws,
-                SysState* hs, bool use_graphs = true) {
+                SysState* hs, bool use_graphs = true, double* hist_host = nullptr) {
   using namespace std::chrono;
   const auto t0 = steady_clock::now();
   Engine<OpD, OpF, MIXED> e(g, opd, opf, a.r, a.nsys, const_cast<double2*>(a.chi), a.x, ws, hs, hs + a.nsys,
@@ -854,18 +876,35 @@ int run_cgne_ws(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& 
   }
   e.flush_profile();
   prof_flush();
-  std::vector<double> hh;
+  // the CG coefficients, for the Ritz values: by kernel into mapped pinned
+  // memory when the caller has such a buffer (so the read does not queue
+  // behind bulk copies on a copy engine), else by cudaMemcpyAsync
+  std::vector<double> hv;
+  const double* hh = nullptr;
   if (a.infos) {
-    hh.resize((size_t)2 * kHist * a.nsys);
-    if (cudaMemcpyAsync(hh.data(), ws.hist, sizeof(double) * hh.size(), cudaMemcpyDeviceToHost, a.stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(a.stream) != cudaSuccess)
-      return SW_ERR_CUDA;
+    const size_t nh = (size_t)2 * kHist * a.nsys;
+    cudaPointerAttributes at{};
+    const bool mapped = hist_host && cudaPointerGetAttributes(&at, hist_host) == cudaSuccess &&
+                        at.type == cudaMemoryTypeHost && at.devicePointer;
+    cudaGetLastError();
+    if (mapped) {
+      const int blocks = (int)std::min<size_t>((nh + 255) / 256, (size_t)sm_count() * 4);
+      copy_words<<<blocks, 256, 0, a.stream>>>(reinterpret_cast<const unsigned long long*>(ws.hist),
+                                               static_cast<unsigned long long*>(at.devicePointer), nh);
+      note_launches(1);
+      hh = hist_host;
+    } else {
+      hv.resize(nh);
+      if (cudaMemcpyAsync(hv.data(), ws.hist, sizeof(double) * nh, cudaMemcpyDeviceToHost, a.stream) != cudaSuccess)
+        return SW_ERR_CUDA;
+      hh = hv.data();
+    }
+    if (cudaStreamSynchronize(a.stream) != cudaSuccess) return SW_ERR_CUDA;
   }
   const double secs = duration<double>(steady_clock::now() - t0).count();
   int worst = SW_OK;
   for (int i = 0; i < a.nsys; ++i) {
-    int code = fill_info(e.state(i), a.infos ? hh.data() + (size_t)i * 2 * kHist : nullptr, a.precision, secs,
+    int code = fill_info(e.state(i), a.infos ? hh + (size_t)i * 2 * kHist : nullptr, a.precision, secs,
                          a.infos ? a.infos + i : nullptr);
     if (rc != SW_OK) code = rc;
     if (a.infos && rc != SW_OK) a.infos[i].status = rc;
@@ -884,7 +923,8 @@ int run_cgne(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a) 
   SysState* hs = nullptr;
   if (int e = pinned_states(2 * a.nsys, &hs)) return e;
   const Workspace ws = carve_workspace_for<VF>(mem.p, g.V, OpD::NC, a.nsys, MIXED);
-  return run_cgne_ws<OpD, OpF, MIXED>(g, opd, opf, a, ws, hs);
+  return run_cgne_ws<OpD, OpF, MIXED>(g, opd, opf, a, ws, hs, true,
+                                      a.infos ? pinned_hist((size_t)2 * kHist * a.nsys) : nullptr);
 }
 
 }  // namespace swc

@@ -44,6 +44,13 @@ bool overlap(const void* a, size_t na, const void* b, size_t nb);
 // Device properties cached per device.
 int sm_count();
 
+// Stream-ordered memory pool of the library's device workspace on the current
+// device (nullptr if it cannot be created).  Its release threshold keeps
+// freed blocks for the next call instead of handing them back to the driver
+// at every synchronisation, so a solve does not map gigabytes of workspace
+// anew; sw_trim_workspace() returns them.
+cudaMemPool_t lib_pool();
+
 // Kernel timing (instrumentation, off by default).  The driver brackets
 // sampled launches with events from a pool; once the solve has synchronised,
 // prof_flush() turns them into per-class launch counts, times and the
