@@ -130,7 +130,14 @@ int cgne_solve(const sw_lattice* lat, int op, const void* U, const void* W,
  * Each system follows exactly the iteration of cgne_solve with its own
  * scalars and reductions, so its result does not depend on the other systems
  * in the batch.  Returns SW_OK if every system converged, else the most
- * severe status (negative codes before SW_NOT_CONVERGED).  Blocks until done. */
+ * severe status (negative codes before SW_NOT_CONVERGED).  Blocks until done.
+ * Memory: the device workspace comes from the library's pool (see
+ * sw_workspace_reserved); each calling host thread keeps two pinned host
+ * buffers, reused by its later calls: the status words (2 nsys x 112 B) and,
+ * when infos is not NULL, the CG coefficients behind the Ritz estimates
+ * (nsys x 64 KB, in ordinary host memory beyond 256 MB).  Both move by
+ * kernel, so they never wait behind bulk copies the caller has queued on a
+ * copy engine. */
 int cgne_solve_batch(const sw_lattice* lat, int op, const void* U, const void* W, int nsys,
                      const void* chi, void* x, const double* masses, double r, double tol,
                      int max_iter, int precision, sw_solve_info* infos, void* stream);
