@@ -883,14 +883,15 @@ int run_cgne_ws(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& 
   const double* hh = nullptr;
   if (a.infos) {
     const size_t nh = (size_t)2 * kHist * a.nsys;
-    cudaPointerAttributes at{};
-    const bool mapped = hist_host && cudaPointerGetAttributes(&at, hist_host) == cudaSuccess &&
-                        at.type == cudaMemoryTypeHost && at.devicePointer;
-    cudaGetLastError();
-    if (mapped) {
+    void* hist_dev = nullptr;
+    if (hist_host && cudaHostGetDevicePointer(&hist_dev, hist_host, 0) != cudaSuccess) {
+      cudaGetLastError();  // not mapped: read by cudaMemcpyAsync below
+      hist_dev = nullptr;
+    }
+    if (hist_dev) {
       const int blocks = (int)std::min<size_t>((nh + 255) / 256, (size_t)sm_count() * 4);
       copy_words<<<blocks, 256, 0, a.stream>>>(reinterpret_cast<const unsigned long long*>(ws.hist),
-                                               static_cast<unsigned long long*>(at.devicePointer), nh);
+                                               static_cast<unsigned long long*>(hist_dev), nh);
       note_launches(1);
       hh = hist_host;
     } else {
