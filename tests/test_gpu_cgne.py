@@ -457,3 +457,63 @@ def test_workspace_pool_keeps_and_trims(sw):
         assert sw.sw_workspace_reserved() < held
         out.append(x)
     assert np.array_equal(out[0], out[1])
+
+
+def test_bench_batch_at_full_size(sw):
+    """The bench's launch configuration at its full size: one 16^3x32
+    configuration (mean plaquette 0.59), 12 staggered Wilson systems (3 colour
+    point sources x 4 masses) and 48 Wilson systems (12 spin-colour point
+    sources x 4 masses), mass-major, each operator in one cgne_solve_batch with
+    the library's defaults (FP32 inner iterations, CUDA graphs, reliable
+    updates beside the iterations, register blocking).  Every system meets the
+    FP64 true residual 1e-8, computed with the FP64 operators (which
+    test_gpu_dslash pins to the oracle site by site at full size), and at
+    sampled sites the oracle's one-site operator reproduces (D+m) x of the
+    first and last system of each batch."""
+    import torch
+    from oracle import site
+    dims, masses, tol = (16, 16, 16, 32), (0.02, 0.05, 0.1, 0.2), 1e-8
+    V = ls.volume(dims)
+    Uh = ls.su3_links(dims, 0, ls.PLAQ_EPS, processes=8)
+    U = dev(Uh)
+    W = torch.empty((V, 8, 3, 3), dtype=torch.complex128, device="cuda")
+    sw.sw_hypercube_build(dims, U, W)
+    rng = np.random.default_rng(11)
+    sites = [0, 1, V - 1, 16 * 16 * 16 - 1] + [int(v) for v in rng.integers(0, V, 6)]
+    for op, nsrc, shape in ((sw.SW_OP_STAGGERED_WILSON, 3, (V, 3)), (sw.SW_OP_WILSON, 12, (V, 4, 3))):
+        chis = np.stack([ls.point_source(dims, 3 if nsrc == 3 else 12, a).reshape(shape)
+                         for m in masses for a in range(nsrc)])
+        ms = [m for m in masses for _ in range(nsrc)]
+        chi = dev(chis)
+        x = torch.zeros_like(chi)
+        rc, infos = sw.cgne_solve_batch(dims, op, U, W if op == sw.SW_OP_STAGGERED_WILSON else None, chi, x, ms,
+                                        1.0, tol, 100000, sw.SW_PREC_F32_RELIABLE)
+        assert rc == sw.SW_OK and all(i.status == sw.SW_OK and i.true_rel_resid <= tol for i in infos)
+
+        def apply(v, m, dag):
+            out = torch.empty_like(v)
+            if op == sw.SW_OP_STAGGERED_WILSON:
+                sw.sw_dslash_apply(dims, U, W, v, out, m, 1.0, dag)
+            else:
+                sw.wilson_dslash_apply(dims, U, v, out, m, 1.0, dag)
+            return out
+
+        for k, m in enumerate(ms):
+            Dx = apply(x[k], m, False)
+            b = apply(chi[k], m, True)
+            r = b - apply(Dx, m, True)
+            rel = float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(b))
+            assert rel <= 1.01 * tol, (op, k, rel)
+            if k in (0, len(ms) - 1):
+                xh, got = x[k].cpu().numpy(), Dx.cpu().numpy()
+                # (D+m)x is ~chi, i.e. ~0 away from the source: a cancellation
+                # of O(|x|) terms, so the rounding scale is |x|, not the output
+                scale = np.abs(xh).max()
+                for n in sites:
+                    if op == sw.SW_OP_STAGGERED_WILSON:
+                        want = site.sw_dslash_site(Uh, xh, dims, n, m, 1.0, False, False)
+                    else:
+                        want = site.wilson_dslash_site(Uh, xh, dims, n, m, 1.0, False, False)
+                    assert np.abs(got[n] - want).max() <= 1e-12 * scale, (op, k, n)
+        del chi, x
+    torch.cuda.empty_cache()
