@@ -78,8 +78,7 @@ def check(sw, P, chi, prec, tol=1e-8):
     assert info.true_rel_resid <= tol
     rr = P.true_resid(chi, x)
     assert rr <= tol * 1.01
-    # the solver's own residual recomputation (FP64, or double-single in the
-    # mixed modes) agrees with the oracle's FP64 one
+    # the solver's own FP64 residual recomputation agrees with the oracle's
     assert abs(info.true_rel_resid - rr) <= 1e-13 + 1e-3 * rr
     ref, _ = P.oracle(chi, 1e-12)
     assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-6
