@@ -147,3 +147,47 @@ def test_stencil_neighbour_counts():
     G, _ = ops.gamma_matrices()
     for mu in range(4):
         assert np.linalg.matrix_rank(np.eye(4) - G[mu]) == g["wilson_spin_components_after_projection"]
+
+
+def antiperiodic_momenta(dims, reduced):
+    """Free-field momenta with the antiperiodic time boundary: p_mu = 2 pi n / L_mu
+    for mu < 3, p_3 = (2n + 1) pi / L_3; n over the full zone, or over [0, pi)
+    (the staggered reduced zone)."""
+    axes = []
+    for mu, L in enumerate(dims):
+        ns = range(L // 2) if reduced else range(L)
+        axes.append([((2 * n + 1) if mu == 3 else 2 * n) * np.pi / L for n in ns])
+    return list(itertools.product(*axes))
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 2, 2, 4), (4, 2, 2, 6)])
+def test_sw_free_spectrum_antiperiodic(dims):
+    """The antiperiodic time boundary shifts p_3 by pi / L_3 and changes nothing
+    else: the same closed form per reduced momentum (Gamma55's corner hops that
+    cross the boundary carry its sign too)."""
+    lat = Lattice(dims, antiperiodic_t=True)
+    U = lat.links(unit_links(lat.volume))
+    m, r = 0.1, 1.0
+    want = []
+    for p in antiperiodic_momenta(dims, reduced=True):
+        c = np.prod(np.abs(np.cos(p)))
+        s = np.sqrt(np.sum(np.sin(p) ** 2))
+        for sig in (1, -1):
+            for tau in (1, -1):
+                want += [m + r * (1 - sig * c) + 1j * tau * s] * 4 * 3
+    ev = np.linalg.eigvals(dense.sw_matrix(lat, U, m, r))
+    assert same_multiset(ev, np.array(want), 1e-9)
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 2, 4, 4)])
+def test_wilson_free_spectrum_antiperiodic(dims):
+    lat = Lattice(dims, antiperiodic_t=True)
+    U = lat.links(unit_links(lat.volume))
+    m, r = 0.1, 1.0
+    want = []
+    for p in antiperiodic_momenta(dims, reduced=False):
+        re = m + r * np.sum(1 - np.cos(p))
+        im = np.sqrt(np.sum(np.sin(np.array(p)) ** 2))
+        want += [re + 1j * im, re - 1j * im] * 2 * 3
+    ev = np.linalg.eigvals(dense.wilson_matrix(lat, U, m, r))
+    assert same_multiset(ev, np.array(want), 1e-9)
