@@ -64,6 +64,16 @@ def test_sw_free_spectrum(dims):
     assert same_multiset(ev, sw_free_eigs(dims, m, r), 1e-9)
 
 
+@pytest.mark.parametrize("r", [0.5, 1.75])
+def test_free_spectra_at_other_wilson_parameters(r):
+    """The closed forms hold for any r (the Wilson term of either operator
+    scales with it, the hopping term does not)."""
+    dims, m = (4, 2, 2, 2), 0.07
+    lat, U = free(dims)
+    assert same_multiset(np.linalg.eigvals(dense.sw_matrix(lat, U, m, r)), sw_free_eigs(dims, m, r), 1e-9)
+    assert same_multiset(np.linalg.eigvals(dense.wilson_matrix(lat, U, m, r)), wilson_free_eigs(dims, m, r), 1e-9)
+
+
 def test_sw_free_2x4_two_eigenvalues_and_two_flavours():
     lat, U = free((2, 2, 2, 2))
     m, r = 0.05, 1.0
