@@ -116,7 +116,9 @@ int wilson_dslash_apply(const sw_lattice* lat, const void* U, const void* in, vo
  * residual |b - A x|/|b| <= tol (tol > 0), or after max_iter iterations
  * (returns SW_NOT_CONVERGED with the best x).  precision: SW_PREC_*.
  * info (host pointer, may be NULL) receives the statistics.  Workspace is
- * allocated and freed inside the call (stream-ordered).  Blocks until done. */
+ * taken and returned inside the call (stream-ordered, from the library's
+ * memory pool, which keeps it for the next call: sw_workspace_reserved,
+ * sw_trim_workspace).  Blocks until done. */
 int cgne_solve(const sw_lattice* lat, int op, const void* U, const void* W,
                const void* chi, void* x, double mass, double r, double tol,
                int max_iter, int precision, sw_solve_info* info, void* stream);
@@ -320,7 +322,9 @@ int sw_server_poll(sw_server srv, int max, long long* requests, sw_solve_info* i
  * timeout_s seconds). */
 int sw_server_drain(sw_server srv, double timeout_s);
 
-/* Stop the scheduler, wait for the device and free everything. */
+/* Stop the scheduler, wait for the device and free everything (the engines'
+ * device memory returns to the library's pool; sw_trim_workspace hands it
+ * back to the driver). */
 int sw_server_destroy(sw_server srv);
 
 /* Human-readable name of a status code (static string). */
