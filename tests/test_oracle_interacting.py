@@ -186,3 +186,18 @@ def test_cg_a_norm_error_decreases():
         e = x - xs
         errs.append(e @ A @ e)
     assert all(errs[i + 1] <= errs[i] * (1 + 1e-12) for i in range(len(errs) - 1))
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 4, 2, 6)])
+def test_transport_of_a_pure_gauge_is_path_independent(dims):
+    """Pure-gauge links U_mu(x) = Omega(x) Omega(x+mu)^+: every path from x to
+    x+s gives Omega(x) Omega(x+s)^+, so the average over the 24 orderings is
+    exactly that for all 16 displacements (pins the order of the path
+    products and the backward links U_mu(y-mu)^+)."""
+    lat = Lattice(dims)
+    Om = lat.links(np.repeat(ls.haar_su3(dims, 21)[:, None], 4, axis=1))[0]
+    U = ops.gauge_transform_links(lat, lat.links(unit_links(lat.volume)), Om)
+    W16 = ops.hypercube_all(lat, U, stored_only=False)
+    for k, s in enumerate(hypercube_vectors(False)):
+        want = Om @ np.conj(np.swapaxes(lat.shift_links(Om, list(s)), -1, -2))
+        assert np.abs(W16[k] - want).max() < 1e-13, s
