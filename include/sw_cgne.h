@@ -109,6 +109,25 @@ int sw_dslash_apply(const sw_lattice* lat, const void* U, const void* W,
 int wilson_dslash_apply(const sw_lattice* lat, const void* U, const void* in, void* out,
                         double mass, double r, int dagger, void* stream);
 
+/* The operator exactly as the inner iterations of the mixed-precision solves
+ * apply it (Eq. 2's matvecs in SW_PREC_F32_RELIABLE or SW_PREC_F16_RELIABLE
+ * storage): U (and W for op = SW_OP_STAGGERED_WILSON) and the nsys input
+ * vectors are converted to that precision's packed storage, then
+ * out = (D+m) in (dagger = 0; by the first stencil kernel of a CG iteration,
+ * whose output is stored in the same precision as its input) or
+ * out = (D+m)^+ in (dagger != 0; by the second one, whose output is the FP32
+ * residual), with the register-blocking width and site order the solves use,
+ * and returned in FP64.  in, out: nsys vectors back to back, device,
+ * [nsys][V][3] or [nsys][V][4][3] complex128, not overlapping.  masses: HOST
+ * array [nsys].  For checking the inner-precision arithmetic against the FP64
+ * operators; not a fast path (the gauge field is converted on every call, and
+ * device workspace comes from the library's pool).  Blocks until done.
+ * SW_ERR_ARG for precision SW_PREC_F64 (use sw_dslash_apply and
+ * wilson_dslash_apply) and, in FP16 storage, for links that are not SU(3). */
+int dslash_apply_inner(const sw_lattice* lat, int op, const void* U, const void* W, int nsys,
+                       const void* in, void* out, const double* masses, double r, int dagger,
+                       int precision, void* stream);
+
 /* Solve (D+m)^+(D+m) x = (D+m)^+ chi by unpreconditioned CG (Eq. 2).
  * op: SW_OP_STAGGERED_WILSON (W required, vectors [V][3]) or SW_OP_WILSON
  * (W ignored, spinors [V][4][3]).  x: on entry the initial guess (zeros for
@@ -146,20 +165,23 @@ int cgne_solve_batch(const sw_lattice* lat, int op, const void* U, const void* W
 
 /* FP64 CGNE exactly as cgne_solve with SW_PREC_F64, but allocating nothing:
  * its device workspace is a static array of SW_NOALLOC_SCRATCH_BYTES inside the
- * library.  The paper has no counterpart; this is for callers that cannot
- * call cudaMalloc while they run -- code executing during CUDA graph capture,
- * runtimes whose device memory belongs to another allocator, allocation-free
- * latency loops.  They pass U, W, chi and x as for cgne_solve.
+ * library.  The paper has no counterpart.  It is for callers that cannot call
+ * cudaMalloc (or any allocator) while they run: plugins and runtimes whose
+ * device memory belongs to, and is budgeted by, another allocator, and
+ * latency-critical loops that must not enter the driver's allocator.  They
+ * pass U, W, chi and x as for cgne_solve.  The call creates no stream, event
+ * or graph either, and with profiling enabled it takes no timing samples.
  * Limit: the workspace is 4 FP64 vectors of the lattice plus about 0.1 MB
  * (192 B per site for staggered Wilson, 768 B per site for Wilson), so at
  * most ~174k sites (16^3x32) for staggered Wilson and ~43k (12^3x24) for
  * Wilson; larger lattices return SW_ERR_ARG before anything is launched.
  * The array is loaded with the library and every GPU that loads it keeps it
  * until exit.  The first call on a device looks up the array's address with
- * cudaGetSymbolAddress (that device must be current); make that first call
- * before any stream capture.  All calls share the array and it keeps the last
- * call's contents (the solve initialises everything it reads); calls whose
- * GPU work overlaps race on it and must be serialised by the caller.
+ * cudaGetSymbolAddress (that device must be current) and keeps it for the
+ * process.  All calls share the array and it keeps the last call's contents
+ * (the solve initialises everything it reads).  No two calls may be in
+ * progress at once -- on any stream, from any host thread -- since each
+ * overwrites the other's vectors and status words: the caller serialises them.
  * Blocks until done, like cgne_solve. */
 #define SW_NOALLOC_SCRATCH_BYTES (32u << 20)
 int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, const void* W,

@@ -14,7 +14,7 @@ from ._binding import (  # noqa: F401
     SWError, SolveInfo, Server, lib, lib_path,
     SW_OK, SW_NOT_CONVERGED, SW_OP_STAGGERED_WILSON, SW_OP_WILSON,
     SW_PREC_F64, SW_PREC_F32_RELIABLE, SW_PREC_F16_RELIABLE,
-    sw_hypercube_build, sw_dslash_apply, wilson_dslash_apply, cgne_solve, cgne_solve_batch,
+    sw_hypercube_build, sw_dslash_apply, wilson_dslash_apply, dslash_apply_inner, cgne_solve, cgne_solve_batch,
     sw_status_string, sw_last_cuda_error, sw_profile_enable, sw_profile_reset, sw_profile_read,
     sw_kernel_launches, sw_workspace_reserved, sw_trim_workspace, cgne_solve_noalloc, sw_set_param, sw_get_param,
     sw_autotune, sw_autotune_layout, SW_PARAM_CHUNK, SW_PARAM_RELIABLE_DELTA, SW_PARAM_NS_SW, SW_PARAM_NS_WILSON, SW_PARAM_GRAPHS,

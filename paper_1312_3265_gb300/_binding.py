@@ -89,6 +89,8 @@ def lib():
         L.cgne_solve.argtypes = [lat, i, vp, vp, vp, vp, d, d, d, i, i, ctypes.POINTER(_Info), vp]
         L.cgne_solve_batch.argtypes = [lat, i, vp, vp, i, vp, vp, ctypes.POINTER(ctypes.c_double), d, d, i, i,
                                        ctypes.POINTER(_Info), vp]
+        L.dslash_apply_inner.argtypes = [lat, i, vp, vp, i, vp, vp, ctypes.POINTER(ctypes.c_double), d, i, i, vp]
+        L.dslash_apply_inner.restype = i
         L.cgne_solve_noalloc.argtypes = [lat, i, vp, vp, vp, vp, d, d, d, i, ctypes.POINTER(_Info), vp]
         L.cgne_solve_noalloc.restype = i
         srv = ctypes.c_void_p
@@ -186,6 +188,17 @@ def wilson_dslash_apply(dims, U, inp, out, mass, r=1.0, dagger=False, t_antiperi
     _check(lib().wilson_dslash_apply(_lat(dims, t_antiperiodic), _ptr(U), _ptr(inp), _ptr(out),
                                      float(mass), float(r), int(bool(dagger)), _stream(stream)),
            "wilson_dslash_apply")
+
+
+def dslash_apply_inner(dims, op, U, W, inp, out, masses, r=1.0, dagger=False, precision=SW_PREC_F32_RELIABLE,
+                       t_antiperiodic=False, stream=None):
+    """(D+m) or (D+m)^+ on len(masses) systems back to back, in the inner precision
+    of the mixed-mode iterations (by the CG iteration kernels), returned in FP64."""
+    n = len(masses)
+    m = (ctypes.c_double * n)(*[float(v) for v in masses])
+    _check(lib().dslash_apply_inner(_lat(dims, t_antiperiodic), int(op), _ptr(U), _ptr(W), n, _ptr(inp), _ptr(out), m,
+                                    float(r), int(bool(dagger)), int(precision), _stream(stream)),
+           "dslash_apply_inner")
 
 
 def cgne_solve(dims, op, U, W, chi, x, mass, r=1.0, tol=1e-8, max_iter=100000, precision=SW_PREC_F64,

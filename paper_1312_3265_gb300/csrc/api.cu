@@ -451,4 +451,32 @@ int cgne_solve_batch(const sw_lattice* lat, int op, const void* U, const void* W
   return rc;
 }
 
+
+int dslash_apply_inner(const sw_lattice* lat, int op, const void* U, const void* W, int nsys, const void* in,
+                       void* out, const double* masses, double r, int dagger, int precision, void* stream) {
+  Geom g;
+  SW_TRY(make_geom(lat, &g));
+  if (op != SW_OP_STAGGERED_WILSON && op != SW_OP_WILSON) return SW_ERR_ARG;
+  if (precision != SW_PREC_F32_RELIABLE && precision != SW_PREC_F16_RELIABLE) return SW_ERR_ARG;
+  if (nsys < 1 || nsys > 65535) return SW_ERR_ARG;
+  if (!masses) return SW_ERR_NULL;
+  for (int i = 0; i < nsys; ++i)
+    if (!(masses[i] == masses[i])) return SW_ERR_ARG;
+  if (!(r == r)) return SW_ERR_ARG;
+  const size_t V = g.V;
+  const size_t vb = V * (op == SW_OP_WILSON ? 192 : 48) * (size_t)nsys;
+  SW_TRY(check_buf(U, V * 576));
+  if (op == SW_OP_STAGGERED_WILSON) SW_TRY(check_buf(W, V * 1152));
+  SW_TRY(check_buf(in, vb));
+  SW_TRY(check_buf(out, vb));
+  if (overlap(in, vb, out, vb)) return SW_ERR_ARG;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const auto* u = static_cast<const double2*>(U);
+  const auto* v = static_cast<const double2*>(in);
+  auto* o = static_cast<double2*>(out);
+  return (op == SW_OP_WILSON)
+             ? wilson_inner_apply(g, u, v, o, nsys, masses, r, dagger, precision, st)
+             : sw_inner_apply(g, u, static_cast<const double2*>(W), v, o, nsys, masses, r, dagger, precision, st);
+}
+
 }  // extern "C"

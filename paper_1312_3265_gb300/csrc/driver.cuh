@@ -250,13 +250,16 @@ class Engine {
   // chi, x: cap slots in the canonical layout (x: initial guess in, solution
   // out).  hs_read / hs_stage: host arrays [cap] (pinned for overlap).
   // ev: event marking the status copy (nullptr: complete() syncs the stream).
-  // use_graphs: replay chunks as a captured CUDA graph (creating the graph
-  // allocates driver resources, so allocation-free callers pass false).
+  // use_graphs: replay chunks as a captured CUDA graph, run reliable updates on
+  // a side stream and time launches with events when profiling is enabled;
+  // all of these create driver resources, so allocation-free callers pass
+  // false (they get one stream, direct launches and no timing samples).
   Engine(const Geom& g, const OpD& opd, const OpF& opf, double r, int cap, double2* chi, double2* x,
          const Workspace& ws, SysState* hs_read, SysState* hs_stage, cudaStream_t st, cudaEvent_t ev,
          bool use_graphs = true)
       : g_(g), opd_(opd), opf_(opf), r_(r), cap_(cap), chi_(chi), x_(x), ws_(ws), hr_(hs_read), hst_(hs_stage),
-        st_(st), ev_(ev), n_((size_t)g.V * NC), use_graphs_(use_graphs && param_graphs()) {
+        st_(st), ev_(ev), n_((size_t)g.V * NC), use_graphs_(use_graphs && param_graphs()),
+        driver_resources_(use_graphs) {
     ntiles_ = (g.V + kTile - 1) / kTile;
     pstride_ = kWarps * ntiles_;
     gb_ = make_blocked(g, g.shape);
@@ -290,7 +293,7 @@ class Engine {
       hr_[i] = z;
     }
     cudaMemsetAsync(ws.tickets, 0, sizeof(unsigned) * 2 * cap, st);
-    if (use_graphs_) {  // callers that allow driver resources get the overlapped reliable update
+    if (driver_resources_) {  // callers that allow driver resources get the overlapped reliable update
       if (cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming) != cudaSuccess ||
           cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming) != cudaSuccess) {
@@ -314,7 +317,7 @@ class Engine {
     int apps;
   };
   FpSample* fp_sample(int apps, cudaStream_t sx) {
-    if (!prof_enabled() || fsamples_.size() >= (size_t)kProfSlots / 2) return nullptr;
+    if (!prof() || fsamples_.size() >= (size_t)kProfSlots / 2) return nullptr;
     FpSample f{prof_event(), prof_event(), ws_.pcount + 2 * kProfSlots - 1 - fsamples_.size(), apps};
     cudaEventRecord(f.e0, sx);
     fsamples_.push_back(f);
@@ -438,7 +441,7 @@ class Engine {
         note_launches(1);
       } else {
         FpSample* fs = fp_sample(1, st_);
-        if (prof_enabled()) prof_count(cls_rhs(), 1);
+        if (prof()) prof_count(cls_rhs(), 1);
         apply_kernel<double, OpD><<<dim3(grid_of((const void*)apply_kernel<double, OpD>, kTile, na), cap_), kTile,
                                     0, st_>>>(g_, opd_, V64{chi_}, V64{ws_.b64}, 0.0, n_, r_, 1, S, ST_ADMIT,
                                               fs ? fs->cnt : nullptr);
@@ -476,7 +479,7 @@ class Engine {
       // host's launch latency
       // (never in a round whose reliable update runs alongside: the events
       // would time the two streams' kernels sharing the GPU)
-      const bool prof = prof_enabled() && chunk_ > 1 && samples_.size() < (size_t)kProfSlots / 2 &&
+      const bool prof = this->prof() && chunk_ > 1 && samples_.size() < (size_t)kProfSlots / 2 &&
                         (chunks_ % 4 == 0) && !overlap;
       ++chunks_;
       if (!prof && use_graphs_ && chunks_ > 1) {
@@ -581,7 +584,7 @@ class Engine {
     cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, sx>>>(g_.V, fr_, fp_, fx_, n_, vunits_, S, ST_RU_PENDING, 1);
     if constexpr (MIXED) accum_x<NC><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, x_, ws_.x32, n_, n_, S);
     FpSample* fs = fp_sample(2, sx);
-    if (prof_enabled()) prof_count(cls_ru(), 1);
+    if (prof()) prof_count(cls_ru(), 1);
     // r = (D+m)^+ (chi - (D+m) x) = b - A x, all in FP64
     apply_kernel<double, OpD><<<dim3(grid_of((const void*)apply_kernel<double, OpD>, kTile, nsys), cap_), kTile, 0,
                                 sx>>>(g_, opd_, V64{x_}, V64{ws_.t64}, 0.0, n_, r_, 0, S, ST_RU_PENDING,
@@ -620,7 +623,7 @@ class Engine {
     if (ge) {
       cudaGraphLaunch(ge, st_);
       note_launches(4 * chunk_);
-      if (prof_enabled()) {
+      if (prof()) {
         prof_count(cls_k1(), chunk_);
         prof_count(cls_k2(), chunk_);
         prof_count(cls_k3(), chunk_);
@@ -730,7 +733,7 @@ class Engine {
     if (sample) cudaEventRecord(samples_.back().e3, st_);
     if (count) {
       note_launches(4);
-      if (prof_enabled()) {
+      if (prof()) {
         prof_count(cls_k1(), 1);
         prof_count(cls_k2(), 1);
         prof_count(cls_k3(), 1);
@@ -780,6 +783,8 @@ class Engine {
   std::vector<FpSample> fsamples_;
   long long rounds_ = 0, chunks_ = 0;
   bool use_graphs_ = true, graph_failed_ = false;
+  bool driver_resources_ = true;  // false: allocation-free caller (no side stream, graphs or timing events)
+  bool prof() const { return driver_resources_ && prof_enabled(); }
   int cls_ = 0;  // groups the iteration grids are sized for
   std::vector<std::pair<int, cudaGraphExec_t>> gexecs_;
   std::vector<int> staged_;
@@ -883,6 +888,81 @@ int run_cgne(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a) 
   const Workspace ws = carve_workspace_for<VF>(mem.p, g.V, OpD::NC, a.nsys, MIXED);
   return run_cgne_ws<OpD, OpF, MIXED>(g, opd, opf, a, ws, hs, true,
                                       a.infos ? pinned_hist((size_t)2 * kHist * a.nsys) : nullptr);
+}
+
+
+// The inner-precision operator of the mixed modes applied to nsys systems by
+// the CG iteration kernels themselves: (D+m) in by cg_k1 (t = (D+m) p, with p
+// the inner-precision copy of `in`), (D+m)^+ in by cg_k2 (r -= alpha (D+m)^+ t
+// with r = 0, alpha = -1, t the copy of `in`), at the register-blocking width
+// and site order the solves use.  in, out: canonical FP64 [nsys][V][NC];
+// masses: host [nsys].  Blocks until done.
+template <class OpF>
+int run_inner_apply(const Geom& g, const OpF& opf, const double2* in, double2* out, int nsys, const double* masses,
+                    double r, int dagger, cudaStream_t st) {
+  constexpr int NC = OpF::NC;
+  using VF = typename OpF::Vec;
+  using VR = VecP32<NC>;
+  using PU = typename VF::unit;
+  const GeomBlk gb = make_blocked(g, g.shape);
+  const size_t vunits = VF::sys_units(g.V), n = (size_t)g.V * NC;
+  const int ntiles = (g.V + kTile - 1) / kTile, pstride = kWarps * ntiles;
+  const size_t bytes = 2 * align_up(sizeof(PU) * vunits * nsys) + align_up(sizeof(float2) * n * nsys) +
+                       align_up(sizeof(SysState) * nsys) + align_up(sizeof(double) * pstride * nsys) +
+                       align_up(sizeof(unsigned) * nsys);
+  DevMem mem;
+  if (!mem.alloc(bytes, st)) return SW_ERR_OOM;
+  char* c = mem.as<char>();
+  auto take = [&](size_t b) {
+    void* p = c;
+    c += align_up(b);
+    return p;
+  };
+  const VF fp{static_cast<PU*>(take(sizeof(PU) * vunits * nsys)), g.V};
+  const VF ft{static_cast<PU*>(take(sizeof(PU) * vunits * nsys)), g.V};
+  const VR fr{static_cast<float2*>(take(sizeof(float2) * n * nsys)), g.V};
+  SysState* S = static_cast<SysState*>(take(sizeof(SysState) * nsys));
+  double* partials = static_cast<double*>(take(sizeof(double) * pstride * nsys));
+  unsigned* tickets = static_cast<unsigned*>(take(sizeof(unsigned) * nsys));
+  std::vector<SysState> hs(nsys);
+  for (int i = 0; i < nsys; ++i) {
+    hs[i] = SysState{};
+    hs[i].mass = masses[i];
+    hs[i].rr = 1.0;
+    hs[i].alpha = -1.0;
+    hs[i].max_iter = 1 << 30;
+    hs[i].status = ST_ADMIT;
+  }
+  cudaMemcpyAsync(S, hs.data(), sizeof(SysState) * nsys, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(tickets, 0, sizeof(unsigned) * nsys, st);
+  cudaMemsetAsync(fr.p, 0, sizeof(float2) * n * nsys, st);
+  const int gv = grid_for((const void*)demote_chi<NC, VF>, 256, g.V, nsys, ntiles);
+  demote_chi<NC, VF><<<dim3(gv, nsys), 256, 0, st>>>(gb, in, dagger ? ft : fp, n, vunits, S);
+  set_status<<<(nsys + 127) / 128, 128, 0, st>>>(nsys, S, ST_RUNNING);
+  const RedBuf rb{partials, tickets, pstride, nullptr};
+  const BatchParams bp{r, n, n, vunits};
+  const int ns = param_ns(NC);
+  auto launch = [&](auto nsc) {
+    constexpr int NS = decltype(nsc)::value;
+    const int ngrp = (nsys + NS - 1) / NS;
+    if (!dagger) {
+      const int gx = grid_for((const void*)cg_k1<float, OpF, NS, GeomBlk>, kTile, g.V, ngrp, ntiles);
+      cg_k1<float, OpF, NS, GeomBlk><<<dim3(gx, ngrp), kTile, 0, st>>>(gb, opf, fp, ft, bp, nsys, S, rb, nullptr, 0);
+    } else {
+      const int gx = grid_for((const void*)cg_k2<float, OpF, NS, VR, GeomBlk>, kTile, g.V, ngrp, ntiles);
+      cg_k2<float, OpF, NS, VR, GeomBlk><<<dim3(gx, ngrp), kTile, 0, st>>>(gb, opf, ft, fr, bp, nsys, S, rb,
+                                                                          nullptr, 0);
+    }
+  };
+  if (ns == 2) launch(std::integral_constant<int, 2>{});
+  else if (ns == 4) launch(std::integral_constant<int, 4>{});
+  else launch(std::integral_constant<int, 1>{});
+  if (!dagger) promote_vec<NC, VF><<<dim3(gv, nsys), 256, 0, st>>>(gb, ft, vunits, out, n);
+  else promote_vec<NC, VR><<<dim3(gv, nsys), 256, 0, st>>>(gb, fr, n, out, n);
+  note_launches(5);
+  if (const cudaError_t e = cudaStreamSynchronize(st); e != cudaSuccess) return cuda_fail(e);
+  if (const cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(e);
+  return SW_OK;
 }
 
 }  // namespace swc

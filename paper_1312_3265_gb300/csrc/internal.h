@@ -30,6 +30,11 @@ int sw_apply_f64(const Geom& g, const double2* U, const double2* W, const double
 int wilson_apply_f64(const Geom& g, const double2* U, const double2* in, double2* out,
                      double mass, double r, int dagger, cudaStream_t st);
 int sw_cgne(const Geom& g, const SolveArgs& a);
+// The inner-precision operators of the mixed modes, through the CG iteration kernels.
+int sw_inner_apply(const Geom& g, const double2* U, const double2* W, const double2* in, double2* out, int nsys,
+                   const double* masses, double r, int dagger, int precision, cudaStream_t st);
+int wilson_inner_apply(const Geom& g, const double2* U, const double2* in, double2* out, int nsys,
+                       const double* masses, double r, int dagger, int precision, cudaStream_t st);
 int wilson_cgne(const Geom& g, const SolveArgs& a);
 
 // Tunables set through the C ABI (api.cu), also used by the autotuner.

@@ -259,6 +259,29 @@ static __global__ void commit_ready(int nsys, SysState* S) {
   if (i < nsys && S[i].status == ST_READY) S[i].status = ST_RUNNING;
 }
 
+// Every system's status word <- st (set-up of the inner-precision apply).
+static __global__ void set_status(int nsys, SysState* S, int st) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nsys) S[i].status = st;
+}
+
+// Inner-precision field (packed, blocked order; the accessor's own reading,
+// FP16 scales applied) -> canonical FP64, every system of the batch.
+template <int NC, typename Vec>
+__global__ void promote_vec(GeomBlk gb, Vec in, size_t sin, double2* out, size_t s64) {
+  const int sys = blockIdx.y;
+  in = sys_view(in, sys, sin);
+  out += sys * s64;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gb.V; n += gridDim.x * blockDim.x) {
+    const int nb = lex_to_blk(gb, n);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const cx<float> v = in.ld(nb, c);
+      out[(size_t)n * NC + c] = make_double2((double)v.re, (double)v.im);
+    }
+  }
+}
+
 // n 8-byte words from src to dst.  Moves the solver's status words between
 // the device and mapped pinned host memory: the kernel's loads and stores
 // cross the host link directly, so these small transfers never queue behind

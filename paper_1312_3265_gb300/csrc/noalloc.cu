@@ -1,21 +1,24 @@
 // cgne_solve_noalloc: the FP64 CGNE solve with its device workspace in a
 // fixed, file-scope device array instead of memory allocated per call.
 //
-// For callers that cannot allocate device memory while they run: code that
-// executes while a CUDA graph is being captured (an allocation call there
-// breaks the capture or is not recorded), host threads of runtimes whose
-// device memory is owned and budgeted by another allocator, and
-// latency-critical loops that must not hit the driver's allocator.  They pass
-// their inputs and outputs; the library supplies the scratch.
+// For callers that cannot call cudaMalloc (or any other allocator) while they
+// run: plugins and host runtimes whose device memory is owned and budgeted by
+// another allocator, so that an allocation behind its back would break its
+// accounting or fail, and latency-critical loops that must never enter the
+// driver's allocator.  They pass their inputs and outputs; the library
+// supplies the scratch.  The call also creates no stream, event or graph, and
+// it blocks until the solve is done (it reads the solver's status words on the
+// host between rounds of iterations).
 //
 // The scratch array (kNoallocScratchBytes) is part of the module, so every
 // GPU that loads the library holds it until the process exits.  Its device
 // address is looked up once per device with cudaGetSymbolAddress, on the
 // first call made with that device current.  All calls share the one array
 // and it keeps the previous call's contents: everything the solve reads is
-// initialised by the solve itself, and calls whose GPU work overlaps (for
-// example on two streams) race on the array and must be serialised by the
-// caller.
+// initialised by the solve itself.  No two calls may be in progress at the
+// same time -- on one stream or several, from one host thread or several --
+// because each would overwrite the other's vectors and status words; the
+// caller serialises them.
 #include <mutex>
 
 #include "driver.cuh"

@@ -50,4 +50,32 @@ int sw_cgne(const Geom& g, const SolveArgs& a) {
   return SW_ERR_ARG;
 }
 
+
+int sw_inner_apply(const Geom& g, const double2* U, const double2* W, const double2* in, double2* out, int nsys,
+                   const double* masses, double r, int dagger, int precision, cudaStream_t st) {
+  const int gp = sm_count() * 8;
+  if (precision == SW_PREC_F32_RELIABLE) {
+    DevMem mu, mw;
+    if (!mu.alloc(sizeof(float2) * 36 * (size_t)g.V, st) || !mw.alloc(sizeof(float2) * 72 * (size_t)g.V, st))
+      return SW_ERR_OOM;
+    pack_mats_p32<<<gp, 256, 0, st>>>(make_blocked(g, g.shape), 4, U, mu.as<float2>());
+    pack_mats_p32<<<gp, 256, 0, st>>>(make_blocked(g, g.shape), 8, W, mw.as<float2>());
+    note_launches(2);
+    return run_inner_apply(g, SW32{GaugeP32{mu.as<float2>()}, TransP32{mw.as<float2>()}}, in, out, nsys, masses, r,
+                           dagger, st);
+  }
+  if (precision == SW_PREC_F16_RELIABLE) {
+    if (int e = check_su3(g, U, st)) return e;
+    DevMem mu, mw;
+    if (!mu.alloc(sizeof(__half2) * 24 * (size_t)g.V, st) || !mw.alloc(sizeof(__half2) * 72 * (size_t)g.V, st))
+      return SW_ERR_OOM;
+    pack_links_h12<<<gp, 256, 0, st>>>(make_blocked(g, g.shape), U, mu.as<__half2>());
+    pack_mats_h<<<gp, 256, 0, st>>>(make_blocked(g, g.shape), 8, W, mw.as<__half2>());
+    note_launches(2);
+    return run_inner_apply(g, SW16{GaugeP16{mu.as<__half2>()}, TransP16{mw.as<__half2>()}}, in, out, nsys, masses,
+                           r, dagger, st);
+  }
+  return SW_ERR_ARG;
+}
+
 }  // namespace swc

@@ -55,4 +55,32 @@ int wilson_cgne(const Geom& g, const SolveArgs& a) {
   return (a.r == 1.0) ? cgne_impl<true>(g, a) : cgne_impl<false>(g, a);
 }
 
+
+template <bool R1>
+static int inner_impl(const Geom& g, const double2* U, const double2* in, double2* out, int nsys,
+                      const double* masses, double r, int dagger, int precision, cudaStream_t st) {
+  if (precision == SW_PREC_F32_RELIABLE) {
+    DevMem mu;
+    if (!mu.alloc(sizeof(float2) * 36 * (size_t)g.V, st)) return SW_ERR_OOM;
+    pack_mats_p32<<<sm_count() * 8, 256, 0, st>>>(make_blocked(g, g.shape), 4, U, mu.as<float2>());
+    note_launches(1);
+    return run_inner_apply(g, W32<R1>{GaugeP32{mu.as<float2>()}}, in, out, nsys, masses, r, dagger, st);
+  }
+  if (precision == SW_PREC_F16_RELIABLE) {
+    if (int e = check_su3(g, U, st)) return e;
+    DevMem mu;
+    if (!mu.alloc(sizeof(__half2) * 24 * (size_t)g.V, st)) return SW_ERR_OOM;
+    pack_links_h12<<<sm_count() * 8, 256, 0, st>>>(make_blocked(g, g.shape), U, mu.as<__half2>());
+    note_launches(1);
+    return run_inner_apply(g, W16<R1>{GaugeP16{mu.as<__half2>()}}, in, out, nsys, masses, r, dagger, st);
+  }
+  return SW_ERR_ARG;
+}
+
+int wilson_inner_apply(const Geom& g, const double2* U, const double2* in, double2* out, int nsys,
+                       const double* masses, double r, int dagger, int precision, cudaStream_t st) {
+  return (r == 1.0) ? inner_impl<true>(g, U, in, out, nsys, masses, r, dagger, precision, st)
+                    : inner_impl<false>(g, U, in, out, nsys, masses, r, dagger, precision, st);
+}
+
 }  // namespace swc

@@ -1,9 +1,12 @@
-"""cgne_solve_noalloc: the FP64 solve for callers that cannot allocate device
-memory (graph capture, foreign allocators, allocation-free loops), with its
-workspace in the library's static device array.  Checked through the C ABI
-against cgne_solve on two calls in a row, within the solution tolerance of the
-other GPU tests (1e-6 relative), plus the size limit.  Kept last in collection
-order so that a -x run has already run every other test."""
+"""cgne_solve_noalloc: the FP64 solve for callers that cannot call an allocator
+while they run (runtimes whose device memory belongs to another allocator,
+allocation-free latency loops), with its workspace in the library's static
+device array.  Checked through the C ABI against cgne_solve on calls in a row
+-- a staggered Wilson solve, a larger Wilson solve, then a smaller staggered
+Wilson solve from a non-zero initial guess, so that the shared array holds a
+larger call's leftovers -- within the solution tolerance of the other GPU
+tests (1e-6 relative), plus the size limit.  Kept last in collection order so
+that a -x run has already run every other test."""
 import ctypes
 
 import numpy as np
@@ -30,7 +33,8 @@ def dev(a):
 
 
 def c_solve(sw, fn, dims, op, U, W, chi, x, mass, tol):
-    """Call an entry point through ctypes: fn is 'cgne_solve' or 'cgne_solve_noalloc'."""
+    """Call an entry point through ctypes: fn is 'cgne_solve' or 'cgne_solve_noalloc'
+    (x holds the initial guess on entry and the solution on exit)."""
     import torch
     from paper_1312_3265_gb300._binding import Lattice, _Info
     L = sw.lib()
@@ -61,15 +65,19 @@ def problem(sw, dims, op, seed):
     return U, W, chi
 
 
-def test_noalloc_matches_cgne_solve_twice(sw):
+def test_noalloc_matches_cgne_solve_in_a_row(sw):
     import torch
-    cases = [((4, 4, 4, 4), sw.SW_OP_STAGGERED_WILSON, 0.05), ((6, 4, 4, 6), sw.SW_OP_WILSON, 0.1)]
-    for dims, op, mass in cases:  # two calls in a row, different operators and sizes
+    # calls in a row: different operators and sizes, the last one smaller than
+    # the one before it and started from a non-zero guess
+    cases = [((4, 4, 4, 4), sw.SW_OP_STAGGERED_WILSON, 0.05, False), ((6, 4, 4, 6), sw.SW_OP_WILSON, 0.1, False),
+             ((4, 4, 2, 4), sw.SW_OP_STAGGERED_WILSON, 0.07, True)]
+    for dims, op, mass, guess in cases:
         U, W, chi = problem(sw, dims, op, 3)
-        x_ref = torch.zeros_like(chi)
+        x0 = dev(ls.gaussian_source(dims, chi.shape[-1], 17)) if guess else None
+        x_ref = x0.clone() if guess else torch.zeros_like(chi)
         rc, ref_info = c_solve(sw, "cgne_solve", dims, op, U, W, chi, x_ref, mass, 1e-10)
         assert rc == sw.SW_OK
-        x = torch.zeros_like(chi)
+        x = x0.clone() if guess else torch.zeros_like(chi)
         rc, info = c_solve(sw, "cgne_solve_noalloc", dims, op, U, W, chi, x, mass, 1e-10)
         assert rc == sw.SW_OK and info.status == sw.SW_OK
         assert info.true_rel_resid <= 1e-10
