@@ -64,8 +64,9 @@ NCU_TRAFFIC = {
     "wilson.k2.f32": {"bytes": 475.4e6, "algorithmic": 490.7e6, "systems": 12},
 }
 
-# FP64 peak of a GB300 (nominal 1.25 TFLOP/s; not in the measured-peaks file):
-# denominator of the FP64-ALU-bound reliable-update matvecs.
+# FP64 peak of a GB300 when no measurement is given (nominal 1.25 TFLOP/s; the
+# measured-peaks file has no FP64 figure): the bench measures it with the
+# library's FMA-throughput kernel (sw_measure_fp64_peak) and passes that in.
 FP64_PEAK_TFLOPS = 1.25
 
 
@@ -83,7 +84,7 @@ def parse():
     ap.add_argument("--chunk", type=int, default=None, help="CG iterations between status reads")
     ap.add_argument("--ns-sw", type=int, default=None, help="systems per thread, staggered Wilson FP32 stencils")
     ap.add_argument("--ns-wilson", type=int, default=None, help="systems per thread, Wilson FP32 stencils")
-    ap.add_argument("--serving-requests", type=int, default=400,
+    ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests in the Poisson serving phase (0: skip)")
     ap.add_argument("--serving-lattices", default="8x8x8x8,12x12x12x24,16x16x16x32,24x24x24x48")
     ap.add_argument("--no-f64", action="store_true", help="skip the plain-FP64 comparison step")
@@ -105,6 +106,10 @@ def parse():
     ap.add_argument("--sources", default="point",
                     help="'point': 3 colour (SW) / 12 spin-colour (W) point sources per mass; "
                          "'z2:N': N real Z2-noise sources per mass for both operators")
+    ap.add_argument("--no-large-volume", action="store_true",
+                    help="skip the large-volume block (48^3x96 staggered Wilson, 32^3x64 Wilson; FP32 and FP16)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched block (24^3x48, 12 Z2 sources x 6 masses per operator)")
     return ap.parse_args()
 
 
@@ -213,19 +218,26 @@ def host_inputs(seeds, masses=MASSES, w_sources=12, dims=DIMS, sources="point"):
     return U, chi_sw, m_sw, chi_w, m_w
 
 
+def workload_config(workload, dims, masses):
+    """The `config` object of the JSON line: the workload only, the same keys
+    and values in both arms."""
+    return {"workload": workload, "lattice": "x".join(map(str, dims)), "masses": list(masses), "tol": TOL,
+            "l2": "inputs larger than L2: a step touches ~10 GB and each step uses a new configuration"}
+
+
 # ------------------------------------------------------------------ rooflines
 # FP32 peak of a GB300 from its unit counts and clock: 152 SMs x 128 FP32
 # lanes x 2 flop (FMA) x 2.07 GHz (the maximum SM clock).
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def classify_kernels(prof, hbm_peak, peak_kind):
+def classify_kernels(prof, hbm_peak, peak_kind, fp64_peak=None):
     """Per kernel class: time per launch, and the fraction of the roofline
     that bounds it.  FP32/FP16 stencils: algorithmic bytes against the
     measured HBM bandwidth and the paper's flops (Eq. 4) against the FP32 peak;
     the bound is the resource whose roofline time is longer (the launch's
     arithmetic intensity against the ridge).  FP64 matvecs: flops against the
-    nominal FP64 peak.  A class's time in the timed region is its mean timed
+    measured FP64 FMA throughput (fp64_peak, TFLOP/s), else the nominal one.  A class's time in the timed region is its mean timed
     launch times the launches it issued (only some launches are timed).
     Returns (kernels, roofline of the kernel class with the most time,
     roofline of the HBM-bound class with the most time)."""
@@ -246,10 +258,11 @@ def classify_kernels(prof, hbm_peak, peak_kind):
         if fpl > 0:
             tf = fpl / (ms / 1e3) / 1e12
             fp64 = bpl == 0
-            pk = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+            pk = (fp64_peak or FP64_PEAK_TFLOPS) if fp64 else FP32_PEAK_TFLOPS
             e.update({"TFLOP/s": round(tf, 3), ("frac_fp64" if fp64 else "frac_fp32"): round(tf / pk, 4)})
             res.append(("alu", fpl / (pk * 1e12), tf, pk, "TFLOP/s", fpl,
-                        "nominal FP64" if fp64 else "FP32 from unit counts and clock"))
+                        ("measured FP64 FMA throughput" if fp64_peak else "nominal FP64") if fp64
+                        else "FP32 from unit counts and clock"))
         if not res:
             continue
         bound = max(res, key=lambda r: r[1])
@@ -412,6 +425,9 @@ def run_ours(args):
 
     for s in range(Wm):
         step(seed_for(s, rank, world), U[seed_for(s, rank, world)], chi_sw, chi_w, x_sw, x_w)
+    # FP64 FMA throughput of this GPU (the FP64 matvecs' roofline denominator),
+    # measured before the timed region
+    fp64_peak = sw.sw_measure_fp64_peak(stream)
 
     # ---- timed region: device-resident inputs
     clocks = ClockSampler(dev.index)
@@ -522,6 +538,8 @@ def run_ours(args):
     serving = None
     if args.serving_requests > 0 and world == 1:
         serving = run_serving(sw, torch, dev, args)
+    batched = None if (args.no_batched or world > 1) else run_batched(sw, torch, dev)
+    large = None if (args.no_large_volume or world > 1) else run_large_volume(sw, torch, dev)
 
     # ---- per-operator statistics
     it_sw = [i.iters for st in infos for i in st[0]]
@@ -543,7 +561,7 @@ def run_ours(args):
     lats = sorted([v for v in lat_sw for _ in m_sw] + [v for v in lat_w for _ in m_w]) or [0.0]
 
     peak, peak_kind = measured_peaks()
-    kernels, roof, roof_hbm = classify_kernels(prof, peak, peak_kind)
+    kernels, roof, roof_hbm = classify_kernels(prof, peak, peak_kind, fp64_peak)
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": K,
@@ -551,25 +569,27 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": {sw.SW_PREC_F32_RELIABLE: "f32+f64", sw.SW_PREC_F16_RELIABLE: "f16-storage/f32+f64"}.get(prec, "f64"),
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if (dims == DIMS and args.sources == "point") else
-                   f"CGNE batch per configuration: {len(m_sw)} staggered Wilson + {len(m_w)} Wilson solves, "
-                   f"{args.sources} sources", "lattice": "x".join(map(str, dims)), "masses": list(masses),
-                   "solves_per_step": len(m_sw) + len(m_w), "tol": TOL, "r": 1.0,
-                   "precision": args.precision, "configurations": "seeds 0-9, mean plaquette 0.59",
-                   "reliable_delta": sw.sw_get_param(sw.SW_PARAM_RELIABLE_DELTA_F16 if args.precision == "f16"
-                                                     else sw.SW_PARAM_RELIABLE_DELTA),
-                   "chunk": int(sw.sw_get_param(sw.SW_PARAM_CHUNK)),
-                   "graphs": int(sw.sw_get_param(sw.SW_PARAM_GRAPHS)),
-                   "site_blocking": int(sw.sw_get_param(sw.SW_PARAM_SITE_BLOCKING)),
-                   "group_fast": int(sw.sw_get_param(sw.SW_PARAM_GROUP_FAST)),
-                   "autotune": tune,
-                   "systems_per_thread": {"sw": int(sw.sw_get_param(sw.SW_PARAM_NS_SW)),
-                                          "wilson": int(sw.sw_get_param(sw.SW_PARAM_NS_WILSON))},
-                   "l2": "inputs larger than L2: a step touches ~10 GB and each step uses a new configuration",
-                   "parallelism": f"replicas x{world}",
-                   "operator_batches": ("concurrent, one stream and host thread each"
-                                        if (args.concurrent_ops and args.ops == "both") else "one after the other")},
+        "config": workload_config(WORKLOAD if (dims == DIMS and args.sources == "point") else
+                                  f"CGNE batch per configuration: {len(m_sw)} staggered Wilson + {len(m_w)} Wilson "
+                                  f"solves, {args.sources} sources", dims, masses),
+        "settings": {"solves_per_step": len(m_sw) + len(m_w), "r": 1.0,
+                     "precision": args.precision, "configurations": "seeds 0-9, mean plaquette 0.59",
+                     "reliable_delta": sw.sw_get_param(sw.SW_PARAM_RELIABLE_DELTA_F16 if args.precision == "f16"
+                                                       else sw.SW_PARAM_RELIABLE_DELTA),
+                     "chunk": int(sw.sw_get_param(sw.SW_PARAM_CHUNK)),
+                     "graphs": int(sw.sw_get_param(sw.SW_PARAM_GRAPHS)),
+                     "site_blocking": int(sw.sw_get_param(sw.SW_PARAM_SITE_BLOCKING)),
+                     "group_fast": int(sw.sw_get_param(sw.SW_PARAM_GROUP_FAST)),
+                     "autotune": tune,
+                     "systems_per_thread": {"sw": int(sw.sw_get_param(sw.SW_PARAM_NS_SW)),
+                                            "wilson": int(sw.sw_get_param(sw.SW_PARAM_NS_WILSON))},
+                     "parallelism": f"replicas x{world}",
+                     "operator_batches": ("concurrent, one stream and host thread each"
+                                          if (args.concurrent_ops and args.ops == "both") else "one after the other")},
         "clocks": ck, "gpu_launches": int(launches), "roofline": roof, "roofline_hbm_top": roof_hbm,
+        "fp64_peak_tflops": {"value": round(fp64_peak, 4), "kind": "measured",
+                             "how": "library FMA-throughput kernel (sw_measure_fp64_peak): every SM filled with "
+                                    "independent FP64 FMA chains, best of 3 event-timed launches"},
         "kernels": kernels,
         "latency_ms": {"p50": round(float(np.percentile(lats, 50)), 2),
                        "p99": round(float(np.percentile(lats, 99)), 2),
@@ -596,6 +616,10 @@ def run_ours(args):
         line["f64_baseline"] = f64
     if serving:
         line["serving"] = serving
+    if batched:
+        line["batched"] = batched
+    if large:
+        line["large_volume"] = large
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(Uh[seeds[0]], by_mass, dims)
     if rank == 0:
@@ -604,32 +628,150 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ further workloads
+def run_workload(sw, torch, dev, dims, op, precision, nsrc, masses, steps=1, warmup=1, persistent=False):
+    """One operator's batch on one lattice (configuration seed 0, mean
+    plaquette 0.59): nsrc real Z2-noise sources x the masses, one
+    cgne_solve_batch per step to the FP64 true residual 1e-8.  The timed steps
+    run with kernel timing on (host-driven rounds) unless `persistent`, which
+    runs each batch as one device-driven CUDA graph launch (no kernel timing).
+    Returns solves/s (CUDA events on the stream), iterations and the stencil
+    kernels' roofline fractions."""
+    import lattice_synth as ls
+    V = ls.volume(dims)
+    nc = 3 if op == sw.SW_OP_STAGGERED_WILSON else 12
+    shape = (V, 3) if nc == 3 else (V, 4, 3)
+    U = torch.from_numpy(ls.su3_links(dims, 0, ls.PLAQ_EPS, processes=min(16, os.cpu_count() or 1))).to(dev)
+    W = None
+    if nc == 3:
+        W = torch.empty((V, 8, 3, 3), dtype=torch.complex128, device=dev)
+        sw.sw_hypercube_build(dims, U, W)
+    ms = [m for m in masses for _ in range(nsrc)]
+    chi = torch.empty((len(ms),) + shape, dtype=torch.complex128, device=dev)
+    for k in range(nsrc):
+        z = torch.from_numpy(ls.z2_source(dims, nc, k).reshape(shape)).to(dev)
+        for i in range(len(masses)):
+            chi[i * nsrc + k] = z
+        del z
+    x = torch.zeros_like(chi)
+    stream = torch.cuda.current_stream(dev)
+    old = sw.sw_get_param(sw.SW_PARAM_PERSISTENT)
+
+    def solve():
+        x.zero_()
+        rc, infos = sw.cgne_solve_batch(dims, op, U, W, chi, x, ms, 1.0, TOL, 100000, precision, stream=stream)
+        for inf in infos:
+            if inf.status != sw.SW_OK or not (inf.true_rel_resid <= TOL):
+                raise RuntimeError(f"solve failed: {inf}")
+        return infos
+
+    try:
+        sw.sw_set_param(sw.SW_PARAM_PERSISTENT, 1 if persistent else 0)
+        for _ in range(warmup):
+            solve()
+        if not persistent:
+            sw.sw_profile_reset()
+            sw.sw_profile_enable(True)
+        launches0 = sw.sw_kernel_launches()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = []
+        for _ in range(steps):
+            infos += solve()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sw.sw_profile_enable(False)
+    finally:
+        sw.sw_set_param(sw.SW_PARAM_PERSISTENT, old)
+    tms = e0.elapsed_time(e1)
+    by_mass = {}
+    for m, inf in zip(ms * steps, infos):
+        by_mass.setdefault(m, []).append(inf.iters)
+    out = {"lattice": "x".join(map(str, dims)), "operator": "sw" if nc == 3 else "wilson",
+           "precision": {sw.SW_PREC_F32_RELIABLE: "f32", sw.SW_PREC_F16_RELIABLE: "f16"}.get(precision, "f64"),
+           "systems": len(ms), "sources": f"{nsrc} Z2", "masses": list(masses), "steps": steps,
+           "solves_per_s": round(len(ms) * steps / (tms / 1e3), 3), "ms_per_step": round(tms / steps, 1),
+           "iters_by_mass": {str(m): float(np.mean(v)) for m, v in by_mass.items()},
+           "gpu_launches": int(sw.sw_kernel_launches() - launches0),
+           "sqrt_kappa_by_mass": {str(m): round(float(np.mean([np.sqrt(i.kappa) for mm, i in zip(ms * steps, infos)
+                                                                if mm == m])), 2) for m in masses}}
+    if persistent:
+        out["launch"] = "one device-driven CUDA graph launch per batch (conditional WHILE node over rounds)"
+    else:
+        peak, kind = measured_peaks()
+        kernels, _, _ = classify_kernels(sw.sw_profile_read(), peak, kind)
+        out["dslash"] = {k: {kk: v[kk] for kk in ("ms_per_launch", "frac_hbm", "frac_fp32", "bound") if kk in v}
+                         for k, v in kernels.items() if ".k1." in k or ".k2." in k}
+        out["iteration_frac_hbm"] = {k: v["frac_hbm"] for k, v in kernels.items() if k.endswith(".iteration")}
+    del chi, x, U, W
+    torch.cuda.empty_cache()
+    sw.sw_trim_workspace()
+    return out
+
+
+def run_large_volume(sw, torch, dev):
+    """48^3x96 staggered Wilson and 32^3x64 Wilson at the smallest bare mass
+    0.01 and three more, 4 Z2 sources each, FP32 storage and FP16 storage
+    (12-real links, per-site-scaled vectors), FP64 reliable updates."""
+    masses = (0.01, 0.02, 0.05, 0.1)
+    out = []
+    for dims, op in (((48, 48, 48, 96), sw.SW_OP_STAGGERED_WILSON), ((32, 32, 32, 64), sw.SW_OP_WILSON)):
+        for prec in (sw.SW_PREC_F32_RELIABLE, sw.SW_PREC_F16_RELIABLE):
+            out.append(run_workload(sw, torch, dev, dims, op, prec, 4, masses))
+    return out
+
+
+def run_batched(sw, torch, dev):
+    """24^3x48, 12 Z2 sources x 6 masses per operator (72 systems each), FP32
+    inner iterations with FP64 reliable updates: each operator's batch as one
+    device-driven CUDA graph launch, then one host-driven step with kernel timing."""
+    masses = (0.02, 0.04, 0.06, 0.1, 0.15, 0.2)
+    out = {}
+    for op, name in ((sw.SW_OP_STAGGERED_WILSON, "sw"), (sw.SW_OP_WILSON, "wilson")):
+        out[name] = {"persistent": run_workload(sw, torch, dev, (24, 24, 24, 48), op, sw.SW_PREC_F32_RELIABLE, 12,
+                                                masses, persistent=True),
+                     "profiled": run_workload(sw, torch, dev, (24, 24, 24, 48), op, sw.SW_PREC_F32_RELIABLE, 12,
+                                              masses, warmup=0)}
+    tot = sum(v["persistent"]["systems"] for v in out.values())
+    secs = sum(v["persistent"]["systems"] / v["persistent"]["solves_per_s"] for v in out.values())
+    out["solves_per_s_both_operators"] = round(tot / secs, 3)
+    return out
+
+
 # ------------------------------------------------------------------ serving phase
 def run_serving(sw, torch, dev, args, seed=0, slots=8):
     """Poisson stream of solve requests through the continuous-batching server:
-    lattices drawn uniformly from --serving-lattices, operator uniform
-    (staggered Wilson or Wilson), bare mass uniform in [0.02, 0.2], complex
-    Gaussian sources, FP32 inner / FP64 reliable updates, tol 1e-8.  The rate is
-    80% of the capacity measured by a burst of requests first."""
+    lattices drawn uniformly from --serving-lattices (one resident gauge field
+    each), operator uniform (staggered Wilson or Wilson), inner precision
+    uniform (FP32 or FP16 storage; FP64 reliable updates), bare mass uniform in
+    [0.02, 0.2], complex Gaussian sources, tol 1e-8.  Requests name a field,
+    operator and precision; the server admits them by device memory, creating
+    each (field, operator, precision) engine on demand within its budget.  The
+    rate is 80% of the capacity measured by a burst of requests first (after
+    one warm-up request per engine)."""
     import lattice_synth as ls
     lats = [tuple(int(v) for v in t.split("x")) for t in args.serving_lattices.split(",")]
     rng = np.random.default_rng(seed)
     srv = sw.Server(200 << 30)
-    engines, pools = [], []
+    classes, pools, fields = [], [], []
+    precs = (sw.SW_PREC_F32_RELIABLE, sw.SW_PREC_F16_RELIABLE)
     for li, dims in enumerate(lats):
         Ud = torch.from_numpy(ls.su3_links(dims, 100 + li, ls.PLAQ_EPS, processes=min(16, os.cpu_count() or 1))).to(dev)
+        f = srv.add_field(dims, Ud, slots)
+        del Ud
+        V = ls.volume(dims)
         for op in (sw.SW_OP_STAGGERED_WILSON, sw.SW_OP_WILSON):
             nc = 3 if op == sw.SW_OP_STAGGERED_WILSON else 12
-            engines.append((dims, op, srv.add_engine(dims, op, Ud, 1.0, sw.SW_PREC_F32_RELIABLE, slots)))
-            V = ls.volume(dims)
             srcs = []
             for j in range(2):
                 c = torch.empty((V, nc), dtype=torch.complex128).pin_memory().numpy()
                 c[:] = ls.gaussian_source(dims, nc, 1000 * li + 10 * op + j)
                 srcs.append(c)
-            outs = [torch.empty((V, nc), dtype=torch.complex128).pin_memory().numpy() for _ in range(3 * slots)]
-            pools.append({"src": srcs, "free": list(range(len(outs))), "out": outs})
-        del Ud
+            for prec in precs:
+                outs = [torch.empty((V, nc), dtype=torch.complex128).pin_memory().numpy() for _ in range(3 * slots)]
+                classes.append((dims, op, prec, f))
+                pools.append({"src": srcs, "free": list(range(len(outs))), "out": outs})
     pending = {}
 
     def submit(k):
@@ -637,8 +779,9 @@ def run_serving(sw, torch, dev, args, seed=0, slots=8):
         if not pool["free"]:
             return False
         o = pool["free"].pop()
-        rid = srv.submit(engines[k][2], pool["src"][int(rng.integers(0, 2))], pool["out"][o],
-                         float(rng.uniform(0.02, 0.2)), TOL)
+        dims, op, prec, f = classes[k]
+        rid = srv.submit_field(f, op, pool["src"][int(rng.integers(0, 2))], pool["out"][o],
+                               float(rng.uniform(0.02, 0.2)), prec, tol=TOL)
         pending[rid] = (k, o)
         return True
 
@@ -648,54 +791,65 @@ def run_serving(sw, torch, dev, args, seed=0, slots=8):
             pools[k]["free"].append(o)
             res.append((k, info))
 
+    def drain(res):
+        while pending:
+            collect(res)
+            time.sleep(0.0005)
+
+    warm = []
+    for k in range(len(classes)):  # every engine created on demand once
+        submit(k)
+    drain(warm)
     # capacity: a burst of requests with every engine busy
     burst = []
     t0 = time.perf_counter()
     nb = 0
     for _ in range(3):
-        for k in range(len(engines)):
+        for k in range(len(classes)):
             nb += submit(k)
-    while pending:
-        collect(burst)
-        time.sleep(0.0005)
+    drain(burst)
     cap = nb / (time.perf_counter() - t0)
     rate = 0.8 * cap
     # Poisson stream at 80% of capacity
     n = args.serving_requests
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
-    picks = rng.integers(0, len(engines), size=n)
-    res, waited = [], 0
+    picks = rng.integers(0, len(classes), size=n)
+    res = []
     t0 = time.perf_counter()
     for a, k in zip(arrivals, picks):
         while time.perf_counter() - t0 < a:
             collect(res)
             time.sleep(0.0002)
-        while not submit(int(k)):  # this engine's output buffers are all in flight
+        while not submit(int(k)):  # this class's output buffers are all in flight
             collect(res)
-            waited += 1
             time.sleep(0.0002)
-    while pending:
-        collect(res)
-        time.sleep(0.0005)
+    drain(res)
     wall = time.perf_counter() - t0
+    stats = srv.stats()
     srv.close()
-    bad = [i for _, i in res if i.status != sw.SW_OK or not i.true_rel_resid <= TOL]
+    bad = [i for _, i in warm + burst + res if i.status != sw.SW_OK or not i.true_rel_resid <= TOL]
     if bad:
         raise RuntimeError(f"serving: {len(bad)} requests failed, e.g. {bad[0]}")
     lat = np.array([i.seconds * 1e3 for _, i in res])
     per = {}
     for k, i in res:
-        d, op, _ = engines[k]
-        key = "x".join(map(str, d)) + ("/sw" if op == sw.SW_OP_STAGGERED_WILSON else "/wilson")
+        d, op, prec, _ = classes[k]
+        key = ("x".join(map(str, d)) + ("/sw" if op == sw.SW_OP_STAGGERED_WILSON else "/wilson") +
+               ("/f16" if prec == sw.SW_PREC_F16_RELIABLE else "/f32"))
         per.setdefault(key, []).append(i.seconds * 1e3)
     return {"requests": n, "solves_per_s": round(n / wall, 2), "capacity_burst_solves_per_s": round(cap, 2),
             "offered_rate_per_s": round(rate, 2),
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 2),
                            "p99": round(float(np.percentile(lat, 99)), 2)},
             "latency_p50_ms_by_engine": {k: round(float(np.median(v)), 2) for k, v in sorted(per.items())},
-            "slots_per_engine": slots, "engines": len(engines),
+            "slots_per_engine": slots, "engines": len(classes),
+            "admission": {k: stats[k] for k in ("engines_created", "engines_retired", "requests_waited_for_memory",
+                                                "bytes_charged", "budget")},
             "workload": "Poisson arrivals at 80% of burst capacity; lattices " + args.serving_lattices +
-                        "; operator uniform; mass U[0.02,0.2]; Gaussian sources; tol 1e-8; FP32 inner + FP64"}
+                        "; operator uniform; inner precision uniform over FP32 / FP16 storage (FP64 reliable "
+                        "updates); mass U[0.02,0.2]; Gaussian sources; tol 1e-8; requests name a resident field "
+                        "and the server creates each (field, operator, precision) engine on demand within its "
+                        "device-memory budget"}
 
 
 # ------------------------------------------------------------------ CPU oracle sample
@@ -824,8 +978,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "masses": list(MASSES),
-                   "tol": TOL, "parallelism": "cpu oracle, rank 0 only"},
+        "config": workload_config(WORKLOAD, DIMS, MASSES),
+        "settings": {"parallelism": "cpu oracle, rank 0 only"},
         "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,

@@ -219,12 +219,22 @@ int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, const void*
  *   call takes the value current when it starts.
  * SW_PARAM_GROUP_FAST: 1 makes the system groups the fastest grid dimension
  *   of the stencil kernels, 0 (default) the tiles.
+ * SW_PARAM_PERSISTENT: 1 runs each cgne_solve / cgne_solve_batch call as one
+ *   launch of one CUDA graph: the admission kernels, then a conditional WHILE
+ *   node that loops over rounds on the device (reliable updates beside a
+ *   chunk of SW_PARAM_CHUNK iterations; the loop ends when no system is in
+ *   flight), then the read of the status words: one launch and one host
+ *   synchronisation per call, with results bit-identical to the host-driven
+ *   rounds.  Its grids are sized for every system of the batch.  0 (default)
+ *   reads the status words on the host after every round.  Solves taken while
+ *   kernel timing is enabled (sw_profile_enable), the server's engines and
+ *   cgne_solve_noalloc always use the host-driven rounds.
  * None of these changes what a solve converges to: convergence is always
  * decided on an FP64 residual.  Returns SW_ERR_ARG for an unknown key or a
  * value out of range. */
 enum { SW_PARAM_CHUNK = 0, SW_PARAM_RELIABLE_DELTA = 1, SW_PARAM_NS_SW = 2, SW_PARAM_NS_WILSON = 3,
        SW_PARAM_GRAPHS = 4, SW_PARAM_SITE_BLOCKING = 5, SW_PARAM_GROUP_FAST = 6,
-       SW_PARAM_RELIABLE_DELTA_F16 = 9 };
+       SW_PARAM_RELIABLE_DELTA_F16 = 9, SW_PARAM_PERSISTENT = 10 };
 enum { SW_SITE_SHAPES = 6 };
 int sw_set_param(int key, double value);
 int sw_get_param(int key, double* value);
@@ -277,6 +287,12 @@ int sw_autotune_layout(const sw_lattice* lat, int op, const void* U, const void*
  * its mean time per timed launch times its issued launches.
  * Process-wide and thread-safe; disabled by default. */
 int sw_profile_enable(int on);
+/* FP64 fused multiply-add throughput of the current device in TFLOP/s, into
+ * *tflops (HOST): the best of 3 timed launches (CUDA events on `stream`, after
+ * one warm-up) of a kernel filling every SM with independent FMA chains; about
+ * 0.1 s.  The denominator of the FP64 matvecs' roofline (the reliable updates
+ * are bound by the FP64 pipe).  No counterpart in the paper.  Blocks. */
+int sw_measure_fp64_peak(double* tflops, void* stream);
 /* Total kernel launches this library has issued in the process (always on). */
 long long sw_kernel_launches(void);
 
@@ -311,11 +327,15 @@ int sw_profile_issued(int i, long long* issued);
  * iterating.  A request's result does not depend on what else is running
  * (per-slot scalars and fixed-order reductions): it is bit-identical to the
  * same request served alone.
+ * Requests either name an engine added by hand (sw_server_add_engine) or a
+ * resident field plus operator and precision (sw_server_add_field,
+ * sw_server_submit_field), for which the server creates engines on demand
+ * within its device-memory budget.
  * The paper has no serving layer; each request is one CGNE solve of Eq. 2. */
 typedef struct sw_server_s* sw_server;
 
-/* New server on the current device; engines may hold at most hbm_budget_bytes
- * of device memory in total. */
+/* New server on the current device; fields and engines may hold at most
+ * hbm_budget_bytes of device memory in total. */
 int sw_server_create(size_t hbm_budget_bytes, sw_server* out);
 
 /* Add an engine before the first submit: the links U ([V][4][3][3] complex128,
@@ -326,6 +346,40 @@ int sw_server_create(size_t hbm_budget_bytes, sw_server* out);
  * also be SW_PREC_F16_RELIABLE. */
 int sw_server_add_engine(sw_server srv, const sw_lattice* lat, int op, const void* U, double r,
                          int precision, int slots, int* engine);
+
+/* Register a resident gauge field for requests that name it
+ * (sw_server_submit_field): the links U ([V][4][3][3] complex128, device) are
+ * copied to the device (the caller may free U afterwards) and charged against
+ * the budget; slots: the system slots of every engine the server creates on
+ * this field.  May be called while serving.  SW_ERR_OOM if the field does not
+ * fit beside the fields and the engines added with sw_server_add_engine (idle
+ * engines created on demand are retired to make room). */
+int sw_server_add_field(sw_server srv, const sw_lattice* lat, const void* U, int slots, int* field);
+
+/* Queue one solve on a resident field, with the operator, r and precision
+ * (SW_PREC_*) it asks for.  Admission by device memory: the request goes to
+ * the engine of that (field, op, r, precision); if there is none, the
+ * scheduler creates it as soon as the budget allows -- first retiring
+ * engines it created on demand that hold no request, least recently used
+ * first -- and until then the request waits (requests behind it whose engines
+ * exist go ahead).  Other arguments as for sw_server_submit.  SW_ERR_OOM at
+ * once if that engine could never fit beside the fields and the engines added
+ * with sw_server_add_engine. */
+int sw_server_submit_field(sw_server srv, int field, int op, double r, int precision, const void* chi_host,
+                           void* x_host, double mass, double tol, int max_iter, long long* request);
+
+typedef struct {
+  int engines_live;                      /* engines holding device memory */
+  int engines_created;                   /* engines created on demand for field requests */
+  int engines_retired;                   /* on-demand engines retired to free memory */
+  long long requests_waited_for_memory;  /* field requests that had to wait for their engine's memory */
+  long long requests_waiting;            /* field requests waiting for memory now */
+  unsigned long long bytes_charged;      /* device bytes charged against the budget now */
+  unsigned long long budget;             /* the budget */
+} sw_server_stats_t;
+
+/* Counters of the server's memory admission into *out (HOST). */
+int sw_server_stats(sw_server srv, sw_server_stats_t* out);
 
 /* Queue one solve on an engine.  chi_host: the source ([V][3] or [V][4][3]
  * complex128, HOST memory, pinned for asynchronous copies); x_host: HOST

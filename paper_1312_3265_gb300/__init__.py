@@ -16,8 +16,8 @@ from ._binding import (  # noqa: F401
     SW_PREC_F64, SW_PREC_F32_RELIABLE, SW_PREC_F16_RELIABLE,
     sw_hypercube_build, sw_dslash_apply, wilson_dslash_apply, dslash_apply_inner, cgne_solve, cgne_solve_batch,
     sw_status_string, sw_last_cuda_error, sw_profile_enable, sw_profile_reset, sw_profile_read,
-    sw_kernel_launches, sw_workspace_reserved, sw_trim_workspace, cgne_solve_noalloc, sw_set_param, sw_get_param,
+    sw_kernel_launches, sw_measure_fp64_peak, sw_workspace_reserved, sw_trim_workspace, cgne_solve_noalloc, sw_set_param, sw_get_param,
     sw_autotune, sw_autotune_layout, SW_PARAM_CHUNK, SW_PARAM_RELIABLE_DELTA, SW_PARAM_NS_SW, SW_PARAM_NS_WILSON, SW_PARAM_GRAPHS,
     SW_PARAM_SITE_BLOCKING, SW_PARAM_GROUP_FAST,
-    SW_PARAM_RELIABLE_DELTA_F16, SW_SITE_SHAPES,
+    SW_PARAM_RELIABLE_DELTA_F16, SW_PARAM_PERSISTENT, SW_SITE_SHAPES,
 )

@@ -22,6 +22,7 @@ SW_PARAM_GRAPHS = 4
 SW_PARAM_SITE_BLOCKING = 5
 SW_PARAM_GROUP_FAST = 6
 SW_PARAM_RELIABLE_DELTA_F16 = 9
+SW_PARAM_PERSISTENT = 10
 SW_SITE_SHAPES = 6  # SW_PARAM_SITE_BLOCKING values: 0 lexicographic, 1..5 site-block shapes
 
 
@@ -33,6 +34,12 @@ class _Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("status", ctypes.c_int),
                 ("precision", ctypes.c_int), ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("lambda_min", ctypes.c_double), ("lambda_max", ctypes.c_double)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("engines_live", ctypes.c_int), ("engines_created", ctypes.c_int), ("engines_retired", ctypes.c_int),
+                ("requests_waited_for_memory", ctypes.c_longlong), ("requests_waiting", ctypes.c_longlong),
+                ("bytes_charged", ctypes.c_ulonglong), ("budget", ctypes.c_ulonglong)]
 
 
 @dataclass
@@ -97,12 +104,16 @@ def lib():
         L.sw_server_create.argtypes = [ctypes.c_size_t, ctypes.POINTER(srv)]
         L.sw_server_add_engine.argtypes = [srv, lat, i, vp, d, i, i, ctypes.POINTER(i)]
         L.sw_server_submit.argtypes = [srv, i, vp, vp, d, d, i, ctypes.POINTER(ctypes.c_longlong)]
+        L.sw_server_add_field.argtypes = [srv, lat, vp, i, ctypes.POINTER(i)]
+        L.sw_server_submit_field.argtypes = [srv, i, i, d, i, vp, vp, d, d, i, ctypes.POINTER(ctypes.c_longlong)]
+        L.sw_server_stats.argtypes = [srv, ctypes.POINTER(_ServerStats)]
         L.sw_server_poll.argtypes = [srv, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_Info),
                                      ctypes.POINTER(i)]
         L.sw_server_drain.argtypes = [srv, d]
         L.sw_server_destroy.argtypes = [srv]
         for f in ("sw_server_create", "sw_server_add_engine", "sw_server_submit", "sw_server_poll",
-                  "sw_server_drain", "sw_server_destroy"):
+                  "sw_server_drain", "sw_server_destroy", "sw_server_add_field", "sw_server_submit_field",
+                  "sw_server_stats"):
             getattr(L, f).restype = i
         L.sw_autotune.argtypes = [lat, i, vp, vp, i, i, d, i, ctypes.POINTER(d), ctypes.POINTER(i), vp]
         L.sw_autotune.restype = i
@@ -113,6 +124,8 @@ def lib():
         L.sw_get_param.argtypes = [i, ctypes.POINTER(d)]
         L.sw_set_param.restype = i
         L.sw_get_param.restype = i
+        L.sw_measure_fp64_peak.argtypes = [ctypes.POINTER(d), vp]
+        L.sw_measure_fp64_peak.restype = i
         L.sw_kernel_launches.argtypes = []
         L.sw_kernel_launches.restype = ctypes.c_longlong
         L.sw_workspace_reserved.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
@@ -251,6 +264,13 @@ def sw_profile_read():
     return out
 
 
+def sw_measure_fp64_peak(stream=None):
+    """FP64 FMA throughput of the current device, TFLOP/s (measured by the library)."""
+    v = ctypes.c_double()
+    _check(lib().sw_measure_fp64_peak(ctypes.byref(v), _stream(stream)), "sw_measure_fp64_peak")
+    return v.value
+
+
 def sw_kernel_launches():
     return int(lib().sw_kernel_launches())
 
@@ -322,6 +342,28 @@ class Server:
                                       float(tol), int(max_iter), ctypes.byref(rid)), "sw_server_submit")
         self._keep[rid.value] = (chi_host, x_host)
         return rid.value
+
+    def add_field(self, dims, U, slots=8, t_antiperiodic=False):
+        """Resident gauge field for submit_field; returns its index."""
+        f = ctypes.c_int()
+        _check(lib().sw_server_add_field(self._h, _lat(dims, t_antiperiodic), _ptr(U), int(slots), ctypes.byref(f)),
+               "sw_server_add_field")
+        return f.value
+
+    def submit_field(self, field, op, chi_host, x_host, mass, precision=SW_PREC_F32_RELIABLE, r=1.0, tol=1e-8,
+                     max_iter=100000):
+        """Queue a solve on a resident field; the server admits it by device memory."""
+        rid = ctypes.c_longlong()
+        _check(lib().sw_server_submit_field(self._h, int(field), int(op), float(r), int(precision), _host_ptr(chi_host),
+                                            _host_ptr(x_host), float(mass), float(tol), int(max_iter),
+                                            ctypes.byref(rid)), "sw_server_submit_field")
+        self._keep[rid.value] = (chi_host, x_host)
+        return rid.value
+
+    def stats(self):
+        st = _ServerStats()
+        _check(lib().sw_server_stats(self._h, ctypes.byref(st)), "sw_server_stats")
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_}
 
     def poll(self, max_n=1024):
         ids = (ctypes.c_longlong * max_n)()

@@ -20,6 +20,8 @@
 // other systems share the launch -- so a system gives bit-identical results
 // alone and in any batch.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "dslash.cuh"
 
@@ -115,6 +117,7 @@ struct SWOp {
   static constexpr int kGaugeBytes = G::kBytes + Wt::kBytes;  // stored links + transports per site
   static constexpr double kFlops = 1743.0;  // per site and application (Eq. 4)
   static constexpr const char* kPrec = G::kPrec;
+  static constexpr bool kHalf = std::is_same<G, GaugeP16>::value;  // FP16 storage
   // default systems per thread in the CG kernels (FP32 shares each matrix load
   // over several systems; FP64 is ALU-bound and gains nothing from it)
   static constexpr int kNS = sizeof(T) == 4 ? 4 : 1;
@@ -132,7 +135,10 @@ struct SWOp {
   __device__ __forceinline__ void apply_multi(const GG& g, int n, const Vec& in, size_t stride, unsigned act,
                                               const T* m, T r, bool dag, CV<T, 3>* out) const {
     V3<T> o[NS];
-    sw_site_multi<T, NS>(g, n, U, W, in, stride, act, m, r, dag, o);
+    if constexpr (std::is_same<T, float>::value && NS % 2 == 0)
+      sw_site_multi_pair<NS>(g, n, U, W, in, stride, act, m, r, dag, o);  // two systems per float2
+    else
+      sw_site_multi<T, NS>(g, n, U, W, in, stride, act, m, r, dag, o);
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -148,8 +154,10 @@ struct WOp {
   static constexpr int kGaugeBytes = G::kBytes;
   static constexpr const char* kPrec = G::kPrec;
   static constexpr double kFlops = 1392.0;  // per site and application (Eq. 4)
+  static constexpr bool kHalf = std::is_same<G, GaugeP16>::value;  // FP16 storage
   static constexpr int kNS = 1;
   using Vec = VA<12>;
+
   G U;
   __device__ __forceinline__ CV<T, 12> apply(const Geom& g, int n, const Vec& in, T m, T r, bool dag) const {
     const Sp<T> o = wilson_site<T, R1>(g, n, U, in, m, r, dag);
@@ -202,6 +210,41 @@ __device__ __forceinline__ void st_site(const VecP32q<NC>& v, int n, const CV<fl
     v.p[pk(n, NC / 2, q)] = make_float4(a.c[2 * q].re, a.c[2 * q].im, a.c[2 * q + 1].re, a.c[2 * q + 1].im);
 }
 
+// Load a whole site: plain accessors component by component; the float4
+// layouts with one 16-byte load per pair of components.
+template <typename Vec> struct SiteLoad {
+  template <typename T, int NC> static __device__ __forceinline__ CV<T, NC> ld(const Vec& v, int n) {
+    CV<T, NC> a;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) a.c[c] = v.ld(n, c);
+    return a;
+  }
+};
+template <int NC> struct SiteLoad<VecP32q<NC>> {
+  template <typename T, int N> static __device__ __forceinline__ CV<float, NC> ld(const VecP32q<NC>& v, int n) {
+    CV<float, NC> a;
+    const float4* b = v.p + pk(n, NC / 2, 0);
+#pragma unroll
+    for (int q = 0; q < NC / 2; ++q) {
+      const float4 w = __ldg(b + q * 16);
+      a.c[2 * q] = {w.x, w.y};
+      a.c[2 * q + 1] = {w.z, w.w};
+    }
+    return a;
+  }
+};
+template <typename T, int NC, typename Vec> __device__ __forceinline__ CV<T, NC> ld_site(const Vec& v, int n) {
+  return SiteLoad<Vec>::template ld<T, NC>(v, n);
+}
+
+// FP32 residual / solution storage that goes with a stencil storage: the
+// Wilson float4 planes keep r and x in float4 planes too (the r update of k2
+// and the streaming k3 then move whole sites in 16-byte units, half the
+// memory instructions of float2 planes); every other storage pairs with plain
+// float2 planes.
+template <typename VF, int NC> struct RVecOf { using type = VecP32<NC>; };
+template <> struct RVecOf<VecP32q<12>, 12> { using type = VecP32q<12>; };
+
 // Per-system view of a batched vector: system `sys` starts `sys * sstride`
 // complex numbers after the base pointer (layout inside a system unchanged).
 template <typename Vec> __device__ __forceinline__ Vec sys_view(Vec v, int sys, size_t sstride) {
@@ -215,6 +258,19 @@ struct BatchParams {
   size_t sstride64;    // same for FP64 canonical vectors
   size_t vstride;      // same for the stencil vectors p and t
 };
+
+// (D+m) or (D+m)^+ at site n for the systems of a group selected by `act`
+// (register-blocked: every gauge load is shared by the group's systems), each
+// result handed to f(s, v).
+template <int NS, typename Op, typename GG, typename T, typename F>
+__device__ __forceinline__ void site_results(const Op& op, const GG& g, int n, const typename Op::Vec& in,
+                                             size_t stride, unsigned act, const T* m, T r, bool dag, F&& f) {
+  CV<T, Op::NC> v[NS];
+  op.template apply_multi<NS, GG>(g, n, in, stride, act, m, r, dag, v);
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+    if (act & (1u << s)) f(s, v[s]);
+}
 
 // ---------------------------------------------------------------- plain apply (ABI)
 // out = (D+m) in, or (D+m)^+ in with dagger; with has_sub, out = sub - (D+m) in
@@ -303,10 +359,15 @@ __device__ __forceinline__ unsigned running_mask(const SysState* S, int sys0, in
 // Minimum resident blocks per SM requested from the compiler for the
 // inner-precision stencil kernels (caps their registers): they are
 // latency-bound, so more resident warps hide more of the L2 latency
-// (staggered Wilson 8 blocks = 64 registers, Wilson 7 = 72, chosen from the
-// spill counts of ptxas and GB300 timings).  FP64 kernels are ALU-bound: no cap.
+// (FP32 storage: staggered Wilson 8 blocks = 64 registers, Wilson 7 = 72,
+// chosen from the spill counts of ptxas and GB300 timings).  The FP16-storage
+// stencils also convert and scale every value they load: at 7 blocks they
+// spill about 0.5 KB per thread (Wilson) and take 5 blocks (96 registers,
+// no spills), staggered Wilson 7.  FP64 kernels are ALU-bound: no cap.
 template <typename T, typename Op> constexpr int stencil_min_blocks() {
-  return sizeof(T) == 4 ? (Op::NC == 3 ? 8 : 7) : 1;
+  if (sizeof(T) != 4) return 1;
+  if (Op::kHalf) return Op::NC == 3 ? 7 : 5;
+  return Op::NC == 3 ? 8 : 7;
 }
 
 template <typename T, typename Op, int NS, typename GG>
@@ -337,17 +398,13 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k1(GG g
 #pragma unroll
     for (int s = 0; s < NS; ++s) acc[s] = 0.0;
     if (n < g.V) {
-      CV<T, Op::NC> v[NS];
-      op.template apply_multi<NS, GG>(g, n, p, bp.vstride, act, m, (T)bp.r, false, v);
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        if (!(act & (1u << s))) continue;
-        st_site(sys_at(t, s, bp.vstride), n, v[s]);
+      site_results<NS>(op, g, n, p, bp.vstride, act, m, (T)bp.r, false, [&](int s, const CV<T, Op::NC>& v) {
+        st_site(sys_at(t, s, bp.vstride), n, v);
         T a = T(0);
 #pragma unroll
-        for (int c = 0; c < Op::NC; ++c) a += norm2(v[s].c[c]);
+        for (int c = 0; c < Op::NC; ++c) a += norm2(v.c[c]);
         acc[s] = (double)a;
-      }
+      });
     }
     put_warp_sums<NS>(rb, sys0, act, tile, acc);
   }
@@ -403,21 +460,18 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(GG g
 #pragma unroll
     for (int s = 0; s < NS; ++s) acc[s] = 0.0;
     if (n < g.V) {
-      CV<T, Op::NC> ap[NS];
-      op.template apply_multi<NS, GG>(g, n, t, bp.vstride, act, m, (T)bp.r, true, ap);
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        if (!(act & (1u << s))) continue;
+      site_results<NS>(op, g, n, t, bp.vstride, act, m, (T)bp.r, true, [&](int s, const CV<T, Op::NC>& ap) {
         const RVec rs = sys_at(r, s, bp.sstride);
+        CV<T, Op::NC> rv = ld_site<T, Op::NC>(rs, n);
         T a = T(0);
 #pragma unroll
         for (int c = 0; c < Op::NC; ++c) {
-          const cx<T> rc = rs.ld(n, c) - alpha[s] * ap[s].c[c];
-          rs.st(n, c, rc);
-          a += norm2(rc);
+          rv.c[c] = rv.c[c] - alpha[s] * ap.c[c];
+          a += norm2(rv.c[c]);
         }
+        st_site(rs, n, rv);
         acc[s] = (double)a;
-      }
+      });
     }
     put_warp_sums<NS>(rb, sys0, act, tile, acc);
   }
@@ -461,17 +515,17 @@ __global__ void __launch_bounds__(256) cg_k3(int V, RVec r, PVec p, RVec x, size
   x = sys_view(x, sys, rstride);
   const T beta = (T)S[sys].beta, alpha = (T)S[sys].alpha;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < V; n += gridDim.x * blockDim.x) {
-    CV<T, NC> po;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) po.c[c] = p.ld(n, c);
+    const CV<T, NC> po = ld_site<T, NC>(p, n);
     if (mode & 1) {
+      CV<T, NC> xv = ld_site<T, NC>(x, n);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) x.st(n, c, x.ld(n, c) + alpha * po.c[c]);
+      for (int c = 0; c < NC; ++c) xv.c[c] = xv.c[c] + alpha * po.c[c];
+      st_site(x, n, xv);
     }
     if (mode & 2) {
-      CV<T, NC> v;
+      CV<T, NC> v = ld_site<T, NC>(r, n);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) v.c[c] = r.ld(n, c) + beta * po.c[c];
+      for (int c = 0; c < NC; ++c) v.c[c] = v.c[c] + beta * po.c[c];
       st_site(p, n, v);
     }
   }
@@ -563,10 +617,8 @@ __global__ void __launch_bounds__(kTile) rhs_lo(GG g, Op op, typename Op::Vec ch
       op.template apply_multi<1, GG>(g, n, chi, bp.vstride, 1u, &m, (T)bp.r, true, &v);
       T a = T(0);
 #pragma unroll
-      for (int c = 0; c < Op::NC; ++c) {
-        r.st(n, c, v.c[c]);
-        a += norm2(v.c[c]);
-      }
+      for (int c = 0; c < Op::NC; ++c) a += norm2(v.c[c]);
+      st_site(r, n, v);
       st_site(p, n, v);
       acc = (double)a;
     }

@@ -383,6 +383,23 @@ template <int NC> struct VecP32q {
   }
 };
 
+// Packed two-lane FP32 arithmetic (one f32x2 instruction for two FP32
+// operations; an operand used in both lanes is broadcast).
+// (The library is built for sm_103a only; the lane-by-lane forms exist so that
+// host-side tests that include this header compile for the default arch.)
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+#if !defined(__CUDA_ARCH__) || __CUDA_ARCH__ >= 1000
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+#else
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+#endif
+
 // Packed FP16 storage (mixed precision "half" mode; arithmetic stays FP32).
 //   links: the first two rows only (12 reals) as 6 half2 planes per direction
 //          (24 planes); the third row is rebuilt as conj(row0 x row1), exact

@@ -38,6 +38,7 @@ double param_delta(bool half);
 int param_ns(int nc);  // systems per thread of the FP32 stencils (1, 2 or 4) for NC components
 bool param_group_fast();     // system groups as the fastest grid dimension of the stencils
 bool param_graphs();   // replay chunks of iterations as captured CUDA graphs
+bool param_persistent();  // whole solve as one CUDA graph with a device-driven loop of rounds
 
 inline int grid_for(const void* kernel, int block, int V, int nsys, int cap) {
   static std::mutex mu;
@@ -152,6 +153,7 @@ struct Workspace {
   double* mass;
   double* hist;  // CG coefficients, [nsys][kHist][2]
   int* pcount;   // systems computed per sampled launch: [kProfSlots/2][3] (k1, k2, k3), then the FP64 samples
+  int* ctl;      // device-driven solve: [0] rounds run, [1] round cap reached
 };
 
 constexpr int kProfSlots = 1024;  // sampled iterations per solve
@@ -168,7 +170,8 @@ inline size_t workspace_bytes_pt(int V, int NC, int nsys, bool mixed, size_t pt)
   b += mixed ? 2 * align_up(pt * nsys) + 2 * align_up(sizeof(float2) * n) : align_up(pt * nsys);
   b += align_up(sizeof(SysState) * nsys) + align_up(sizeof(double) * 2 * kWarps * ntiles * nsys) +
        align_up(sizeof(unsigned) * 2 * nsys) + align_up(sizeof(double) * nsys) +
-       align_up(sizeof(double) * 2 * kHist * nsys) + align_up(sizeof(int) * 2 * kProfSlots);
+       align_up(sizeof(double) * 2 * kHist * nsys) + align_up(sizeof(int) * 2 * kProfSlots) +
+       align_up(sizeof(int) * 8);
   return b;
 }
 // FP64 or FP32 storage of p and t
@@ -207,6 +210,7 @@ inline Workspace carve_workspace_pt(void* base, int V, int NC, int nsys, bool mi
   w.mass = (double*)take(sizeof(double) * nsys);
   w.hist = (double*)take(sizeof(double) * 2 * kHist * nsys);
   w.pcount = (int*)take(sizeof(int) * 2 * kProfSlots);
+  w.ctl = (int*)take(sizeof(int) * 8);
   return w;
 }
 inline Workspace carve_workspace(void* base, int V, int NC, int nsys, bool mixed) {
@@ -242,7 +246,8 @@ class Engine {
   using V64 = typename OpD::Vec;
   using VF = typename OpF::Vec;  // stencil vectors p, t
   using TF = typename std::conditional<MIXED, float, double>::type;
-  using VR = typename std::conditional<MIXED, VecP32<NC>, V64>::type;  // r and x of the inner iteration
+  // r and x of the inner iteration
+  using VR = typename std::conditional<MIXED, typename RVecOf<VF, NC>::type, V64>::type;
   // geometry of the inner iteration: blocked site order for the packed
   // FP32/FP16 storage, the canonical order for FP64
   using GK = typename std::conditional<MIXED, GeomBlk, Geom>::type;
@@ -258,7 +263,7 @@ class Engine {
          const Workspace& ws, SysState* hs_read, SysState* hs_stage, cudaStream_t st, cudaEvent_t ev,
          bool use_graphs = true)
       : g_(g), opd_(opd), opf_(opf), r_(r), cap_(cap), chi_(chi), x_(x), ws_(ws), hr_(hs_read), hst_(hs_stage),
-        st_(st), ev_(ev), n_((size_t)g.V * NC), use_graphs_(use_graphs && param_graphs()),
+        st_(st), ist_(st), ev_(ev), n_((size_t)g.V * NC), use_graphs_(use_graphs && param_graphs()),
         driver_resources_(use_graphs) {
     ntiles_ = (g.V + kTile - 1) / kTile;
     pstride_ = kWarps * ntiles_;
@@ -271,13 +276,14 @@ class Engine {
     // run on the side: their own block tickets (per system, not per group)
     rbu_ = RedBuf{ws.partials, ws.tickets + cap, pstride_, ws.hist};
     vunits_ = VF::sys_units(g.V);
-    bp_ = BatchParams{r, n_, n_, vunits_};
+    runits_ = VR::sys_units(g.V);
+    bp_ = BatchParams{r, runits_, n_, vunits_};
     ns_ = MIXED ? param_ns(NC) : 1;
     ngrp_ = (cap + ns_ - 1) / ns_;
     set_grids(ngrp_);
     if constexpr (MIXED) {
-      fr_ = VR{ws.r32, g.V};
-      fx_ = VR{ws.x32, g.V};
+      fr_ = VR{reinterpret_cast<typename VR::unit*>(ws.r32), g.V};
+      fx_ = VR{reinterpret_cast<typename VR::unit*>(ws.x32), g.V};
       fp_ = VF{static_cast<typename VF::unit*>(ws.p_lo), g.V};
       ft_ = VF{static_cast<typename VF::unit*>(ws.t_lo), g.V};
     } else {
@@ -360,7 +366,7 @@ class Engine {
     // stencil vector (p or t) and inner-precision vector (r or x)
     const double gauge = (double)g_.V * OpF::kGaugeBytes;
     const double pv = (double)sizeof(typename VF::unit) * vunits_;
-    const double rv = (double)sizeof(typename VR::unit) * n_;
+    const double rv = (double)sizeof(typename VR::unit) * runits_;
     // flops: the paper's count per site and application (Eq. 4) for every
     // computed system (k2's r update is not counted)
     const double fl = OpF::kFlops * g_.V;
@@ -425,32 +431,7 @@ class Engine {
       const int na = (int)staged_.size();
       n_ru += na;  // admitted systems with a guess x0 != 0 take an FP64 residual now
       upload_staged();
-      using PU = typename VF::unit;
-      const int gv = grid_of((const void*)admit_clear<PU>, 256, na);
-      admit_clear<PU><<<dim3(gv, cap_), 256, 0, st_>>>(vunits_, static_cast<PU*>(ws_.p_lo), vunits_,
-                                                       MIXED ? ws_.x32 : nullptr, MIXED ? n_ : 0, S);
-      const int gn = grid_of((const void*)norm_b<NC>, kTile, na);
-      if constexpr (MIXED) {
-        // b = (D+m)^+ chi in the inner precision: r = p = b and |b|^2
-        demote_chi<NC, VF><<<dim3(grid_of((const void*)demote_chi<NC, VF>, 256, na), cap_), 256, 0, st_>>>(
-            gb_, chi_, ft_, n_, vunits_, S);
-        rhs_lo<TF, OpF, VR, GK><<<dim3(grid_of((const void*)rhs_lo<TF, OpF, VR, GK>, kTile, na), cap_), kTile, 0,
-                                  st_>>>(gk_, opf_, ft_, fp_, fr_, bp_, S, rb_);
-        norm_b<NC><<<dim3(gn, cap_), kTile, 0, st_>>>(g_.V, nullptr, x_, n_, S, rb_);
-        admit_vectors<NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, nullptr, n_, S);
-        note_launches(1);
-      } else {
-        FpSample* fs = fp_sample(1, st_);
-        if (prof()) prof_count(cls_rhs(), 1);
-        apply_kernel<double, OpD><<<dim3(grid_of((const void*)apply_kernel<double, OpD>, kTile, na), cap_), kTile,
-                                    0, st_>>>(g_, opd_, V64{chi_}, V64{ws_.b64}, 0.0, n_, r_, 1, S, ST_ADMIT,
-                                              fs ? fs->cnt : nullptr);
-        if (fs) cudaEventRecord(fs->e1, st_);
-        norm_b<NC><<<dim3(gn, cap_), kTile, 0, st_>>>(g_.V, ws_.b64, x_, n_, S, rb_);
-        admit_vectors<NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, ws_.b64, n_, S);
-      }
-      admit_states<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S, MIXED ? 1 : 0);
-      note_launches(5);
+      admit(na);
       ru = true;
     }
     // After reliable updates with nothing known to be running, read the
@@ -462,7 +443,7 @@ class Engine {
     const bool overlap = ru && run && side_ != nullptr;
     if (ru) {
       mark_ru<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S);
-      note_launches(1);
+      launches(1);
       if (overlap) {
         cudaEventRecord(ev_fork_, st_);
         cudaStreamWaitEvent(side_, ev_fork_, 0);
@@ -502,6 +483,13 @@ class Engine {
     const cudaError_t e = ev_ ? cudaEventSynchronize(ev_) : cudaStreamSynchronize(st_);
     if (e != cudaSuccess) return cuda_fail(e);
     if (const cudaError_t l = cudaGetLastError(); l != cudaSuccess) return cuda_fail(l);
+    const int active = complete_scan();
+    ++rounds_;
+    return active;
+  }
+
+  // Scan the status words read back (the host copy hr_).
+  int complete_scan() {
     int active = 0, nrun = 0;
     need_ru_ = false;
     nneed_ = 0;
@@ -514,7 +502,6 @@ class Engine {
                  s == ST_ZERO_B || s == ST_ZERO_GUESS || s == ST_RU_PENDING || s == ST_READY);
     }
     nrun_ = nrun;
-    ++rounds_;
     return active;
   }
 
@@ -529,9 +516,149 @@ class Engine {
     }
   }
 
+  // Whether this engine may run a solve as one device-driven CUDA graph
+  // (it needs driver resources, and the kernel-timing samples need the
+  // host-driven rounds).
+  bool can_persist() const { return driver_resources_ && side_ != nullptr && !prof(); }
+
+  // Solve the staged systems with one launch of one CUDA graph: the
+  // admission kernels, then a conditional WHILE node whose body is one round
+  // -- the start of the reliable updates the statuses ask for (NEED_RU ->
+  // RU_PENDING), their FP64 kernels on a parallel branch beside a chunk of
+  // iterations of the running systems, then round_end, which keeps the loop
+  // going while any system is in flight (at most max_rounds rounds, else a
+  // timeout) -- and the copy of the status words to the host.  The host
+  // launches once and waits once.  The rounds are those of the host-driven
+  // loop, and a system's arithmetic does not depend on when its update runs
+  // beside the other systems' iterations, so the results are the same bit for
+  // bit.  Grids are sized for every slot: as systems finish, their blocks
+  // return at once.  Returns the number of slots still in flight (0), or a
+  // negative SW_ERR_* code; SW_ERR_CUDA before anything was launched means the
+  // graph could not be built (the caller then runs host-driven rounds).
+  int solve_persistent(int max_rounds, bool* launched) {
+    *launched = false;
+    if (staged_.empty()) return 0;
+    const int na = (int)staged_.size();
+    upload_staged();
+    set_grids(ngrp_);
+    SysState* S = ws_.S;
+    cudaMemsetAsync(ws_.ctl, 0, sizeof(int) * 8, st_);
+    cudaStream_t body_st = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&body_st, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    int per_round = 0;
+    if (ok) {
+      capturing_ = true;
+      admit(na);
+      cudaStreamCaptureStatus cs;
+      cudaGraph_t cg = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t ndeps = 0;
+      cudaGraphConditionalHandle loop = 0;
+      cudaGraphNode_t wnode = nullptr;
+      cudaGraphNodeParams cp{};
+      ok = cudaStreamGetCaptureInfo(st_, &cs, nullptr, &cg, &deps, nullptr, &ndeps) == cudaSuccess &&
+           cs == cudaStreamCaptureStatusActive &&
+           cudaGraphConditionalHandleCreate(&loop, cg, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+      if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = loop;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&wnode, cg, deps, nullptr, ndeps, &cp) == cudaSuccess;
+      }
+      if (ok) {  // the loop body: one round
+        ok = cudaStreamBeginCaptureToGraph(body_st, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+          ist_ = body_st;
+          mark_ru<<<(cap_ + 127) / 128, 128, 0, body_st>>>(cap_, S);
+          cudaEventRecord(ev_fork_, body_st);
+          cudaStreamWaitEvent(side_, ev_fork_, 0);
+          reliable_update(cap_, side_);
+          cudaEventRecord(ev_join_, side_);
+          for (int i = 0; i < chunk_; ++i) iterate(false, false);
+          cudaStreamWaitEvent(body_st, ev_join_, 0);
+          round_end<<<1, 256, 0, body_st>>>(cap_, S, ws_.ctl, max_rounds, loop);
+          ist_ = st_;
+          cudaGraph_t body = nullptr;
+          ok = cudaStreamEndCapture(body_st, &body) == cudaSuccess;
+          per_round = 2 + (MIXED ? 7 : 5) + 4 * chunk_;
+        }
+      }
+      ok = ok && cudaStreamUpdateCaptureDependencies(st_, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                     cudaSuccess;
+      move_states(hr_, S, hrd_, cap_, cudaMemcpyDeviceToHost);
+      cudaGraph_t done = nullptr;
+      ok = (cudaStreamEndCapture(st_, &done) == cudaSuccess) && ok && done;
+      graph = done;
+      ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    }
+    capturing_ = false;
+    if (graph) cudaGraphDestroy(graph);
+    if (body_st) cudaStreamDestroy(body_st);
+    ist_ = st_;
+    if (!ok) {
+      if (exec) cudaGraphExecDestroy(exec);
+      cudaGetLastError();
+      // nothing of the solve ran: restage for the host-driven rounds
+      for (int i = 0; i < cap_; ++i)
+        if (hr_[i].status == ST_ADMIT) staged_.push_back(i);
+      return SW_ERR_CUDA;
+    }
+    const cudaError_t le = cudaGraphLaunch(exec, st_);
+    *launched = le == cudaSuccess;
+    const cudaError_t se = cudaStreamSynchronize(st_);
+    cudaGraphExecDestroy(exec);
+    if (le != cudaSuccess) return cuda_fail(le);
+    if (se != cudaSuccess) return cuda_fail(se);
+    int ctl[2] = {0, 0};
+    if (const cudaError_t e = cudaMemcpy(ctl, ws_.ctl, sizeof(ctl), cudaMemcpyDeviceToHost); e != cudaSuccess)
+      return cuda_fail(e);
+    note_launches(6 + ctl[0] * per_round + 1);
+    rounds_ += ctl[0];
+    if (ctl[1]) return SW_ERR_TIMEOUT;
+    const int active = complete_scan();
+    return active;
+  }
+
   long long rounds() const { return rounds_; }
 
  private:
+  // Admission launches for the na slots staged (their status words already on
+  // the device): see the class comment.
+  void admit(int na) {
+    SysState* S = ws_.S;
+    using PU = typename VF::unit;
+    const int gv = grid_of((const void*)admit_clear<PU>, 256, na);
+    admit_clear<PU><<<dim3(gv, cap_), 256, 0, st_>>>(vunits_, static_cast<PU*>(ws_.p_lo), vunits_,
+                                                     MIXED ? ws_.x32 : nullptr, MIXED ? n_ : 0, S);
+    const int gn = grid_of((const void*)norm_b<NC>, kTile, na);
+    if constexpr (MIXED) {
+      // b = (D+m)^+ chi in the inner precision: r = p = b and |b|^2
+      demote_chi<NC, VF><<<dim3(grid_of((const void*)demote_chi<NC, VF>, 256, na), cap_), 256, 0, st_>>>(
+          gb_, chi_, ft_, n_, vunits_, S);
+      rhs_lo<TF, OpF, VR, GK><<<dim3(grid_of((const void*)rhs_lo<TF, OpF, VR, GK>, kTile, na), cap_), kTile, 0,
+                                st_>>>(gk_, opf_, ft_, fp_, fr_, bp_, S, rb_);
+      norm_b<NC><<<dim3(gn, cap_), kTile, 0, st_>>>(g_.V, nullptr, x_, n_, S, rb_);
+      admit_vectors<NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, nullptr, n_, S);
+      launches(1);
+    } else {
+      FpSample* fs = fp_sample(1, st_);
+      if (prof()) prof_count(cls_rhs(), 1);
+      apply_kernel<double, OpD><<<dim3(grid_of((const void*)apply_kernel<double, OpD>, kTile, na), cap_), kTile,
+                                  0, st_>>>(g_, opd_, V64{chi_}, V64{ws_.b64}, 0.0, n_, r_, 1, S, ST_ADMIT,
+                                            fs ? fs->cnt : nullptr);
+      if (fs) cudaEventRecord(fs->e1, st_);
+      norm_b<NC><<<dim3(gn, cap_), kTile, 0, st_>>>(g_.V, ws_.b64, x_, n_, S, rb_);
+      admit_vectors<NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, ws_.b64, n_, S);
+    }
+    admit_states<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S, MIXED ? 1 : 0);
+    launches(5);
+  }
+
   // Device address of a host status buffer that is pinned and mapped, else
   // nullptr (ordinary host memory, e.g. the allocation-free entry's).
   static SysState* mapped_alias(SysState* h) {
@@ -556,7 +683,7 @@ class Engine {
       const int blocks = (int)std::min<size_t>((words + 255) / 256, (size_t)sm_count());
       copy_words<<<blocks, 256, 0, st_>>>(reinterpret_cast<const unsigned long long*>(from),
                                           reinterpret_cast<unsigned long long*>(to), words);
-      note_launches(1);
+      launches(1);
     } else {
       cudaMemcpyAsync(dst, src, sizeof(SysState) * n, kind, st_);
     }
@@ -581,8 +708,8 @@ class Engine {
     SysState* S = ws_.S;
     const int gv = grid_of((const void*)cg_k3<TF, VR, VF, NC>, 256, nsys);
     // the last x += alpha p of each system (k2 stopped it before k3)
-    cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, sx>>>(g_.V, fr_, fp_, fx_, n_, vunits_, S, ST_RU_PENDING, 1);
-    if constexpr (MIXED) accum_x<NC><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, x_, ws_.x32, n_, n_, S);
+    cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, sx>>>(g_.V, fr_, fp_, fx_, runits_, vunits_, S, ST_RU_PENDING, 1);
+    if constexpr (MIXED) accum_x<NC, VR><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, x_, fx_, n_, runits_, S);
     FpSample* fs = fp_sample(2, sx);
     if (prof()) prof_count(cls_ru(), 1);
     // r = (D+m)^+ (chi - (D+m) x) = b - A x, all in FP64
@@ -592,10 +719,10 @@ class Engine {
     residual64<OpD><<<dim3(grid_of((const void*)residual64<OpD>, kTile, nsys), cap_), kTile, 0, sx>>>(
         g_, opd_, V64{ws_.t64}, V64{ws_.r64}, bp_, S, rbu_);
     if (fs) cudaEventRecord(fs->e1, sx);
-    if constexpr (MIXED) demote_r<NC><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, ws_.r64, ws_.r32, n_, n_, S);
-    cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, sx>>>(g_.V, fr_, fp_, fx_, n_, vunits_, S, ST_JUST_UPDATED, 2);
+    if constexpr (MIXED) demote_r<NC, VR><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, ws_.r64, fr_, n_, runits_, S);
+    cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, sx>>>(g_.V, fr_, fp_, fx_, runits_, vunits_, S, ST_JUST_UPDATED, 2);
     mark_ready<<<(cap_ + 127) / 128, 128, 0, sx>>>(cap_, S);
-    note_launches(MIXED ? 7 : 5);
+    launches(MIXED ? 7 : 5);
   }
 
   // One graph per grid class (see size_for_live), captured on first use.
@@ -622,7 +749,7 @@ class Engine {
     }
     if (ge) {
       cudaGraphLaunch(ge, st_);
-      note_launches(4 * chunk_);
+      launches(4 * chunk_);
       if (prof()) {
         prof_count(cls_k1(), chunk_);
         prof_count(cls_k2(), chunk_);
@@ -700,10 +827,10 @@ class Engine {
   template <int NS> void launch_k12(int* c) {
     SysState* S = ws_.S;
     const dim3 grid1 = gfast_ ? dim3(ngrp_, g1_) : dim3(g1_, ngrp_), grid2 = gfast_ ? dim3(ngrp_, g2_) : dim3(g2_, ngrp_);
-    cg_k1<TF, OpF, NS, GK><<<grid1, kTile, 0, st_>>>(gk_, opf_, fp_, ft_, bp_, cap_, S, rb_, c, gfast_);
-    if (c) cudaEventRecord(samples_.back().e1, st_);
-    cg_k2<TF, OpF, NS, VR, GK><<<grid2, kTile, 0, st_>>>(gk_, opf_, ft_, fr_, bp_, cap_, S, rb_,
-                                                         c ? c + 1 : nullptr, gfast_);
+    cg_k1<TF, OpF, NS, GK><<<grid1, kTile, 0, ist_>>>(gk_, opf_, fp_, ft_, bp_, cap_, S, rb_, c, gfast_);
+    if (c) cudaEventRecord(samples_.back().e1, ist_);
+    cg_k2<TF, OpF, NS, VR, GK><<<grid2, kTile, 0, ist_>>>(gk_, opf_, ft_, fr_, bp_, cap_, S, rb_,
+                                                          c ? c + 1 : nullptr, gfast_);
   }
 
   // One CG iteration (k1, k2, k3).  A sampled iteration is bracketed by
@@ -717,9 +844,9 @@ class Engine {
     if (sample) {
       samples_.push_back(Sample{prof_event(), prof_event(), prof_event(), prof_event()});
       c = ws_.pcount + 3 * (samples_.size() - 1);
-      cudaEventRecord(samples_.back().e0, st_);
+      cudaEventRecord(samples_.back().e0, ist_);
     }
-    commit_ready<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S);
+    commit_ready<<<(cap_ + 127) / 128, 128, 0, ist_>>>(cap_, S);
     if constexpr (MIXED) {
       if (ns_ == 2) launch_k12<2>(c);
       else if (ns_ == 4) launch_k12<4>(c);
@@ -727,12 +854,12 @@ class Engine {
     } else {
       launch_k12<1>(c);
     }
-    if (sample) cudaEventRecord(samples_.back().e2, st_);
-    cg_k3<TF, VR, VF, NC><<<dim3(gV_, cap_), 256, 0, st_>>>(g_.V, fr_, fp_, fx_, n_, vunits_, S, ST_RUNNING, 3,
-                                                            c ? c + 2 : nullptr);
-    if (sample) cudaEventRecord(samples_.back().e3, st_);
+    if (sample) cudaEventRecord(samples_.back().e2, ist_);
+    cg_k3<TF, VR, VF, NC><<<dim3(gV_, cap_), 256, 0, ist_>>>(g_.V, fr_, fp_, fx_, runits_, vunits_, S, ST_RUNNING, 3,
+                                                             c ? c + 2 : nullptr);
+    if (sample) cudaEventRecord(samples_.back().e3, ist_);
     if (count) {
-      note_launches(4);
+      launches(4);
       if (prof()) {
         prof_count(cls_k1(), 1);
         prof_count(cls_k2(), 1);
@@ -759,6 +886,7 @@ class Engine {
   SysState* hrd_ = nullptr;   // device alias of hr_ when mapped
   SysState* hstd_ = nullptr;  // device alias of hst_ when mapped
   cudaStream_t st_;
+  cudaStream_t ist_;  // stream the iteration kernels go to (st_, or the loop body's capture stream)
   cudaEvent_t ev_;
   size_t n_;
   int ntiles_ = 0, pstride_ = 0, ngrp_ = 0, gV_ = 0, g1_ = 0, g2_ = 0;
@@ -768,7 +896,7 @@ class Engine {
   BatchParams bp_{};
   VF fp_{}, ft_{};
   VR fr_{}, fx_{};
-  size_t vunits_ = 0;
+  size_t vunits_ = 0, runits_ = 0;  // storage units of one system's p (t) and r (x)
   int chunk_ = 16;
   double delta_ = 0.1;
   bool need_ru_ = false;
@@ -785,6 +913,10 @@ class Engine {
   bool use_graphs_ = true, graph_failed_ = false;
   bool driver_resources_ = true;  // false: allocation-free caller (no side stream, graphs or timing events)
   bool prof() const { return driver_resources_ && prof_enabled(); }
+  bool capturing_ = false;  // building the device-driven solve's graph: its launches are counted when it runs
+  void launches(int k) const {
+    if (!capturing_) note_launches(k);
+  }
   int cls_ = 0;  // groups the iteration grids are sized for
   std::vector<std::pair<int, cudaGraphExec_t>> gexecs_;
   std::vector<int> staged_;
@@ -826,7 +958,20 @@ int run_cgne_ws(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& 
   for (int i = 0; i < a.nsys; ++i) e.stage(i, a.masses[i], a.tol, a.max_iter);
   const long long max_rounds = 4LL * (a.max_iter / param_chunk() + 2) + 1000;
   int rc = SW_OK;
-  for (;;) {
+  bool host_rounds = true;
+  if (param_persistent() && e.can_persist()) {
+    bool launched = false;
+    const int p = e.solve_persistent((int)std::min<long long>(max_rounds, 1 << 30), &launched);
+    if (p == SW_ERR_TIMEOUT) {
+      rc = SW_ERR_TIMEOUT;
+      host_rounds = false;
+    } else if (p < 0 && launched) {
+      return p;
+    } else if (p >= 0) {
+      host_rounds = p > 0;  // (0: every system finished on the device)
+    }
+  }
+  for (; host_rounds;) {
     e.issue();
     const int active = e.complete();
     if (active < 0) return active;
@@ -902,7 +1047,7 @@ int run_inner_apply(const Geom& g, const OpF& opf, const double2* in, double2* o
                     double r, int dagger, cudaStream_t st) {
   constexpr int NC = OpF::NC;
   using VF = typename OpF::Vec;
-  using VR = VecP32<NC>;
+  using VR = typename RVecOf<VF, NC>::type;
   using PU = typename VF::unit;
   const GeomBlk gb = make_blocked(g, g.shape);
   const size_t vunits = VF::sys_units(g.V), n = (size_t)g.V * NC;
@@ -920,7 +1065,8 @@ int run_inner_apply(const Geom& g, const OpF& opf, const double2* in, double2* o
   };
   const VF fp{static_cast<PU*>(take(sizeof(PU) * vunits * nsys)), g.V};
   const VF ft{static_cast<PU*>(take(sizeof(PU) * vunits * nsys)), g.V};
-  const VR fr{static_cast<float2*>(take(sizeof(float2) * n * nsys)), g.V};
+  const VR fr{static_cast<typename VR::unit*>(take(sizeof(float2) * n * nsys)), g.V};
+  const size_t runits = VR::sys_units(g.V);
   SysState* S = static_cast<SysState*>(take(sizeof(SysState) * nsys));
   double* partials = static_cast<double*>(take(sizeof(double) * pstride * nsys));
   unsigned* tickets = static_cast<unsigned*>(take(sizeof(unsigned) * nsys));
@@ -940,7 +1086,7 @@ int run_inner_apply(const Geom& g, const OpF& opf, const double2* in, double2* o
   demote_chi<NC, VF><<<dim3(gv, nsys), 256, 0, st>>>(gb, in, dagger ? ft : fp, n, vunits, S);
   set_status<<<(nsys + 127) / 128, 128, 0, st>>>(nsys, S, ST_RUNNING);
   const RedBuf rb{partials, tickets, pstride, nullptr};
-  const BatchParams bp{r, n, n, vunits};
+  const BatchParams bp{r, runits, n, vunits};
   const int ns = param_ns(NC);
   auto launch = [&](auto nsc) {
     constexpr int NS = decltype(nsc)::value;
@@ -958,7 +1104,7 @@ int run_inner_apply(const Geom& g, const OpF& opf, const double2* in, double2* o
   else if (ns == 4) launch(std::integral_constant<int, 4>{});
   else launch(std::integral_constant<int, 1>{});
   if (!dagger) promote_vec<NC, VF><<<dim3(gv, nsys), 256, 0, st>>>(gb, ft, vunits, out, n);
-  else promote_vec<NC, VR><<<dim3(gv, nsys), 256, 0, st>>>(gb, fr, n, out, n);
+  else promote_vec<NC, VR><<<dim3(gv, nsys), 256, 0, st>>>(gb, fr, runits, out, n);
   note_launches(5);
   if (const cudaError_t e = cudaStreamSynchronize(st); e != cudaSuccess) return cuda_fail(e);
   if (const cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(e);

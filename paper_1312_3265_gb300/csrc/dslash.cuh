@@ -251,6 +251,34 @@ __device__ __forceinline__ Sp<T> wilson_site(const Geom& g, int n, const G& U, c
   return o;
 }
 
+// ------------------------------------------------------------------ two-lane colour products (FP32)
+// u = M h for two colour vectors at once, held in the two lanes of float2
+// registers (real parts in one array, imaginary parts in the other): one
+// two-lane FMA does the work of two scalar ones, with the matrix entries
+// broadcast to both lanes.
+// u = M h (DAG = false) or M^+ h (DAG = true)
+template <bool DAG>
+__device__ __forceinline__ void mv_pair(const M3<float>& M, const float2 hre[3], const float2 him[3], float2 ure[3],
+                                        float2 uim[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const cx<float> m0 = DAG ? M.e[0][i] : M.e[i][0];
+    const float s = DAG ? -1.f : 1.f;  // conj: the imaginary parts change sign
+    ure[i] = fmul2(bc2(m0.re), hre[0]);
+    ure[i] = ffma2(bc2(-s * m0.im), him[0], ure[i]);
+    uim[i] = fmul2(bc2(m0.re), him[0]);
+    uim[i] = ffma2(bc2(s * m0.im), hre[0], uim[i]);
+#pragma unroll
+    for (int j = 1; j < 3; ++j) {
+      const cx<float> m = DAG ? M.e[j][i] : M.e[i][j];
+      ure[i] = ffma2(bc2(m.re), hre[j], ure[i]);
+      ure[i] = ffma2(bc2(-s * m.im), him[j], ure[i]);
+      uim[i] = ffma2(bc2(m.re), him[j], uim[i]);
+      uim[i] = ffma2(bc2(s * m.im), hre[j], uim[i]);
+    }
+  }
+}
+
 }  // namespace swc
 
 // ------------------------------------------------------------------ multi-system forms
@@ -325,6 +353,143 @@ __device__ __forceinline__ void sw_site_multi(const GG& g, int n, const G& U, co
       axpy3(acc[s], r + mass[s], self);
       out[s] = acc[s];
     }
+}
+
+// The same operator for NS (even) FP32 systems with the systems of each pair
+// in the two lanes of float2 registers: one two-lane FMA does the work of two
+// scalar ones, with the link and transport entries broadcast to both lanes.
+// The 16 hypercube corners accumulate unscaled (their coefficients
+// eps eta5 r/16 are one value per site, up to the time-boundary sign), and
+// are scaled once per direction sign.  A lane whose system is not computed
+// reads its partner's vector (never memory outside the batch) and is dropped.
+template <int NS, typename G, typename Wt, typename In, typename GG>
+__device__ __forceinline__ void sw_site_multi_pair(const GG& g, int n, const G& U, const Wt& W, const In& in,
+                                                   size_t stride, unsigned act, const float* mass, float r,
+                                                   bool dagger, V3<float>* out) {
+  static_assert(NS % 2 == 0, "pairs of systems");
+  constexpr int NP = NS / 2;
+  int x[4], df[4], db[4];
+  coords(g, n, x);
+  hop_deltas(g, n, x, df, db);
+  In lane0[NP], lane1[NP];
+  bool on[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const unsigned a = (act >> (2 * q)) & 3u;
+    on[q] = a != 0;
+    lane0[q] = sys_at(in, (a & 1u) ? 2 * q : 2 * q + 1, stride);
+    lane1[q] = sys_at(in, (a & 2u) ? 2 * q + 1 : 2 * q, stride);
+  }
+  float2 are[NP][3], aim[NP][3];
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) are[q][i] = aim[q][i] = make_float2(0.f, 0.f);
+  // packed vector of pair q at site y: lanes (first, second system)
+  auto ldp = [&](int q, int y, float2 vre[3], float2 vim[3]) {
+    const V3<float> a = ld3<In, float>(lane0[q], y), b = ld3<In, float>(lane1[q], y);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      vre[j] = make_float2(a.c[j].re, b.c[j].re);
+      vim[j] = make_float2(a.c[j].im, b.c[j].im);
+    }
+  };
+  const float half = dagger ? -0.5f : 0.5f;
+  int par = 0;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int nf = n + df[mu], nb = n + db[mu];
+    const float eta = (par & 1) ? -half : half;
+    float cf = eta, cb = -eta;
+    if (mu == 3) {
+      if (bc_flip(g, x, +1)) cf = -cf;
+      if (bc_flip(g, x, -1)) cb = -cb;
+    }
+    float2 vre[3], vim[3], ure[3], uim[3];
+    const M3<float> Uf = U.link(n, mu);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      if (!on[q]) continue;
+      ldp(q, nf, vre, vim);
+      mv_pair<false>(Uf, vre, vim, ure, uim);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        are[q][i] = ffma2(bc2(cf), ure[i], are[q][i]);
+        aim[q][i] = ffma2(bc2(cf), uim[i], aim[q][i]);
+      }
+    }
+    const M3<float> Ub = U.link(nb, mu);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      if (!on[q]) continue;
+      ldp(q, nb, vre, vim);
+      mv_pair<true>(Ub, vre, vim, ure, uim);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        are[q][i] = ffma2(bc2(cb), ure[i], are[q][i]);
+        aim[q][i] = ffma2(bc2(cb), uim[i], aim[q][i]);
+      }
+    }
+    par += x[mu];
+  }
+  const float hs = (eps_eta5_neg(x) ? r : -r) * 0.0625f;
+  const float hf = bc_flip(g, x, +1) ? -hs : hs, hb = bc_flip(g, x, -1) ? -hs : hs;
+  // the 8 corners x + s (s3 = +1) by the stored W(x, s), then the 8 corners
+  // x - s by W(x - s, s)^+
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    float2 hre[NP][3], him[NP][3];
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) hre[q][i] = him[q][i] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+      int of, ob;
+      corner_offsets(k, df, db, of, ob);
+      const int y = n + (side ? ob : of);
+      const M3<float> M = side ? W.mat(y, k) : W.mat(n, k);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        if (!on[q]) continue;
+        float2 vre[3], vim[3];
+        ldp(q, y, vre, vim);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const cx<float> m = side ? M.e[j][i] : M.e[i][j];
+            const float mi = side ? -m.im : m.im;  // W^+: conjugate transpose
+            hre[q][i] = ffma2(bc2(m.re), vre[j], hre[q][i]);
+            hre[q][i] = ffma2(bc2(-mi), vim[j], hre[q][i]);
+            him[q][i] = ffma2(bc2(m.re), vim[j], him[q][i]);
+            him[q][i] = ffma2(bc2(mi), vre[j], him[q][i]);
+          }
+      }
+    }
+    const float c = side ? hb : hf;
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        are[q][i] = ffma2(bc2(c), hre[q][i], are[q][i]);
+        aim[q][i] = ffma2(bc2(c), him[q][i], aim[q][i]);
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    if (!on[q]) continue;
+    float2 vre[3], vim[3];
+    ldp(q, n, vre, vim);
+    const float2 d = make_float2(r + mass[2 * q], r + mass[2 * q + 1]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      are[q][i] = ffma2(d, vre[i], are[q][i]);
+      aim[q][i] = ffma2(d, vim[i], aim[q][i]);
+      out[2 * q].c[i] = {are[q][i].x, aim[q][i].x};
+      out[2 * q + 1].c[i] = {are[q][i].y, aim[q][i].y};
+    }
+  }
 }
 
 template <typename T, bool R1, int NS, typename G, typename In, typename GG>

@@ -78,42 +78,47 @@ static __global__ void su3_deviation(int V, const double2* __restrict__ U, unsig
 }
 
 // x64 (canonical) += x32 (packed, blocked order); x32 = 0   -- systems with status RU_PENDING
-template <int NC>
-__global__ void accum_x(GeomBlk gb, double2* x64, float2* x32, size_t s64, size_t s32, const SysState* S) {
+// (x32: the FP32 correction in its storage RV; s32 in RV's units)
+template <int NC, typename RV>
+__global__ void accum_x(GeomBlk gb, double2* x64, RV x32, size_t s64, size_t s32, const SysState* S) {
   const int sys = blockIdx.y;
   if (S[sys].status != ST_RU_PENDING) return;
   const int V = gb.V;
   x64 += sys * s64;
-  x32 += sys * s32;
+  x32 = sys_view(x32, sys, s32);
+  CV<float, NC> zero;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) zero.c[c] = {0.f, 0.f};
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < V; n += gridDim.x * blockDim.x) {
     const int nb = lex_to_blk(gb, n);
+    const CV<float, NC> a = ld_site<float, NC>(x32, nb);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      const float2 a = x32[pk(nb, NC, c)];
       double2 b = x64[(size_t)n * NC + c];
-      b.x += (double)a.x;
-      b.y += (double)a.y;
+      b.x += (double)a.c[c].re;
+      b.y += (double)a.c[c].im;
       x64[(size_t)n * NC + c] = b;
-      x32[pk(nb, NC, c)] = make_float2(0.f, 0.f);
     }
+    st_site(x32, nb, zero);
   }
 }
 
-// r32 (packed, blocked order) = (float) r64 (canonical)   -- systems with status JUST_UPDATED
-template <int NC>
-__global__ void demote_r(GeomBlk gb, const double2* r64, float2* r32, size_t s64, size_t s32, const SysState* S) {
+// r32 (packed, blocked order, storage RV) = (float) r64 (canonical)   -- systems with status JUST_UPDATED
+template <int NC, typename RV>
+__global__ void demote_r(GeomBlk gb, const double2* r64, RV r32, size_t s64, size_t s32, const SysState* S) {
   const int sys = blockIdx.y;
   if (S[sys].status != ST_JUST_UPDATED) return;
   const int V = gb.V;
   r64 += sys * s64;
-  r32 += sys * s32;
+  r32 = sys_view(r32, sys, s32);
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < V; n += gridDim.x * blockDim.x) {
-    const int nb = lex_to_blk(gb, n);
+    CV<float, NC> v;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const double2 a = r64[(size_t)n * NC + c];
-      r32[pk(nb, NC, c)] = make_float2((float)a.x, (float)a.y);
+      v.c[c] = {(float)a.x, (float)a.y};
     }
+    st_site(r32, lex_to_blk(gb, n), v);
   }
 }
 
@@ -279,6 +284,30 @@ __global__ void promote_vec(GeomBlk gb, Vec in, size_t sin, double2* out, size_t
       const cx<float> v = in.ld(nb, c);
       out[(size_t)n * NC + c] = make_double2((double)v.re, (double)v.im);
     }
+  }
+}
+
+// End of a round of the device-driven solve: keep the loop of the solve's
+// CUDA graph going while any system is in flight and fewer than max_rounds
+// rounds have run; on the round cap, flag a timeout.  One block.
+// ctl[0]: rounds run, ctl[1]: timeout flag.
+static __global__ void round_end(int nsys, const SysState* S, int* ctl, int max_rounds,
+                                 cudaGraphConditionalHandle loop) {
+  __shared__ int busy;
+  if (threadIdx.x == 0) busy = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nsys; i += blockDim.x) {
+    const int s = S[i].status;
+    if (s == ST_RUNNING || s == ST_NEED_RU || s == ST_JUST_UPDATED || s == ST_ADMIT || s == ST_ZERO_B ||
+        s == ST_ZERO_GUESS || s == ST_RU_PENDING || s == ST_READY)
+      busy = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int r = ++ctl[0];
+    const bool cap = busy && r >= max_rounds;
+    if (cap) ctl[1] = 1;
+    cudaGraphSetConditional(loop, (busy && !cap) ? 1u : 0u);
   }
 }
 

@@ -12,10 +12,16 @@
 // reductions in a fixed order), so each result is bit-identical alone and in
 // any mix.
 //
-// Admission by memory: every engine's device memory (resident field, packed
-// copies, slot vectors, workspace) is charged against the server's budget when
-// the engine is added; a request waits in its engine's queue until a slot is
-// free.
+// Admission by memory.  Gauge fields are resident (sw_server_add_field), and a
+// request names a field, an operator, r and a precision: the scheduler finds
+// the engine of that combination or creates it when the device-memory budget
+// allows, first retiring engines it created that have gone idle (least
+// recently used first); while the memory is not there the request waits,
+// and requests behind it whose engines exist go ahead.  Every engine's device
+// memory (packed copies, slot vectors, workspace; the links too for engines
+// added with sw_server_add_engine, which are never retired) is charged
+// against the budget.  Inside an engine a request waits in the engine's queue
+// until a slot is free.
 #include <condition_variable>
 #include <deque>
 #include <memory>
@@ -137,11 +143,11 @@ static int build_engine(const Geom& g, int cap, double r, int prec, MakeOps make
 
 // Device bytes an engine will hold: resident field (+ transports), packed
 // FP32 copies, chi and x slots, workspace.
-static size_t engine_bytes(const Geom& g, int op, int prec, int cap) {
+static size_t engine_bytes(const Geom& g, int op, int prec, int cap, bool own_links = true) {
   const size_t V = g.V;
   const int nc = op == SW_OP_WILSON ? 12 : 3;
   const bool mixed = prec != SW_PREC_F64;
-  size_t b = V * 576 + (op == SW_OP_WILSON ? 0 : V * 1152);
+  size_t b = (own_links ? V * 576 : 0) + (op == SW_OP_WILSON ? 0 : V * 1152);
   if (prec == SW_PREC_F32_RELIABLE) b += V * 288 + (op == SW_OP_WILSON ? 0 : V * 576);
   if (prec == SW_PREC_F16_RELIABLE) b += V * 96 + (op == SW_OP_WILSON ? 0 : V * 288);
   const size_t ws = prec == SW_PREC_F16_RELIABLE
@@ -151,11 +157,17 @@ static size_t engine_bytes(const Geom& g, int op, int prec, int cap) {
   return b;
 }
 
+// own_links: the engine keeps its own copy of U (the caller's buffer may be
+// freed after the call); otherwise U is a resident field of the server, which
+// outlives the engine.
 static int make_engine(const Geom& g, int op, const double2* U, double r, int prec, int cap,
-                       std::unique_ptr<EngineBase>* out) {
+                       std::unique_ptr<EngineBase>* out, bool own_links = true) {
   const size_t V = g.V;
-  // resident copy of the links (the caller's buffer may be freed after the call)
   auto copy_links = [&](std::vector<DevMem*>& owned, cudaStream_t st, double2** Ur) -> int {
+    if (!own_links) {
+      *Ur = const_cast<double2*>(U);
+      return SW_OK;
+    }
     *Ur = (double2*)own(owned, V * 576, st);
     if (!*Ur) return SW_ERR_OOM;
     return cudaMemcpyAsync(*Ur, U, V * 576, cudaMemcpyDeviceToDevice, st) == cudaSuccess ? SW_OK : SW_ERR_CUDA;
@@ -249,7 +261,31 @@ static int make_engine(const Geom& g, int op, const double2* U, double r, int pr
 struct Server {
   int device = 0;
   size_t budget = 0, used = 0;
-  std::vector<std::unique_ptr<EngineBase>> engines;
+  size_t fixed = 0;  // bytes of the fields and of the engines added by hand (never released while serving)
+  // resident gauge fields (std::deque: references stay valid as fields are added)
+  struct Field {
+    Geom g;
+    DevMem* mem = nullptr;
+    int slots = 0;
+  };
+  std::deque<Field> fields;
+  // the (field, operator, r, precision) an engine was created for on demand (field < 0: added by hand)
+  struct Key {
+    int field = -1, op = 0, prec = 0;
+    double r = 1.0;
+    bool operator==(const Key& o) const { return field == o.field && op == o.op && prec == o.prec && r == o.r; }
+  };
+  std::vector<Key> keys;
+  std::vector<size_t> charged;  // bytes each engine holds against the budget
+  std::vector<long long> last_used;  // scheduler pass of the engine's last work (LRU retirement)
+  struct Waiting {
+    Request rq;
+    Key key;
+    bool counted = false;
+  };
+  std::deque<Waiting> waiting;  // requests whose engine does not exist yet
+  long long created = 0, retired = 0, waited = 0, pass = 0;
+  std::vector<std::unique_ptr<EngineBase>> engines;  // nullptr: retired
   std::vector<Geom> geoms;
   std::vector<std::deque<Request>> queues;
   std::vector<std::vector<Request>> slots;  // per engine, per slot: the request it holds (id < 0: free)
@@ -287,6 +323,89 @@ struct Server {
     cv_done.notify_all();
   }
 
+  // An engine created on demand that holds no request (queued, in a slot or
+  // in flight) may be retired.
+  bool idle(size_t k) {
+    if (!engines[k] || keys[k].field < 0 || in_flight[k] || has_work[k] || !queues[k].empty()) return false;
+    for (const Request& rq : slots[k])
+      if (rq.id >= 0) return false;
+    return true;
+  }
+
+  // Give requests without an engine one: an existing engine of their
+  // (field, operator, r, precision), else a new one if the budget allows after
+  // retiring idle engines created on demand (least recently used first).  A
+  // request whose engine cannot fit yet keeps waiting; the ones behind it go
+  // ahead if their engines exist.  Scheduler thread only.
+  bool admit_waiting() {
+    bool moved = false;
+    std::unique_lock<std::mutex> lk(mu);
+    for (auto it = waiting.begin(); it != waiting.end();) {
+      int k = -1;
+      for (size_t j = 0; j < engines.size(); ++j)
+        if (engines[j] && keys[j] == it->key) k = (int)j;
+      if (k < 0) {
+        const Field& f = fields[it->key.field];
+        const size_t need = engine_bytes(f.g, it->key.op, it->key.prec, f.slots, false);
+        while (used + need > budget) {  // retire the least recently used idle engine
+          int victim = -1;
+          for (size_t j = 0; j < engines.size(); ++j)
+            if (idle(j) && (victim < 0 || last_used[j] < last_used[victim])) victim = (int)j;
+          if (victim < 0) break;
+          cudaStreamSynchronize(engines[victim]->stream());
+          engines[victim].reset();  // its device memory goes back to the library's pool
+          used -= charged[victim];
+          charged[victim] = 0;
+          ++retired;
+        }
+        if (used + need > budget) {  // not yet: wait for memory
+          if (!it->counted) {
+            it->counted = true;
+            ++waited;
+          }
+          ++it;
+          continue;
+        }
+        std::unique_ptr<EngineBase> eng;
+        const Key key = it->key;
+        const Geom g = f.g;
+        const int slots_per = f.slots;
+        const double2* U = f.mem->as<double2>();
+        lk.unlock();  // engine set-up allocates and waits on the device: submitters need not wait for it
+        const int rc = make_engine(g, key.op, U, key.r, key.prec, slots_per, &eng, false);
+        lk.lock();
+        if (rc != SW_OK) {
+          if (error == SW_OK) error = rc;
+          cv_done.notify_all();
+          return moved;
+        }
+        used += need;
+        ++created;
+        k = (int)engines.size();
+        push_engine(std::move(eng), g, slots_per, key, need);
+      }
+      queues[k].push_back(it->rq);
+      it = waiting.erase(it);
+      moved = true;
+    }
+    return moved;
+  }
+
+  // Append an engine and its bookkeeping (caller holds mu, or serving has not started).
+  void push_engine(std::unique_ptr<EngineBase> eng, const Geom& g, int nslots, const Key& key, size_t bytes) {
+    engines.push_back(std::move(eng));
+    geoms.push_back(g);
+    queues.emplace_back();
+    Request freeslot{};
+    freeslot.id = -1;
+    slots.emplace_back(nslots, freeslot);
+    in_flight.push_back(0);
+    has_work.push_back(0);
+    keys.push_back(key);
+    charged.push_back(bytes);
+    last_used.push_back(pass);
+  }
+
   // Scheduler thread: see the file comment.
   void loop() {
     cudaSetDevice(device);
@@ -298,7 +417,11 @@ struct Server {
         std::unique_lock<std::mutex> lk(mu);
         if (stop) break;
       }
+      ++pass;
+      if (admit_waiting()) progressed = true;
+      if (error != SW_OK) return;
       for (size_t k = 0; k < engines.size(); ++k) {
+        if (!engines[k]) continue;  // retired
         EngineBase& e = *engines[k];
         if (in_flight[k]) {
           if (!e.ready()) continue;
@@ -352,6 +475,7 @@ struct Server {
           e.issue();
           in_flight[k] = 1;
           progressed = true;
+          last_used[k] = pass;
         }
       }
       // solutions whose copies have landed
@@ -421,15 +545,103 @@ int sw_server_add_engine(sw_server srv, const sw_lattice* lat, int op, const voi
   std::unique_ptr<EngineBase> eng;
   if (int e = make_engine(g, op, static_cast<const double2*>(U), r, precision, slots, &eng)) return e;
   s.used += need;
+  s.fixed += need;
   *engine = (int)s.engines.size();
-  s.engines.push_back(std::move(eng));
-  s.geoms.push_back(g);
-  s.queues.emplace_back();
-  Request freeslot{};
-  freeslot.id = -1;
-  s.slots.emplace_back(slots, freeslot);
-  s.in_flight.push_back(0);
-  s.has_work.push_back(0);
+  s.push_engine(std::move(eng), g, slots, Server::Key{}, need);
+  return SW_OK;
+}
+
+int sw_server_add_field(sw_server srv, const sw_lattice* lat, const void* U, int slots, int* field) {
+  if (!srv || !field) return SW_ERR_NULL;
+  Server& s = srv->s;
+  Geom g;
+  if (int e = make_geom(lat, &g)) return e;
+  if (slots < 1 || slots > 4096) return SW_ERR_ARG;
+  const size_t bytes = (size_t)g.V * 576;
+  if (int e = check_buf(U, bytes)) return e;
+  std::lock_guard<std::mutex> lk(s.mu);
+  if (s.error != SW_OK) return s.error;
+  if (s.fixed + bytes > s.budget) return SW_ERR_OOM;
+  // retire idle on-demand engines if the field does not fit beside them
+  while (s.used + bytes > s.budget) {
+    int victim = -1;
+    for (size_t j = 0; j < s.engines.size(); ++j)
+      if (s.idle(j) && (victim < 0 || s.last_used[j] < s.last_used[victim])) victim = (int)j;
+    if (victim < 0) return SW_ERR_OOM;
+    cudaStreamSynchronize(s.engines[victim]->stream());
+    s.engines[victim].reset();
+    s.used -= s.charged[victim];
+    s.charged[victim] = 0;
+    ++s.retired;
+  }
+  Server::Field f;
+  f.g = g;
+  f.slots = slots;
+  f.mem = new DevMem();
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete f.mem;
+    return SW_ERR_CUDA;
+  }
+  int rc = SW_OK;
+  if (!f.mem->alloc(bytes, st)) rc = SW_ERR_OOM;
+  else if (cudaMemcpyAsync(f.mem->p, U, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+           cudaStreamSynchronize(st) != cudaSuccess)
+    rc = SW_ERR_CUDA;
+  f.mem->s = nullptr;  // later frees are ordered on the legacy stream, after every engine has synchronised
+  cudaStreamDestroy(st);
+  if (rc != SW_OK) {
+    delete f.mem;
+    return rc;
+  }
+  s.used += bytes;
+  s.fixed += bytes;
+  *field = (int)s.fields.size();
+  s.fields.push_back(f);
+  return SW_OK;
+}
+
+int sw_server_submit_field(sw_server srv, int field, int op, double r, int precision, const void* chi_host,
+                           void* x_host, double mass, double tol, int max_iter, long long* request) {
+  if (!srv || !chi_host || !x_host || !request) return SW_ERR_NULL;
+  Server& s = srv->s;
+  if (op != SW_OP_STAGGERED_WILSON && op != SW_OP_WILSON) return SW_ERR_ARG;
+  if (precision != SW_PREC_F64 && precision != SW_PREC_F32_RELIABLE && precision != SW_PREC_F16_RELIABLE)
+    return SW_ERR_ARG;
+  if (!(tol > 0.0 && tol < 1.0) || max_iter < 1 || !(mass == mass) || !(r == r)) return SW_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s.mu);
+  if (s.error != SW_OK) return s.error;
+  if (field < 0 || field >= (int)s.fields.size()) return SW_ERR_ARG;
+  const Server::Field& f = s.fields[field];
+  // a request whose engine could never fit beside the fields and the fixed engines is refused now
+  if (s.fixed + engine_bytes(f.g, op, precision, f.slots, false) > s.budget) return SW_ERR_OOM;
+  if (!s.thread.joinable()) s.thread = std::thread([&s] { s.loop(); });
+  Server::Waiting w;
+  w.rq = Request{s.next_id++, chi_host, x_host, mass, tol, max_iter, std::chrono::steady_clock::now()};
+  w.key.field = field;
+  w.key.op = op;
+  w.key.prec = precision;
+  w.key.r = r;
+  s.waiting.push_back(w);
+  ++s.outstanding;
+  *request = w.rq.id;
+  s.cv_work.notify_one();
+  return SW_OK;
+}
+
+int sw_server_stats(sw_server srv, sw_server_stats_t* out) {
+  if (!srv || !out) return SW_ERR_NULL;
+  Server& s = srv->s;
+  std::lock_guard<std::mutex> lk(s.mu);
+  int live = 0;
+  for (auto& e : s.engines) live += e != nullptr;
+  out->engines_live = live;
+  out->engines_created = (int)s.created;
+  out->engines_retired = (int)s.retired;
+  out->requests_waited_for_memory = s.waited;
+  out->requests_waiting = (long long)s.waiting.size();
+  out->bytes_charged = s.used;
+  out->budget = s.budget;
   return SW_OK;
 }
 
@@ -437,9 +649,9 @@ int sw_server_submit(sw_server srv, int engine, const void* chi_host, void* x_ho
                      int max_iter, long long* request) {
   if (!srv || !chi_host || !x_host || !request) return SW_ERR_NULL;
   Server& s = srv->s;
-  if (engine < 0 || engine >= (int)s.engines.size()) return SW_ERR_ARG;
   if (!(tol > 0.0 && tol < 1.0) || max_iter < 1 || !(mass == mass)) return SW_ERR_ARG;
   std::lock_guard<std::mutex> lk(s.mu);
+  if (engine < 0 || engine >= (int)s.engines.size() || s.keys[engine].field >= 0) return SW_ERR_ARG;
   if (s.error != SW_OK) return s.error;
   if (!s.thread.joinable()) s.thread = std::thread([&s] { s.loop(); });
   Request rq{s.next_id++, chi_host, x_host, mass, tol, max_iter, std::chrono::steady_clock::now()};
@@ -484,10 +696,12 @@ int sw_server_destroy(sw_server srv) {
     s.cv_work.notify_all();
   }
   if (s.thread.joinable()) s.thread.join();
-  for (auto& e : s.engines) cudaStreamSynchronize(e->stream());
+  for (auto& e : s.engines)
+    if (e) cudaStreamSynchronize(e->stream());
   for (auto& c : s.copies) cudaEventDestroy(c.ev);
   for (cudaEvent_t e : s.event_pool) cudaEventDestroy(e);
   s.engines.clear();
+  for (auto& f : s.fields) delete f.mem;
   delete srv;
   return SW_OK;
 }

@@ -122,3 +122,12 @@ def test_autotune_single_operator_and_fp64():
     lib = FakeLib({})
     assert "skipped" in bench.autotune_layout(lib, (4, 4, 4, 4), None, None, lib.SW_PREC_F64, 12, 48, None)
     assert lib.params == {}
+
+
+def test_both_arms_name_the_same_config():
+    """The reference arm and ours describe the workload with the same config
+    object (the driver compares them); tuning details go elsewhere."""
+    a = bench.workload_config(bench.WORKLOAD, bench.DIMS, bench.MASSES)
+    b = bench.workload_config(bench.WORKLOAD, bench.DIMS, bench.MASSES)
+    assert a == b and set(a) == {"workload", "lattice", "masses", "tol", "l2"}
+    assert a["lattice"] == "16x16x16x32" and a["tol"] == 1e-8

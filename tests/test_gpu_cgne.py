@@ -516,3 +516,34 @@ def test_bench_batch_at_full_size(sw):
                     assert np.abs(got[n] - want).max() <= 1e-12 * scale, (op, k, n)
         del chi, x
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("op,prec", [(1, 1), (0, 1), (1, 2), (0, 0)])
+def test_persistent_graph_is_bitwise_host_rounds(sw, op, prec):
+    """The whole solve as one CUDA graph (admission, a conditional WHILE node
+    over rounds of reliable updates beside chunks of iterations, the status
+    read) gives bit for bit the solutions and iteration counts of the
+    host-driven rounds, and issues fewer host-visible launches; three masses,
+    so the systems take their reliable updates in different rounds."""
+    import torch
+    P = Problem(sw, (6, 4, 4, 6), op, 14, ls.PLAQ_EPS, 0.05, apbc=True)
+    masses = [0.05, 0.1, 0.2]
+    chis = np.stack([ls.gaussian_source(P.dims, P.nc, 110 + i).reshape((-1,) + P.internal) for i in range(3)])
+    chi = dev(chis)
+    out, iters = {}, {}
+    old = sw.sw_get_param(sw.SW_PARAM_PERSISTENT)
+    try:
+        for pflag in (0, 1):
+            sw.sw_set_param(sw.SW_PARAM_PERSISTENT, pflag)
+            x = torch.zeros_like(chi)
+            rc, infos = sw.cgne_solve_batch(P.dims, P.op, P.U, P.W, chi, x, masses, 1.0, 1e-10, 10000, prec, True)
+            assert rc == sw.SW_OK and all(i.true_rel_resid <= 1e-10 for i in infos)
+            out[pflag] = x.cpu().numpy()
+            iters[pflag] = [(i.iters, i.reliable_updates) for i in infos]
+    finally:
+        sw.sw_set_param(sw.SW_PARAM_PERSISTENT, old)
+    assert iters[0] == iters[1]
+    assert np.array_equal(out[0], out[1])
+    for i, m in enumerate(masses):
+        P.mass = m
+        assert P.true_resid(chis[i].reshape(-1), out[1][i].reshape(-1)) <= 1.01e-10

@@ -1,7 +1,11 @@
 """GPU parity of the FP64 operator kernels against the oracle, through the C ABI.
 
 Tolerance: 1e-12 relative (max-norm of the difference over max-norm of the
-oracle result) for FP64 matvecs; hypercube transports 1e-13.
+oracle result) for FP64 matvecs; hypercube transports 1e-13.  On lattices too
+large for the whole-field oracle the same measure is taken over sampled
+sites: the largest difference at the samples over the largest oracle value at
+the samples (the rounding error of a site scales with its inputs, not with
+its own output, which can be small).
 """
 import numpy as np
 import pytest
@@ -38,6 +42,20 @@ def rand_vec(V, nc, seed):
 
 def relerr(got, want):
     return np.abs(got - want).max() / np.abs(want).max()
+
+
+class Sampled:
+    """Max-norm relative error over sampled sites (see the module docstring)."""
+
+    def __init__(self):
+        self.diff, self.scale = 0.0, 0.0
+
+    def add(self, got, want):
+        self.diff = max(self.diff, float(np.abs(got - want).max()))
+        self.scale = max(self.scale, float(np.abs(want).max()))
+
+    def rel(self):
+        return self.diff / self.scale
 
 
 def make_fields(sw, dims, seed=3, eps=0.5):
@@ -113,12 +131,12 @@ def test_full_size_sampled_sites(sw):
     a, b = o1.cpu().numpy(), o2.cpu().numpy()
     rng = np.random.default_rng(0)
     sites = np.concatenate([[0, V - 1, 16 * 16 * 16 * 31, 15], rng.integers(0, V, 28)])
+    es, ew = Sampled(), Sampled()
     for n in sites:
         n = int(n)
-        want = site.sw_dslash_site(Uh, psi_h, dims, n, 0.02, 1.0, True, True)
-        assert np.abs(a[n] - want).max() < TOL * np.abs(want).max() * 10
-        want = site.wilson_dslash_site(Uh, spn_h, dims, n, 0.02, 1.0, False, True)
-        assert np.abs(b[n] - want).max() < TOL * np.abs(want).max() * 10
+        es.add(a[n], site.sw_dslash_site(Uh, psi_h, dims, n, 0.02, 1.0, True, True))
+        ew.add(b[n], site.wilson_dslash_site(Uh, spn_h, dims, n, 0.02, 1.0, False, True))
+    assert es.rel() < TOL and ew.rel() < TOL, (es.rel(), ew.rel())
 
 
 def test_abi_rejects_bad_arguments(sw):
@@ -167,12 +185,12 @@ def test_large_lattice_sampled_sites(sw):
     torch.cuda.synchronize()
     a, b = o1.cpu().numpy(), o2.cpu().numpy()
     rng = np.random.default_rng(1)
+    es, ew = Sampled(), Sampled()
     for n in np.concatenate([[0, V - 1], rng.integers(0, V, 14)]):
         n = int(n)
-        want = site.sw_dslash_site(Uh, psi_h, dims, n, 0.05, 1.0, False, False)
-        assert np.abs(a[n] - want).max() < TOL * np.abs(want).max() * 10
-        want = site.wilson_dslash_site(Uh, spn_h, dims, n, 0.05, 1.0, True, False)
-        assert np.abs(b[n] - want).max() < TOL * np.abs(want).max() * 10
+        es.add(a[n], site.sw_dslash_site(Uh, psi_h, dims, n, 0.05, 1.0, False, False))
+        ew.add(b[n], site.wilson_dslash_site(Uh, spn_h, dims, n, 0.05, 1.0, True, False))
+    assert es.rel() < TOL and ew.rel() < TOL, (es.rel(), ew.rel())
 
 
 def test_largest_lattices_sampled_sites(sw):
@@ -199,9 +217,10 @@ def test_largest_lattices_sampled_sites(sw):
             torch.cuda.synchronize()
             got = out.cpu().numpy()
             del W, out
+            e = Sampled()
             for n in sites:
-                want = site.sw_dslash_site(Uh, psi_h, dims, int(n), 0.01, 1.0, False, False)
-                assert np.abs(got[int(n)] - want).max() < TOL * np.abs(want).max() * 10
+                e.add(got[int(n)], site.sw_dslash_site(Uh, psi_h, dims, int(n), 0.01, 1.0, False, False))
+            assert e.rel() < TOL, (op, e.rel())
         else:
             spn_h = rand_vec(V, 12, 28).reshape(V, 4, 3)
             spn = dev(spn_h)
@@ -210,8 +229,9 @@ def test_largest_lattices_sampled_sites(sw):
             torch.cuda.synchronize()
             got = out.cpu().numpy()
             del out
+            e = Sampled()
             for n in sites:
-                want = site.wilson_dslash_site(Uh, spn_h, dims, int(n), 0.01, 1.0, True, True)
-                assert np.abs(got[int(n)] - want).max() < TOL * np.abs(want).max() * 10
+                e.add(got[int(n)], site.wilson_dslash_site(Uh, spn_h, dims, int(n), 0.01, 1.0, True, True))
+            assert e.rel() < TOL, (op, e.rel())
         del U
         torch.cuda.empty_cache()

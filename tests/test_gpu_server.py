@@ -29,8 +29,9 @@ def links(dims, seed):
     return torch.from_numpy(ls.su3_links(dims, seed, ls.PLAQ_EPS)).cuda()
 
 
-ENGINES = [((4, 4, 4, 4), 0, 1), ((6, 4, 4, 6), 1, 1), ((4, 4, 2, 6), 0, 0), ((4, 4, 4, 4), 1, 2)]
-# (dims, op, precision)
+ENGINES = [((4, 4, 4, 4), 0, 1), ((6, 4, 4, 6), 1, 1), ((4, 4, 2, 6), 0, 0), ((4, 4, 4, 4), 1, 2),
+           ((6, 4, 4, 6), 0, 2)]
+# (dims, op, precision): FP32, FP64 and FP16-storage engines of both operators
 
 
 def make_server(sw, slots=3):
@@ -60,13 +61,13 @@ def test_result_alone_equals_result_in_mix(sw):
         assert got_id == rid and info.status == sw.SW_OK and info.true_rel_resid <= 1e-9
         probe.append(x.copy())
     srv.close()
-    # in a mix: 40 requests over the four engines (3 slots each), the probes in the middle
+    # in a mix: 40 requests over the engines (3 slots each), the probes in the middle
     srv, eng = make_server(sw)
     mix = {}
     rng = np.random.default_rng(0)
     ids = {}
     for j in range(40):
-        k = int(rng.integers(0, 4))
+        k = int(rng.integers(0, len(ENGINES)))
         dims, op, prec = ENGINES[k]
         if j == 20:
             for kk, (d2, o2, p2) in enumerate(ENGINES):
@@ -82,7 +83,7 @@ def test_result_alone_equals_result_in_mix(sw):
         if kind == "probe":
             mix[k] = x
     srv.close()
-    for k in range(4):
+    for k in range(len(ENGINES)):
         assert np.array_equal(mix[k], probe[k]), f"engine {k}"
 
 
@@ -127,4 +128,73 @@ def test_budget_and_arguments(sw):
         srv.submit(eng, chi, x, 0.1)
         srv.add_engine(dims, 0, U, 1.0, sw.SW_PREC_F32_RELIABLE, 4)
     srv.drain(60)
+    srv.close()
+
+
+def field_request_bytes(sw, dims, U, op, prec, slots):
+    """Device bytes the server charges for the engine of one (field, op,
+    precision): measured by serving one request alone."""
+    srv = sw.Server(8 << 30)
+    f = srv.add_field(dims, U, slots)
+    base = srv.stats()["bytes_charged"]
+    chi, x = request(dims, op, 7)
+    srv.submit_field(f, op, chi, x, 0.1, prec, tol=1e-9)
+    srv.drain(120)
+    st = srv.stats()
+    srv.close()
+    return base, st["bytes_charged"] - base
+
+
+def test_field_requests_wait_for_memory(sw):
+    """Admission by device memory: with a budget that holds the field and one
+    engine but not two, a request for a second (operator, precision) on the
+    same field waits until the first engine is idle and retired, then gets
+    its own engine; each result is bit-identical to the same request served
+    alone, and FP16 and FP32 engines alternate in the same budget."""
+    dims = (6, 4, 4, 6)
+    U = links(dims, 21)
+    classes = [(1, sw.SW_PREC_F32_RELIABLE), (0, sw.SW_PREC_F16_RELIABLE), (1, sw.SW_PREC_F16_RELIABLE)]
+    sizes = [field_request_bytes(sw, dims, U, op, prec, 2) for op, prec in classes]
+    field_bytes = sizes[0][0]
+    budget = field_bytes + max(b for _, b in sizes) + 1024
+    assert budget < field_bytes + sizes[0][1] + sizes[1][1]
+    # alone
+    alone = []
+    for k, (op, prec) in enumerate(classes):
+        srv = sw.Server(8 << 30)
+        f = srv.add_field(dims, U, 2)
+        chi, x = request(dims, op, 300 + k)
+        srv.submit_field(f, op, chi, x, 0.05 + 0.02 * k, prec, tol=1e-9)
+        srv.drain(120)
+        (_, info), = srv.poll()
+        assert info.status == sw.SW_OK
+        alone.append(x.copy())
+        srv.close()
+    # all three at once under the tight budget: they must take turns
+    srv = sw.Server(budget)
+    f = srv.add_field(dims, U, 2)
+    ids = {}
+    for k, (op, prec) in enumerate(classes):
+        chi, x = request(dims, op, 300 + k)
+        ids[srv.submit_field(f, op, chi, x, 0.05 + 0.02 * k, prec, tol=1e-9)] = (k, x)
+    srv.drain(300)
+    done = dict(srv.poll())
+    st = srv.stats()
+    srv.close()
+    assert set(done) == set(ids) and all(i.status == sw.SW_OK for i in done.values())
+    assert st["engines_created"] == 3 and st["engines_retired"] >= 2 and st["requests_waited_for_memory"] >= 1
+    assert st["bytes_charged"] <= budget
+    for rid, (k, x) in ids.items():
+        assert np.array_equal(x, alone[k]), k
+
+
+def test_field_request_that_can_never_fit_is_refused(sw):
+    dims = (8, 8, 8, 8)
+    U = links(dims, 2)
+    srv = sw.Server(((8 ** 4) * 576) + (64 << 10))  # the field fits, no engine does
+    f = srv.add_field(dims, U, 4)
+    chi, x = request(dims, 1, 1)
+    with pytest.raises(sw.SWError) as e:
+        srv.submit_field(f, 1, chi, x, 0.1, sw.SW_PREC_F32_RELIABLE)
+    assert e.value.code == -6
     srv.close()

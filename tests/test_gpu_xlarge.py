@@ -8,7 +8,8 @@ epsilon of Sec. 3).
   the FP64 count (a wrong inner-precision stencil, which the FP64 reliable
   updates would otherwise correct, shows up as extra iterations).
 - 24^3x48 batched: 2 Z2 sources x 2 masses per operator in one
-  cgne_solve_batch each (FP32 inner, FP64 reliable updates): the oracle's
+  cgne_solve_batch each, run as one device-driven CUDA graph launch (FP32
+  inner, FP64 reliable updates): the oracle's
   literal operators give each GPU solution's true residual, and the oracle's
   one-site operator reproduces (D+m) x at sampled sites.
 
@@ -122,8 +123,13 @@ def test_batched_24x48_sources_and_masses(sw):
         ms = [m for m in masses for _ in seeds]
         chi = dev(chis)
         x = torch.zeros_like(chi)
-        rc, infos = sw.cgne_solve_batch(DIMS24, op, U, W if nc == 3 else None, chi, x, ms, 1.0, TOL, 100000,
-                                        sw.SW_PREC_F32_RELIABLE)
+        old = sw.sw_get_param(sw.SW_PARAM_PERSISTENT)
+        try:  # each operator's batch as one device-driven CUDA graph launch
+            sw.sw_set_param(sw.SW_PARAM_PERSISTENT, 1)
+            rc, infos = sw.cgne_solve_batch(DIMS24, op, U, W if nc == 3 else None, chi, x, ms, 1.0, TOL, 100000,
+                                            sw.SW_PREC_F32_RELIABLE)
+        finally:
+            sw.sw_set_param(sw.SW_PARAM_PERSISTENT, old)
         assert rc == sw.SW_OK and all(i.status == sw.SW_OK and i.true_rel_resid <= TOL for i in infos)
         xs = x.cpu().numpy()
         for k, m in enumerate(ms):
