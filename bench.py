@@ -944,7 +944,8 @@ def cpu_baseline(Uflat, iters_by_mass, dims=DIMS):
     s_sw = float(np.mean([p["sw"]["s_per_iter"] for p in res]))
     s_w = float(np.mean([p["wilson"]["s_per_iter"] for p in res]))
     return {"value": round(value, 6), "unit": "solves/s", "cores": n, "kind": "oracle",
-            "sample": (f"oracle (numpy FP64) CG on {'x'.join(map(str, dims))} links, m=0.1, one process per "
+            "sample": (f"oracle (numpy FP64; staggered Wilson with the literal symmetrised C-product form of "
+                       f"Gamma55, the oracle as it stands) CG on {'x'.join(map(str, dims))} links, m=0.1, one process per "
                        f"host core ({n}), all timed concurrently: each 2 staggered Wilson + 3 Wilson "
                        f"iterations ({spent:.1f} s wall); mean s/iter SW {s_sw:.2f}, W {s_w:.2f}; each "
                        f"process's rate scaled to the workload's 60 solves with this run's iteration counts "
@@ -970,7 +971,8 @@ def run_reference(args):
             vals.append((v, time.perf_counter() - t0))
     value = float(np.mean([v for v, _ in vals]))
     ms = float(np.mean([t for _, t in vals])) * 1e3
-    sample = (f"per step: 1 staggered Wilson + 1 Wilson CG iteration of the oracle (numpy FP64) on that step's "
+    sample = (f"per step: 1 staggered Wilson + 1 Wilson CG iteration of the oracle (numpy FP64; literal "
+              f"symmetrised C-product form of Gamma55) on that step's "
               f"16^3x32 configuration at m=0.1, in one process per host core ({cores}) timed concurrently; each "
               f"process's rate scaled to the 60 solves with the mean iteration counts per operator and mass of "
               f"the workload, summed over the processes")

@@ -326,13 +326,13 @@ template <int NS> __device__ __forceinline__ void block_sum_multi(double* v, dou
 // so a system's sums are the same whatever the grid or the batch.
 constexpr int kWarps = kTile / 32;
 template <int NS>
-__device__ __forceinline__ void put_warp_sums(const RedBuf& rb, int sys0, unsigned act, int tile, double* v) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__device__ __forceinline__ void put_warp_sums(const RedBuf& rb, int sys0, unsigned act, int slot, double* v) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[s] += __shfl_down_sync(0xffffffffu, v[s], o);
-    if (lane == 0 && (act & (1u << s))) rb.partials[(size_t)(sys0 + s) * rb.pstride + kWarps * tile + w] = v[s];
+    if (lane == 0 && (act & (1u << s))) rb.partials[(size_t)(sys0 + s) * rb.pstride + slot] = v[s];
   }
 }
 
@@ -406,22 +406,23 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k1(GG g
         acc[s] = (double)a;
       });
     }
-    put_warp_sums<NS>(rb, sys0, act, tile, acc);
+    put_warp_sums<NS>(rb, sys0, act, kWarps * tile + (threadIdx.x >> 5), acc);
   }
   __threadfence();  // every warp's partials, before the block's ticket
   if (block_done(rb, grp, &last, nbt)) {
 #pragma unroll 1
     for (int s = 0; s < NS; ++s) {
       if (!(act & (1u << s))) continue;
-      const double pAp = finalize_sum(rb, sys0 + s, kWarps * ntiles, sm);
+      const int sys = sys0 + s;
+      const double pAp = finalize_sum(rb, sys, kWarps * ntiles, sm);
       if (threadIdx.x == 0) {
-        SysState& st = S[sys0 + s];
+        SysState& st = S[sys];
         st.pAp = pAp;
         if (!(pAp > 0.0) || !isfinite(pAp)) {
           st.status = ST_FAILED;
         } else {
           st.alpha = st.rr / pAp;
-          record(rb, sys0 + s, st.iter, 0, st.alpha);
+          record(rb, sys, st.iter, 0, st.alpha);
         }
       }
     }
@@ -435,9 +436,7 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(GG g
                                                int* nact, int gfast) {
   __shared__ double sm[NS * 32];
   __shared__ int last;
-  // gfast: blockIdx.x = group of NS systems (the groups working on the same
-  // tiles are launched side by side), blockIdx.y strides over the tiles;
-  // otherwise the other way round
+  // groups and tiles as in cg_k1
   const int grp = gfast ? blockIdx.x : blockIdx.y, bt = gfast ? blockIdx.y : blockIdx.x;
   const int nbt = gfast ? gridDim.y : gridDim.x;
   const int sys0 = grp * NS;
@@ -451,9 +450,6 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(GG g
   t = sys_view(t, sys0, bp.vstride);
   r = sys_view(r, sys0, bp.sstride);
   const int ntiles = (g.V + kTile - 1) / kTile;
-  // grid-stride over tiles: the blocks resident at a time cover neighbouring
-  // tiles, which keeps their neighbour reads together in L2 (measured faster
-  // on GB300 than giving each block one contiguous range of tiles)
   for (int tile = bt; tile < ntiles; tile += nbt) {
     const int n = tile * kTile + threadIdx.x;
     double acc[NS];
@@ -473,16 +469,17 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(GG g
         acc[s] = (double)a;
       });
     }
-    put_warp_sums<NS>(rb, sys0, act, tile, acc);
+    put_warp_sums<NS>(rb, sys0, act, kWarps * tile + (threadIdx.x >> 5), acc);
   }
   __threadfence();  // every warp's partials, before the block's ticket
   if (block_done(rb, grp, &last, nbt)) {
 #pragma unroll 1
     for (int s = 0; s < NS; ++s) {
       if (!(act & (1u << s))) continue;
-      const double rr = finalize_sum(rb, sys0 + s, kWarps * ntiles, sm);
+      const int sys = sys0 + s;
+      const double rr = finalize_sum(rb, sys, kWarps * ntiles, sm);
       if (threadIdx.x == 0) {
-        SysState& st = S[sys0 + s];
+        SysState& st = S[sys];
         st.iter += 1;
         if (!isfinite(rr)) {
           st.status = ST_FAILED;
@@ -490,7 +487,7 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(GG g
           st.rr_old = st.rr;
           st.rr = rr;
           st.beta = rr / st.rr_old;
-          record(rb, sys0 + s, st.iter - 1, 1, st.beta);
+          record(rb, sys, st.iter - 1, 1, st.beta);
           if (rr > st.rmax2) st.rmax2 = rr;
           if (rr <= st.tol2 || st.iter >= st.max_iter || rr < st.delta2 * st.rmax2) st.status = ST_NEED_RU;
         }
