@@ -57,11 +57,11 @@ ITERS_TABLE = {"sw": {0.02: 41.0, 0.05: 39.0, 0.1: 36.9, 0.2: 32.0},
 # with the systems computed).  Entries are removed when the kernel changes.
 NCU_TRAFFIC = {
     # profiles/ncu_sw_k1k2_fp32_16x16x16x32_12sys.md
-    "sw.k1.f32": {"bytes": 199.6e6, "algorithmic": 188.7e6, "systems": 12},
-    "sw.k2.f32": {"bytes": 230.5e6, "algorithmic": 226.5e6, "systems": 12},
+    "sw.k1.f32": {"bytes": 194.1e6, "algorithmic": 188.7e6, "systems": 12},
+    "sw.k2.f32": {"bytes": 230.9e6, "algorithmic": 226.5e6, "systems": 12},
     # profiles/ncu_wilson_k1k2k3_fp32_16x16x16x32_12sys.md
-    "wilson.k1.f32": {"bytes": 323.9e6, "algorithmic": 339.7e6, "systems": 12},
-    "wilson.k2.f32": {"bytes": 475.4e6, "algorithmic": 490.7e6, "systems": 12},
+    "wilson.k1.f32": {"bytes": 323.6e6, "algorithmic": 339.7e6, "systems": 12},
+    "wilson.k2.f32": {"bytes": 477.4e6, "algorithmic": 490.7e6, "systems": 12},
 }
 
 # FP64 peak of a GB300 when no measurement is given (nominal 1.25 TFLOP/s; the
