@@ -66,7 +66,18 @@ enum {
                             not device memory or smaller than required) */
 };
 
-enum { SW_OP_STAGGERED_WILSON = 0, SW_OP_WILSON = 1 };
+/* SW_OP_WILSON_EVEN_ODD: the Wilson operator, with cgne_solve / cgne_solve_batch
+ * running CGNE on its even-odd Schur complement D^ = M - D_eo D_oe / M (M = 4r + m,
+ * D_eo, D_oe the hops between the parities of x0+x1+x2+x3): chi^_e = chi_e -
+ * D_eo chi_o / M, CGNE on D^+ D^ psi_e = D^+ chi^_e over the even sites,
+ * psi_o = (chi_o - D_oe psi_e) / M.  Same vectors and solution as SW_OP_WILSON;
+ * the returned true_rel_resid is the FP64 normal-equation residual of the full
+ * system, and the solve resumes with a tighter Schur tolerance until it meets
+ * tol (iters counts every Schur iteration).  Precisions SW_PREC_F64 and
+ * SW_PREC_F32_RELIABLE.  This is preconditioning outside the paper's
+ * comparison (which is unpreconditioned); the staggered Wilson operator has no
+ * such form, its Gamma55 term coupling sites of equal parity. */
+enum { SW_OP_STAGGERED_WILSON = 0, SW_OP_WILSON = 1, SW_OP_WILSON_EVEN_ODD = 2 };
 
 /* Arithmetic of the inner CG iterations.  SW_PREC_F64: every step in FP64.
  * SW_PREC_F32_RELIABLE: matvecs and vector updates in FP32 on packed copies,

@@ -12,7 +12,7 @@ from __future__ import annotations
 
 from ._binding import (  # noqa: F401
     SWError, SolveInfo, Server, lib, lib_path,
-    SW_OK, SW_NOT_CONVERGED, SW_OP_STAGGERED_WILSON, SW_OP_WILSON,
+    SW_OK, SW_NOT_CONVERGED, SW_OP_STAGGERED_WILSON, SW_OP_WILSON, SW_OP_WILSON_EVEN_ODD,
     SW_PREC_F64, SW_PREC_F32_RELIABLE, SW_PREC_F16_RELIABLE,
     sw_hypercube_build, sw_dslash_apply, wilson_dslash_apply, dslash_apply_inner, cgne_solve, cgne_solve_batch,
     sw_status_string, sw_last_cuda_error, sw_profile_enable, sw_profile_reset, sw_profile_read,

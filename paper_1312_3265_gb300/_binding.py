@@ -11,6 +11,7 @@ SW_OK = 0
 SW_NOT_CONVERGED = 1
 SW_OP_STAGGERED_WILSON = 0
 SW_OP_WILSON = 1
+SW_OP_WILSON_EVEN_ODD = 2
 SW_PREC_F64 = 0
 SW_PREC_F32_RELIABLE = 1
 SW_PREC_F16_RELIABLE = 2

@@ -399,13 +399,14 @@ int cgne_solve(const sw_lattice* lat, int op, const void* U, const void* W, cons
   if (info) *info = sw_solve_info{};
   Geom g;
   SW_TRY(make_geom(lat, &g));
-  if (op != SW_OP_STAGGERED_WILSON && op != SW_OP_WILSON) return SW_ERR_ARG;
+  if (op != SW_OP_STAGGERED_WILSON && op != SW_OP_WILSON && op != SW_OP_WILSON_EVEN_ODD) return SW_ERR_ARG;
   if (precision != SW_PREC_F64 && precision != SW_PREC_F32_RELIABLE && precision != SW_PREC_F16_RELIABLE)
     return SW_ERR_ARG;
+  if (op == SW_OP_WILSON_EVEN_ODD && precision == SW_PREC_F16_RELIABLE) return SW_ERR_ARG;
   if (!(tol > 0.0) || !(tol < 1.0) || max_iter < 1) return SW_ERR_ARG;
   if (!(mass == mass) || !(r == r)) return SW_ERR_ARG;
   const size_t V = g.V;
-  const size_t vb = V * (op == SW_OP_WILSON ? 192 : 48);
+  const size_t vb = V * (op != SW_OP_STAGGERED_WILSON ? 192 : 48);
   SW_TRY(check_buf(U, V * 576));
   if (op == SW_OP_STAGGERED_WILSON) SW_TRY(check_buf(W, V * 1152));
   SW_TRY(check_buf(chi, vb));
@@ -414,7 +415,8 @@ int cgne_solve(const sw_lattice* lat, int op, const void* U, const void* W, cons
   SolveArgs a{static_cast<const double2*>(U), static_cast<const double2*>(W), static_cast<const double2*>(chi),
               static_cast<double2*>(x), 1, &mass, r, tol, max_iter, precision, info,
               static_cast<cudaStream_t>(stream)};
-  const int rc = (op == SW_OP_WILSON) ? wilson_cgne(g, a) : sw_cgne(g, a);
+  const int rc = (op == SW_OP_WILSON) ? wilson_cgne(g, a) : (op == SW_OP_WILSON_EVEN_ODD) ? wilson_cgne_eo(g, a)
+                                                                                           : sw_cgne(g, a);
   if (info) {
     info->status = rc;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -432,15 +434,16 @@ int cgne_solve_batch(const sw_lattice* lat, int op, const void* U, const void* W
     for (int i = 0; i < nsys; ++i) infos[i] = sw_solve_info{};
   Geom g;
   SW_TRY(make_geom(lat, &g));
-  if (op != SW_OP_STAGGERED_WILSON && op != SW_OP_WILSON) return SW_ERR_ARG;
+  if (op != SW_OP_STAGGERED_WILSON && op != SW_OP_WILSON && op != SW_OP_WILSON_EVEN_ODD) return SW_ERR_ARG;
   if (precision != SW_PREC_F64 && precision != SW_PREC_F32_RELIABLE && precision != SW_PREC_F16_RELIABLE)
     return SW_ERR_ARG;
+  if (op == SW_OP_WILSON_EVEN_ODD && precision == SW_PREC_F16_RELIABLE) return SW_ERR_ARG;
   if (!(tol > 0.0) || !(tol < 1.0) || max_iter < 1) return SW_ERR_ARG;
   for (int i = 0; i < nsys; ++i)
     if (!(masses[i] == masses[i])) return SW_ERR_ARG;
   if (!(r == r)) return SW_ERR_ARG;
   const size_t V = g.V;
-  const size_t vb = V * (op == SW_OP_WILSON ? 192 : 48) * (size_t)nsys;
+  const size_t vb = V * (op != SW_OP_STAGGERED_WILSON ? 192 : 48) * (size_t)nsys;
   SW_TRY(check_buf(U, V * 576));
   if (op == SW_OP_STAGGERED_WILSON) SW_TRY(check_buf(W, V * 1152));
   SW_TRY(check_buf(chi, vb));
@@ -449,7 +452,8 @@ int cgne_solve_batch(const sw_lattice* lat, int op, const void* U, const void* W
   SolveArgs a{static_cast<const double2*>(U), static_cast<const double2*>(W), static_cast<const double2*>(chi),
               static_cast<double2*>(x), nsys, masses, r, tol, max_iter, precision, infos,
               static_cast<cudaStream_t>(stream)};
-  const int rc = (op == SW_OP_WILSON) ? wilson_cgne(g, a) : sw_cgne(g, a);
+  const int rc = (op == SW_OP_WILSON) ? wilson_cgne(g, a) : (op == SW_OP_WILSON_EVEN_ODD) ? wilson_cgne_eo(g, a)
+                                                                                           : sw_cgne(g, a);
   if (infos) {
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     for (int i = 0; i < nsys; ++i) infos[i].seconds = secs;

@@ -21,6 +21,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -39,6 +40,14 @@ int param_ns(int nc);  // systems per thread of the FP32 stencils (1, 2 or 4) fo
 bool param_group_fast();     // system groups as the fastest grid dimension of the stencils
 bool param_graphs();   // replay chunks of iterations as captured CUDA graphs
 bool param_persistent();  // whole solve as one CUDA graph with a device-driven loop of rounds
+
+// Operators applied in two passes (the even-odd Schur complement): before
+// every application the engine launches the operator's pre-pass, which
+// writes the intermediate field into scratch that follows each system's
+// vector; their FP64 vectors therefore take twice the per-system stride.
+template <class Op, class = void> struct two_pass : std::false_type {};
+template <class Op> struct two_pass<Op, std::void_t<decltype(Op::kTwoPass)>> : std::bool_constant<Op::kTwoPass> {};
+template <class Op> constexpr int f64_stride_factor() { return two_pass<Op>::value ? 2 : 1; }
 
 inline int grid_for(const void* kernel, int block, int V, int nsys, int cap) {
   static std::mutex mu;
@@ -163,11 +172,12 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 // Bytes of workspace for nsys systems of NC complex components per site; pt:
 // bytes of one system's p (or t) in the inner precision's storage.
-inline size_t workspace_bytes_pt(int V, int NC, int nsys, bool mixed, size_t pt) {
-  const size_t n = (size_t)V * NC * nsys;
+inline size_t workspace_bytes_pt(int V, int NC, int nsys, bool mixed, size_t pt, int f64_factor = 1) {
+  const size_t n = (size_t)V * NC * nsys * f64_factor;
   const size_t ntiles = (size_t)(V + kTile - 1) / kTile;
   size_t b = (mixed ? 2 : 3) * align_up(sizeof(double2) * n);  // b64 only in FP64 mode
-  b += mixed ? 2 * align_up(pt * nsys) + 2 * align_up(sizeof(float2) * n) : align_up(pt * nsys);
+  const size_t n32 = (size_t)V * NC * nsys;  // FP32 r and x carry no scratch
+  b += mixed ? 2 * align_up(pt * nsys) + 2 * align_up(sizeof(float2) * n32) : align_up(pt * nsys);
   b += align_up(sizeof(SysState) * nsys) + align_up(sizeof(double) * 2 * kWarps * ntiles * nsys) +
        align_up(sizeof(unsigned) * 2 * nsys) + align_up(sizeof(double) * nsys) +
        align_up(sizeof(double) * 2 * kHist * nsys) + align_up(sizeof(int) * 2 * kProfSlots) +
@@ -178,12 +188,16 @@ inline size_t workspace_bytes_pt(int V, int NC, int nsys, bool mixed, size_t pt)
 inline size_t workspace_bytes(int V, int NC, int nsys, bool mixed) {
   return workspace_bytes_pt(V, NC, nsys, mixed, (size_t)V * NC * (mixed ? sizeof(float2) : sizeof(double2)));
 }
-template <class PVec> inline size_t workspace_bytes_for(int V, int NC, int nsys, bool mixed) {
-  return workspace_bytes_pt(V, NC, nsys, mixed, sizeof(typename PVec::unit) * PVec::sys_units(V));
+// f64_factor: 2 for two-pass operators, whose FP64 vectors and stencil
+// vectors p, t carry their scratch after each system's field
+template <class PVec> inline size_t workspace_bytes_for(int V, int NC, int nsys, bool mixed, int f64_factor = 1) {
+  return workspace_bytes_pt(V, NC, nsys, mixed, sizeof(typename PVec::unit) * PVec::sys_units(V) * f64_factor,
+                            f64_factor);
 }
 
-inline Workspace carve_workspace_pt(void* base, int V, int NC, int nsys, bool mixed, size_t pt) {
-  const size_t n = (size_t)V * NC * nsys;
+inline Workspace carve_workspace_pt(void* base, int V, int NC, int nsys, bool mixed, size_t pt, int f64_factor = 1) {
+  const size_t n = (size_t)V * NC * nsys * f64_factor;
+  const size_t n32 = (size_t)V * NC * nsys;
   const size_t ntiles = (size_t)(V + kTile - 1) / kTile;
   char* c = static_cast<char*>(base);
   auto take = [&](size_t bytes) {
@@ -198,8 +212,8 @@ inline Workspace carve_workspace_pt(void* base, int V, int NC, int nsys, bool mi
   if (mixed) {
     w.p_lo = take(pt * nsys);
     w.t_lo = take(pt * nsys);
-    w.r32 = (float2*)take(sizeof(float2) * n);
-    w.x32 = (float2*)take(sizeof(float2) * n);
+    w.r32 = (float2*)take(sizeof(float2) * n32);
+    w.x32 = (float2*)take(sizeof(float2) * n32);
   } else {
     w.p_lo = take(pt * nsys);
     w.t_lo = w.t64;
@@ -217,8 +231,10 @@ inline Workspace carve_workspace(void* base, int V, int NC, int nsys, bool mixed
   return carve_workspace_pt(base, V, NC, nsys, mixed,
                             (size_t)V * NC * (mixed ? sizeof(float2) : sizeof(double2)));
 }
-template <class PVec> inline Workspace carve_workspace_for(void* base, int V, int NC, int nsys, bool mixed) {
-  return carve_workspace_pt(base, V, NC, nsys, mixed, sizeof(typename PVec::unit) * PVec::sys_units(V));
+template <class PVec>
+inline Workspace carve_workspace_for(void* base, int V, int NC, int nsys, bool mixed, int f64_factor = 1) {
+  return carve_workspace_pt(base, V, NC, nsys, mixed, sizeof(typename PVec::unit) * PVec::sys_units(V) * f64_factor,
+                            f64_factor);
 }
 
 // A CGNE engine: `cap` system slots on one gauge field, advanced together.
@@ -263,7 +279,8 @@ class Engine {
          const Workspace& ws, SysState* hs_read, SysState* hs_stage, cudaStream_t st, cudaEvent_t ev,
          bool use_graphs = true)
       : g_(g), opd_(opd), opf_(opf), r_(r), cap_(cap), chi_(chi), x_(x), ws_(ws), hr_(hs_read), hst_(hs_stage),
-        st_(st), ist_(st), ev_(ev), n_((size_t)g.V * NC), use_graphs_(use_graphs && param_graphs()),
+        st_(st), ist_(st), ev_(ev), n_((size_t)g.V * NC), s64_(n_ * f64_stride_factor<OpD>()),
+        use_graphs_(use_graphs && param_graphs()),
         driver_resources_(use_graphs) {
     ntiles_ = (g.V + kTile - 1) / kTile;
     pstride_ = kWarps * ntiles_;
@@ -275,9 +292,10 @@ class Engine {
     // the reliable-update kernels may run while iterations of other systems
     // run on the side: their own block tickets (per system, not per group)
     rbu_ = RedBuf{ws.partials, ws.tickets + cap, pstride_, ws.hist};
-    vunits_ = VF::sys_units(g.V);
-    runits_ = VR::sys_units(g.V);
-    bp_ = BatchParams{r, runits_, n_, vunits_};
+    vunits_ = VF::sys_units(g.V) * f64_stride_factor<OpF>();  // (with a two-pass operator's scratch)
+    // FP64 mode: r and x are the FP64 vectors themselves (stride s64_)
+    runits_ = MIXED ? VR::sys_units(g.V) : s64_;
+    bp_ = BatchParams{r, runits_, s64_, vunits_};
     ns_ = MIXED ? param_ns(NC) : 1;
     ngrp_ = (cap + ns_ - 1) / ns_;
     set_grids(ngrp_);
@@ -365,8 +383,8 @@ class Engine {
     // bytes of the stored gauge data (links, transports) and of one system's
     // stencil vector (p or t) and inner-precision vector (r or x)
     const double gauge = (double)g_.V * OpF::kGaugeBytes;
-    const double pv = (double)sizeof(typename VF::unit) * vunits_;
-    const double rv = (double)sizeof(typename VR::unit) * runits_;
+    const double pv = (double)sizeof(typename VF::unit) * VF::sys_units(g_.V);
+    const double rv = (double)sizeof(typename VR::unit) * VR::sys_units(g_.V);
     // flops: the paper's count per site and application (Eq. 4) for every
     // computed system (k2's r update is not counted)
     const double fl = OpF::kFlops * g_.V;
@@ -396,8 +414,8 @@ class Engine {
 
   int cap() const { return cap_; }
   size_t slot_elems() const { return n_; }
-  double2* chi_slot(int i) const { return chi_ + (size_t)i * n_; }
-  double2* x_slot(int i) const { return x_ + (size_t)i * n_; }
+  double2* chi_slot(int i) const { return chi_ + (size_t)i * s64_; }
+  double2* x_slot(int i) const { return x_ + (size_t)i * s64_; }
   const SysState& state(int i) const { return hr_[i]; }
   const double* hist() const { return ws_.hist; }
   cudaStream_t stream() const { return st_; }
@@ -585,7 +603,7 @@ class Engine {
           ist_ = st_;
           cudaGraph_t body = nullptr;
           ok = cudaStreamEndCapture(body_st, &body) == cudaSuccess;
-          per_round = 2 + (MIXED ? 7 : 5) + 4 * chunk_;
+          per_round = 2 + (MIXED ? 7 : 5) + 4 * chunk_ + (two_pass<OpF>::value ? 2 * chunk_ + 2 : 0);
         }
       }
       ok = ok && cudaStreamUpdateCaptureDependencies(st_, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies) ==
@@ -627,6 +645,17 @@ class Engine {
   long long rounds() const { return rounds_; }
 
  private:
+  // The pre-pass of a two-pass operator (nothing for the others): the
+  // intermediate field of `in`'s systems in `status`, before the operator
+  // is applied to them.
+  template <class Op, class Vec>
+  void prepass(const Op& op, const Vec& in, size_t stride, int status, bool dagger, cudaStream_t s) {
+    if constexpr (two_pass<Op>::value) {
+      op.prepass(in, stride, ws_.S, status, dagger ? 1 : 0, cap_, s);
+      launches(1);
+    }
+  }
+
   // Admission launches for the na slots staged (their status words already on
   // the device): see the class comment.
   void admit(int na) {
@@ -639,21 +668,23 @@ class Engine {
     if constexpr (MIXED) {
       // b = (D+m)^+ chi in the inner precision: r = p = b and |b|^2
       demote_chi<NC, VF><<<dim3(grid_of((const void*)demote_chi<NC, VF>, 256, na), cap_), 256, 0, st_>>>(
-          gb_, chi_, ft_, n_, vunits_, S);
+          gb_, chi_, ft_, s64_, vunits_, S);
+      prepass(opf_, ft_, vunits_, ST_ADMIT, true, st_);
       rhs_lo<TF, OpF, VR, GK><<<dim3(grid_of((const void*)rhs_lo<TF, OpF, VR, GK>, kTile, na), cap_), kTile, 0,
                                 st_>>>(gk_, opf_, ft_, fp_, fr_, bp_, S, rb_);
-      norm_b<NC><<<dim3(gn, cap_), kTile, 0, st_>>>(g_.V, nullptr, x_, n_, S, rb_);
-      admit_vectors<NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, nullptr, n_, S);
+      norm_b<NC><<<dim3(gn, cap_), kTile, 0, st_>>>(g_.V, nullptr, x_, s64_, S, rb_);
+      admit_vectors<NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, nullptr, s64_, S);
       launches(1);
     } else {
       FpSample* fs = fp_sample(1, st_);
       if (prof()) prof_count(cls_rhs(), 1);
+      prepass(opd_, V64{chi_}, s64_, ST_ADMIT, true, st_);
       apply_kernel<double, OpD><<<dim3(grid_of((const void*)apply_kernel<double, OpD>, kTile, na), cap_), kTile,
-                                  0, st_>>>(g_, opd_, V64{chi_}, V64{ws_.b64}, 0.0, n_, r_, 1, S, ST_ADMIT,
+                                  0, st_>>>(g_, opd_, V64{chi_}, V64{ws_.b64}, 0.0, s64_, r_, 1, S, ST_ADMIT,
                                             fs ? fs->cnt : nullptr);
       if (fs) cudaEventRecord(fs->e1, st_);
-      norm_b<NC><<<dim3(gn, cap_), kTile, 0, st_>>>(g_.V, ws_.b64, x_, n_, S, rb_);
-      admit_vectors<NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, ws_.b64, n_, S);
+      norm_b<NC><<<dim3(gn, cap_), kTile, 0, st_>>>(g_.V, ws_.b64, x_, s64_, S, rb_);
+      admit_vectors<NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, x_, ws_.r64, ws_.b64, s64_, S);
     }
     admit_states<<<(cap_ + 127) / 128, 128, 0, st_>>>(cap_, S, MIXED ? 1 : 0);
     launches(5);
@@ -709,17 +740,19 @@ class Engine {
     const int gv = grid_of((const void*)cg_k3<TF, VR, VF, NC>, 256, nsys);
     // the last x += alpha p of each system (k2 stopped it before k3)
     cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, sx>>>(g_.V, fr_, fp_, fx_, runits_, vunits_, S, ST_RU_PENDING, 1);
-    if constexpr (MIXED) accum_x<NC, VR><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, x_, fx_, n_, runits_, S);
+    if constexpr (MIXED) accum_x<NC, VR><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, x_, fx_, s64_, runits_, S);
     FpSample* fs = fp_sample(2, sx);
     if (prof()) prof_count(cls_ru(), 1);
     // r = (D+m)^+ (chi - (D+m) x) = b - A x, all in FP64
+    prepass(opd_, V64{x_}, s64_, ST_RU_PENDING, false, sx);
     apply_kernel<double, OpD><<<dim3(grid_of((const void*)apply_kernel<double, OpD>, kTile, nsys), cap_), kTile, 0,
-                                sx>>>(g_, opd_, V64{x_}, V64{ws_.t64}, 0.0, n_, r_, 0, S, ST_RU_PENDING,
+                                sx>>>(g_, opd_, V64{x_}, V64{ws_.t64}, 0.0, s64_, r_, 0, S, ST_RU_PENDING,
                                       fs ? fs->cnt : nullptr, V64{chi_}, 1);
+    prepass(opd_, V64{ws_.t64}, s64_, ST_RU_PENDING, true, sx);
     residual64<OpD><<<dim3(grid_of((const void*)residual64<OpD>, kTile, nsys), cap_), kTile, 0, sx>>>(
         g_, opd_, V64{ws_.t64}, V64{ws_.r64}, bp_, S, rbu_);
     if (fs) cudaEventRecord(fs->e1, sx);
-    if constexpr (MIXED) demote_r<NC, VR><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, ws_.r64, fr_, n_, runits_, S);
+    if constexpr (MIXED) demote_r<NC, VR><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, ws_.r64, fr_, s64_, runits_, S);
     cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, sx>>>(g_.V, fr_, fp_, fx_, runits_, vunits_, S, ST_JUST_UPDATED, 2);
     mark_ready<<<(cap_ + 127) / 128, 128, 0, sx>>>(cap_, S);
     launches(MIXED ? 7 : 5);
@@ -827,8 +860,10 @@ class Engine {
   template <int NS> void launch_k12(int* c) {
     SysState* S = ws_.S;
     const dim3 grid1 = gfast_ ? dim3(ngrp_, g1_) : dim3(g1_, ngrp_), grid2 = gfast_ ? dim3(ngrp_, g2_) : dim3(g2_, ngrp_);
+    prepass(opf_, fp_, vunits_, ST_RUNNING, false, ist_);
     cg_k1<TF, OpF, NS, GK><<<grid1, kTile, 0, ist_>>>(gk_, opf_, fp_, ft_, bp_, cap_, S, rb_, c, gfast_);
     if (c) cudaEventRecord(samples_.back().e1, ist_);
+    prepass(opf_, ft_, vunits_, ST_RUNNING, true, ist_);
     cg_k2<TF, OpF, NS, VR, GK><<<grid2, kTile, 0, ist_>>>(gk_, opf_, ft_, fr_, bp_, cap_, S, rb_,
                                                           c ? c + 1 : nullptr, gfast_);
   }
@@ -888,7 +923,8 @@ class Engine {
   cudaStream_t st_;
   cudaStream_t ist_;  // stream the iteration kernels go to (st_, or the loop body's capture stream)
   cudaEvent_t ev_;
-  size_t n_;
+  size_t n_;    // complex components of one system's field (g.V x NC)
+  size_t s64_;  // per-system stride of the FP64 vectors (n_, or 2 n_ with a two-pass operator's scratch)
   int ntiles_ = 0, pstride_ = 0, ngrp_ = 0, gV_ = 0, g1_ = 0, g2_ = 0;
   RedBuf rb_{}, rbu_{};
   cudaStream_t side_ = nullptr;  // reliable updates overlapped with iterations
@@ -955,7 +991,7 @@ int run_cgne_ws(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& 
   const auto t0 = steady_clock::now();
   Engine<OpD, OpF, MIXED> e(g, opd, opf, a.r, a.nsys, const_cast<double2*>(a.chi), a.x, ws, hs, hs + a.nsys,
                             a.stream, nullptr, use_graphs);
-  for (int i = 0; i < a.nsys; ++i) e.stage(i, a.masses[i], a.tol, a.max_iter);
+  for (int i = 0; i < a.nsys; ++i) e.stage(i, a.masses[i], a.tols ? a.tols[i] : a.tol, a.max_iter);
   const long long max_rounds = 4LL * (a.max_iter / param_chunk() + 2) + 1000;
   int rc = SW_OK;
   bool host_rounds = true;
@@ -1027,10 +1063,11 @@ template <class OpD, class OpF, bool MIXED>
 int run_cgne(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& a) {
   using VF = typename OpF::Vec;
   DevMem mem;
-  if (!mem.alloc(workspace_bytes_for<VF>(g.V, OpD::NC, a.nsys, MIXED), a.stream)) return SW_ERR_OOM;
+  constexpr int f = f64_stride_factor<OpD>();
+  if (!mem.alloc(workspace_bytes_for<VF>(g.V, OpD::NC, a.nsys, MIXED, f), a.stream)) return SW_ERR_OOM;
   SysState* hs = nullptr;
   if (int e = pinned_states(2 * a.nsys, &hs)) return e;
-  const Workspace ws = carve_workspace_for<VF>(mem.p, g.V, OpD::NC, a.nsys, MIXED);
+  const Workspace ws = carve_workspace_for<VF>(mem.p, g.V, OpD::NC, a.nsys, MIXED, f);
   return run_cgne_ws<OpD, OpF, MIXED>(g, opd, opf, a, ws, hs, true,
                                       a.infos ? pinned_hist((size_t)2 * kHist * a.nsys) : nullptr);
 }

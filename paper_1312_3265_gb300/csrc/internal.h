@@ -22,6 +22,7 @@ struct SolveArgs {
   int precision;
   sw_solve_info* infos;
   cudaStream_t stream;
+  const double* tols = nullptr;  // host [nsys]: per-system tolerances (nullptr: tol for every system)
 };
 
 int hypercube_build_f64(const Geom& g, const double2* U, double2* W, cudaStream_t st);
@@ -36,6 +37,8 @@ int sw_inner_apply(const Geom& g, const double2* U, const double2* W, const doub
 int wilson_inner_apply(const Geom& g, const double2* U, const double2* in, double2* out, int nsys,
                        const double* masses, double r, int dagger, int precision, cudaStream_t st);
 int wilson_cgne(const Geom& g, const SolveArgs& a);
+// Wilson CGNE on the even-odd Schur complement (FP64 or FP32 inner), solution on the full lattice.
+int wilson_cgne_eo(const Geom& g, const SolveArgs& a);
 
 // Tunables set through the C ABI (api.cu), also used by the autotuner.
 extern "C" int sw_set_param(int key, double value);
