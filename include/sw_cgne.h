@@ -71,9 +71,12 @@ enum {
  * D_eo, D_oe the hops between the parities of x0+x1+x2+x3): chi^_e = chi_e -
  * D_eo chi_o / M, CGNE on D^+ D^ psi_e = D^+ chi^_e over the even sites,
  * psi_o = (chi_o - D_oe psi_e) / M.  Same vectors and solution as SW_OP_WILSON;
- * the returned true_rel_resid is the FP64 normal-equation residual of the full
- * system, and the solve resumes with a tighter Schur tolerance until it meets
- * tol (iters counts every Schur iteration).  Precisions SW_PREC_F64 and
+ * convergence is decided on, and true_rel_resid reports, the FP64
+ * normal-equation residual of the full system |b - A psi| / |b| (b = (D+m)^+
+ * chi), which every FP64 reliable update of the Schur solve also evaluates:
+ * with psi_o rebuilt from psi_e the full defect is (chi^_e - D^ psi_e, 0).
+ * iters counts Schur iterations; lambda_min, lambda_max estimate the extreme
+ * eigenvalues of D^+ D^.  Precisions SW_PREC_F64 and
  * SW_PREC_F32_RELIABLE.  This is preconditioning outside the paper's
  * comparison (which is unpreconditioned); the staggered Wilson operator has no
  * such form, its Gamma55 term coupling sites of equal parity. */

@@ -50,7 +50,9 @@ struct SysState {
   double alpha;
   double beta;
   double b2;       // |b|^2
-  double tol2;     // tol^2 |b|^2
+  double tol2;     // tol^2 |b|^2 (|b|^2: cb2 when set)
+  double trig2;    // iterated |r|^2 at or below which a reliable update checks convergence
+  double cb2;      // |b|^2 of the convergence criterion when it is another system's (0: b2)
   double rmax2;    // max |r|^2 since the last reliable update
   double delta2;   // reliable-update trigger factor (0: only at convergence)
   double rr_true;  // last FP64 residual norm^2
@@ -251,6 +253,9 @@ template <typename Vec> __device__ __forceinline__ Vec sys_view(Vec v, int sys, 
   v.p += sys * sstride;
   return v;
 }
+template <int NC> __device__ __forceinline__ VecP32x2<NC> sys_view(VecP32x2<NC> v, int sys, size_t sstride) {
+  return sys_at(v, sys, sstride);
+}
 
 struct BatchParams {
   double r;
@@ -364,8 +369,12 @@ __device__ __forceinline__ unsigned running_mask(const SysState* S, int sys0, in
 // stencils also convert and scale every value they load: at 7 blocks they
 // spill about 0.5 KB per thread (Wilson) and take 5 blocks (96 registers,
 // no spills), staggered Wilson 7.  FP64 kernels are ALU-bound: no cap.
+template <class Op, class = void> struct op_min_blocks : std::integral_constant<int, 0> {};
+template <class Op> struct op_min_blocks<Op, std::void_t<decltype(Op::kMinBlocks)>>
+    : std::integral_constant<int, Op::kMinBlocks> {};
 template <typename T, typename Op> constexpr int stencil_min_blocks() {
   if (sizeof(T) != 4) return 1;
+  if (op_min_blocks<Op>::value > 0) return op_min_blocks<Op>::value;  // the operator's own occupancy target
   if (Op::kHalf) return Op::NC == 3 ? 7 : 5;
   return Op::NC == 3 ? 8 : 7;
 }
@@ -489,7 +498,7 @@ __global__ void __launch_bounds__(kTile, stencil_min_blocks<T, Op>()) cg_k2(GG g
           st.beta = rr / st.rr_old;
           record(rb, sys, st.iter - 1, 1, st.beta);
           if (rr > st.rmax2) st.rmax2 = rr;
-          if (rr <= st.tol2 || st.iter >= st.max_iter || rr < st.delta2 * st.rmax2) st.status = ST_NEED_RU;
+          if (rr <= st.trig2 || st.iter >= st.max_iter || rr < st.delta2 * st.rmax2) st.status = ST_NEED_RU;
         }
       }
     }
@@ -528,6 +537,63 @@ __global__ void __launch_bounds__(256) cg_k3(int V, RVec r, PVec p, RVec x, size
   }
 }
 
+// k3 for a paired p (two systems' lanes per 16-byte unit): one thread per
+// site and pair reads the pair's unit once for both systems.  A lane whose
+// system is in another state keeps its value: when only one lane is active,
+// only its words are stored (another stream may be writing the other
+// lane's); with both active the whole unit is.
+template <typename RVec, typename PVec, int NC>
+__global__ void __launch_bounds__(256) cg_k3_pair(int V, RVec r, PVec p, RVec x, size_t rstride, size_t pstride,
+                                                  const SysState* S, int nsys, int only_status, int mode,
+                                                  int* nact = nullptr) {
+  const int s0 = 2 * blockIdx.y;
+  const bool a0 = S[s0].status == only_status, a1 = s0 + 1 < nsys && S[s0 + 1].status == only_status;
+  if (!a0 && !a1) return;
+  if (nact && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nact, (int)a0 + (int)a1);
+  float4* pp = p.p + (size_t)blockIdx.y * 2 * pstride;
+  const RVec r0 = sys_view(r, s0, rstride), x0 = sys_view(x, s0, rstride);
+  const RVec r1 = sys_view(r, a1 ? s0 + 1 : s0, rstride), x1 = sys_view(x, a1 ? s0 + 1 : s0, rstride);
+  const float beta0 = (float)S[s0].beta, alpha0 = (float)S[s0].alpha;
+  const float beta1 = a1 ? (float)S[s0 + 1].beta : 0.f, alpha1 = a1 ? (float)S[s0 + 1].alpha : 0.f;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < V; n += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float4* u = pp + pk(n, NC, c);
+      const float4 w = *u;  // (s0.re, s1.re, s0.im, s1.im)
+      if (mode & 1) {
+        if (a0) {
+          const cx<float> xv = x0.ld(n, c);
+          x0.st(n, c, {xv.re + alpha0 * w.x, xv.im + alpha0 * w.z});
+        }
+        if (a1) {
+          const cx<float> xv = x1.ld(n, c);
+          x1.st(n, c, {xv.re + alpha1 * w.y, xv.im + alpha1 * w.w});
+        }
+      }
+      if (mode & 2) {
+        float4 o = w;
+        if (a0) {
+          const cx<float> rv = r0.ld(n, c);
+          o.x = rv.re + beta0 * w.x;
+          o.z = rv.im + beta0 * w.z;
+        }
+        if (a1) {
+          const cx<float> rv = r1.ld(n, c);
+          o.y = rv.re + beta1 * w.y;
+          o.w = rv.im + beta1 * w.w;
+        }
+        if (a0 && a1) {
+          *u = o;
+        } else {
+          float* q = reinterpret_cast<float*>(u) + (a0 ? 0 : 1);
+          q[0] = a0 ? o.x : o.y;
+          q[2] = a0 ? o.z : o.w;
+        }
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- FP64 residual (reliable update)
 // A reliable update acts on the systems in ST_RU_PENDING (marked from
 // ST_NEED_RU by the host's round, so that iterations running at the same time
@@ -537,10 +603,18 @@ __global__ void __launch_bounds__(256) cg_k3(int V, RVec r, PVec p, RVec x, size
 // lets the system run again.
 // r64 = (D+m)^+ t64 with t64 = chi - (D+m) x (apply_kernel's has_sub form), so
 // r64 = b - A x for b = (D+m)^+ chi; |r64|^2, then the convergence decision.
+// An operator with a full-system criterion (full_conv) also sums its
+// conv_site over the sites; that sum, not |r64|^2, decides convergence and is
+// reported, and a system that reached its trigger without converging gets
+// the trigger tightened by the ratio the two sums showed.
+template <class Op, class = void> struct full_conv : std::false_type {};
+template <class Op> struct full_conv<Op, std::void_t<decltype(Op::kFullConv)>> : std::bool_constant<Op::kFullConv> {};
+
 template <typename Op>
 __global__ void __launch_bounds__(kTile) residual64(Geom g, Op op, typename Op::Vec t, typename Op::Vec r,
                                                   BatchParams bp, SysState* S, RedBuf rb, int* nact = nullptr) {
-  __shared__ double sm[32];
+  constexpr bool kConv = full_conv<Op>::value;
+  __shared__ double sm[(kConv ? 2 : 1) * 32];
   __shared__ int last;
   const int sys = blockIdx.y;
   if (S[sys].status != ST_RU_PENDING) return;
@@ -549,32 +623,45 @@ __global__ void __launch_bounds__(kTile) residual64(Geom g, Op op, typename Op::
   r = sys_view(r, sys, bp.sstride64);
   const double m = S[sys].mass;
   const int ntiles = (g.V + kTile - 1) / kTile;
+  RedBuf rc = rb;  // the criterion's tile sums: the second half of the partials
+  rc.partials += (size_t)gridDim.y * rb.pstride;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int n = tile * kTile + threadIdx.x;
-    double acc = 0.0;
+    double acc[2] = {0.0, 0.0};
     if (n < g.V) {
       const CV<double, Op::NC> at = op.apply(g, n, t, m, bp.r, true);
 #pragma unroll
       for (int c = 0; c < Op::NC; ++c) {
         r.st(n, c, at.c[c]);
-        acc += norm2(at.c[c]);
+        acc[0] += norm2(at.c[c]);
       }
+      if constexpr (kConv) acc[1] = op.conv_site(n, t, m, bp.r);
     }
-    put_tile(rb, sys, tile, block_sum(acc, sm));
+    if constexpr (kConv) {
+      block_sum_multi<2>(acc, sm);
+      put_tile(rb, sys, tile, acc[0]);
+      put_tile(rc, sys, tile, acc[1]);
+    } else {
+      put_tile(rb, sys, tile, block_sum(acc[0], sm));
+    }
   }
   if (block_done(rb, sys, &last, gridDim.x)) {
     const double rr = finalize_sum(rb, sys, ntiles, sm);
+    double conv = rr;
+    if constexpr (kConv) conv = finalize_sum(rc, sys, ntiles, sm);
     if (threadIdx.x == 0) {
       SysState& s = S[sys];
-      s.rr_true = rr;
+      s.rr_true = conv;
       s.n_ru += 1;
-      if (!isfinite(rr)) {
+      if (!isfinite(rr) || !isfinite(conv)) {
         s.status = ST_FAILED;
-      } else if (rr <= s.tol2) {
+      } else if (conv <= s.tol2) {
         s.status = ST_CONVERGED;
       } else if (s.iter >= s.max_iter) {
         s.status = ST_MAXITER;
       } else {
+        // (conv > tol2 here, so the new trigger is below rr)
+        if constexpr (kConv) s.trig2 = 0.8 * rr * (s.tol2 / conv);
         s.beta = (s.iter == 0) ? 0.0 : rr / s.rr_old;
         record(rb, sys, s.iter - 1, 1, s.beta);
         s.rr = rr;

@@ -17,6 +17,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace swc {
 
 // ------------------------------------------------------------------ complex
@@ -382,6 +384,33 @@ template <int NC> struct VecP32q {
     reinterpret_cast<float2*>(p + pk(n, NC / 2, c >> 1))[c & 1] = make_float2(a.re, a.im);
   }
 };
+
+// Packed FP32 vectors of pairs of systems: systems 2k and 2k+1 share pair k,
+// whose unit (site n, component c) holds (s0.re, s1.re, s0.im, s1.im), so one
+// 16-byte load gives both systems' component as the lanes of two float2
+// registers -- the operands of two-lane arithmetic over a pair of systems,
+// with no regrouping.  An accessor is one system's view: the pair's base and
+// the system's lane.  A system's share of a pair is sys_units (half a pair);
+// batches allocate whole pairs.
+template <int NC> struct VecP32x2 {
+  using unit = float4;
+  static constexpr bool kPaired = true;
+  static size_t sys_units(int V) { return (size_t)V * NC / 2; }
+  float4* p;
+  int V;  // volume (the packed addressing itself needs only n)
+  int lane = 0;
+  __device__ __forceinline__ cx<float> ld(int n, int c) const {
+    const float* q = reinterpret_cast<const float*>(p + pk(n, NC, c));
+    return {__ldg(q + lane), __ldg(q + 2 + lane)};
+  }
+  __device__ __forceinline__ void st(int n, int c, cx<float> a) const {
+    float* q = reinterpret_cast<float*>(p + pk(n, NC, c));
+    q[lane] = a.re;
+    q[2 + lane] = a.im;
+  }
+};
+template <class V, class = void> struct is_paired : std::false_type {};
+template <class V> struct is_paired<V, std::void_t<decltype(V::kPaired)>> : std::bool_constant<V::kPaired> {};
 
 // Packed two-lane FP32 arithmetic (one f32x2 instruction for two FP32
 // operations; an operand used in both lanes is broadcast).

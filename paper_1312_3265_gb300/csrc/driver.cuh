@@ -172,12 +172,16 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 // Bytes of workspace for nsys systems of NC complex components per site; pt:
 // bytes of one system's p (or t) in the inner precision's storage.
-inline size_t workspace_bytes_pt(int V, int NC, int nsys, bool mixed, size_t pt, int f64_factor = 1) {
+// pt: bytes of one system's p (or t); nsys_pt: systems p and t are allocated
+// for (the whole pairs of a paired layout)
+inline size_t workspace_bytes_pt(int V, int NC, int nsys, bool mixed, size_t pt, int f64_factor = 1,
+                                 int nsys_pt = -1) {
+  if (nsys_pt < 0) nsys_pt = nsys;
   const size_t n = (size_t)V * NC * nsys * f64_factor;
   const size_t ntiles = (size_t)(V + kTile - 1) / kTile;
   size_t b = (mixed ? 2 : 3) * align_up(sizeof(double2) * n);  // b64 only in FP64 mode
   const size_t n32 = (size_t)V * NC * nsys;  // FP32 r and x carry no scratch
-  b += mixed ? 2 * align_up(pt * nsys) + 2 * align_up(sizeof(float2) * n32) : align_up(pt * nsys);
+  b += mixed ? 2 * align_up(pt * nsys_pt) + 2 * align_up(sizeof(float2) * n32) : align_up(pt * nsys_pt);
   b += align_up(sizeof(SysState) * nsys) + align_up(sizeof(double) * 2 * kWarps * ntiles * nsys) +
        align_up(sizeof(unsigned) * 2 * nsys) + align_up(sizeof(double) * nsys) +
        align_up(sizeof(double) * 2 * kHist * nsys) + align_up(sizeof(int) * 2 * kProfSlots) +
@@ -190,12 +194,15 @@ inline size_t workspace_bytes(int V, int NC, int nsys, bool mixed) {
 }
 // f64_factor: 2 for two-pass operators, whose FP64 vectors and stencil
 // vectors p, t carry their scratch after each system's field
+template <class PVec> inline int pt_systems(int nsys) { return is_paired<PVec>::value ? (nsys + 1) & ~1 : nsys; }
 template <class PVec> inline size_t workspace_bytes_for(int V, int NC, int nsys, bool mixed, int f64_factor = 1) {
   return workspace_bytes_pt(V, NC, nsys, mixed, sizeof(typename PVec::unit) * PVec::sys_units(V) * f64_factor,
-                            f64_factor);
+                            f64_factor, pt_systems<PVec>(nsys));
 }
 
-inline Workspace carve_workspace_pt(void* base, int V, int NC, int nsys, bool mixed, size_t pt, int f64_factor = 1) {
+inline Workspace carve_workspace_pt(void* base, int V, int NC, int nsys, bool mixed, size_t pt, int f64_factor = 1,
+                                    int nsys_pt = -1) {
+  if (nsys_pt < 0) nsys_pt = nsys;
   const size_t n = (size_t)V * NC * nsys * f64_factor;
   const size_t n32 = (size_t)V * NC * nsys;
   const size_t ntiles = (size_t)(V + kTile - 1) / kTile;
@@ -210,12 +217,12 @@ inline Workspace carve_workspace_pt(void* base, int V, int NC, int nsys, bool mi
   w.r64 = (double2*)take(sizeof(double2) * n);
   w.t64 = (double2*)take(sizeof(double2) * n);
   if (mixed) {
-    w.p_lo = take(pt * nsys);
-    w.t_lo = take(pt * nsys);
+    w.p_lo = take(pt * nsys_pt);
+    w.t_lo = take(pt * nsys_pt);
     w.r32 = (float2*)take(sizeof(float2) * n32);
     w.x32 = (float2*)take(sizeof(float2) * n32);
   } else {
-    w.p_lo = take(pt * nsys);
+    w.p_lo = take(pt * nsys_pt);
     w.t_lo = w.t64;
   }
   w.S = (SysState*)take(sizeof(SysState) * nsys);
@@ -234,7 +241,7 @@ inline Workspace carve_workspace(void* base, int V, int NC, int nsys, bool mixed
 template <class PVec>
 inline Workspace carve_workspace_for(void* base, int V, int NC, int nsys, bool mixed, int f64_factor = 1) {
   return carve_workspace_pt(base, V, NC, nsys, mixed, sizeof(typename PVec::unit) * PVec::sys_units(V) * f64_factor,
-                            f64_factor);
+                            f64_factor, pt_systems<PVec>(nsys));
 }
 
 // A CGNE engine: `cap` system slots on one gauge field, advanced together.
@@ -422,9 +429,12 @@ class Engine {
 
   // Host: put slot i up for admission in the next round.  Its chi and initial
   // guess must be in the slot's buffers (in stream order) before issue().
-  void stage(int i, double mass, double tol, int max_iter) {
+  // cb2: |b|^2 of the convergence criterion of an operator that has its own
+  // (full_conv; 0: the iterated system's).
+  void stage(int i, double mass, double tol, int max_iter, double cb2 = 0.0) {
     SysState s{};
     s.tol2 = tol * tol;
+    s.cb2 = cb2;
     s.delta2 = MIXED ? delta_ * delta_ : 0.0;
     s.max_iter = max_iter;
     s.mass = mass;
@@ -660,10 +670,9 @@ class Engine {
   // the device): see the class comment.
   void admit(int na) {
     SysState* S = ws_.S;
-    using PU = typename VF::unit;
-    const int gv = grid_of((const void*)admit_clear<PU>, 256, na);
-    admit_clear<PU><<<dim3(gv, cap_), 256, 0, st_>>>(vunits_, static_cast<PU*>(ws_.p_lo), vunits_,
-                                                     MIXED ? ws_.x32 : nullptr, MIXED ? n_ : 0, S);
+    const int gv = grid_of((const void*)admit_clear<VF, NC>, 256, na);
+    admit_clear<VF, NC><<<dim3(gv, cap_), 256, 0, st_>>>(g_.V, fp_, vunits_, MIXED ? ws_.x32 : nullptr,
+                                                         MIXED ? n_ : 0, S);
     const int gn = grid_of((const void*)norm_b<NC>, kTile, na);
     if constexpr (MIXED) {
       // b = (D+m)^+ chi in the inner precision: r = p = b and |b|^2
@@ -738,8 +747,9 @@ class Engine {
   void reliable_update(int nsys, cudaStream_t sx) {
     SysState* S = ws_.S;
     const int gv = grid_of((const void*)cg_k3<TF, VR, VF, NC>, 256, nsys);
+    const int g3 = grid_of(k3_ptr(), 256, k3_rows(nsys));
     // the last x += alpha p of each system (k2 stopped it before k3)
-    cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, sx>>>(g_.V, fr_, fp_, fx_, runits_, vunits_, S, ST_RU_PENDING, 1);
+    launch_k3(g3, ST_RU_PENDING, 1, sx, nullptr);
     if constexpr (MIXED) accum_x<NC, VR><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, x_, fx_, s64_, runits_, S);
     FpSample* fs = fp_sample(2, sx);
     if (prof()) prof_count(cls_ru(), 1);
@@ -753,7 +763,7 @@ class Engine {
         g_, opd_, V64{ws_.t64}, V64{ws_.r64}, bp_, S, rbu_);
     if (fs) cudaEventRecord(fs->e1, sx);
     if constexpr (MIXED) demote_r<NC, VR><<<dim3(gv, cap_), 256, 0, sx>>>(gb_, ws_.r64, fr_, s64_, runits_, S);
-    cg_k3<TF, VR, VF, NC><<<dim3(gv, cap_), 256, 0, sx>>>(g_.V, fr_, fp_, fx_, runits_, vunits_, S, ST_JUST_UPDATED, 2);
+    launch_k3(g3, ST_JUST_UPDATED, 2, sx, nullptr);
     mark_ready<<<(cap_ + 127) / 128, 128, 0, sx>>>(cap_, S);
     launches(MIXED ? 7 : 5);
   }
@@ -799,7 +809,7 @@ class Engine {
     cls_ = groups;
     g1_ = grid_for(k1_ptr(), kTile, g_.V, groups, ntiles_);
     g2_ = grid_for(k2_ptr(), kTile, g_.V, groups, ntiles_);
-    gV_ = grid_for((const void*)cg_k3<TF, VR, VF, NC>, 256, g_.V, groups * ns_, ntiles_);
+    gV_ = grid_for(k3_ptr(), 256, g_.V, k3_rows(groups * ns_), ntiles_);
   }
 
   // Size the iteration grids for the groups holding a slot that may run in
@@ -890,8 +900,7 @@ class Engine {
       launch_k12<1>(c);
     }
     if (sample) cudaEventRecord(samples_.back().e2, ist_);
-    cg_k3<TF, VR, VF, NC><<<dim3(gV_, cap_), 256, 0, ist_>>>(g_.V, fr_, fp_, fx_, runits_, vunits_, S, ST_RUNNING, 3,
-                                                             c ? c + 2 : nullptr);
+    launch_k3(gV_, ST_RUNNING, 3, ist_, c ? c + 2 : nullptr);
     if (sample) cudaEventRecord(samples_.back().e3, ist_);
     if (count) {
       launches(4);
@@ -939,6 +948,22 @@ class Engine {
   int nneed_ = 0;  // slots in NEED_RU at the last status read
 
   // Blocks per slot of a launch that computes `nsys` of the engine's slots.
+  // k3 (x += alpha p and/or p = r + beta p, by `mode` bits) on the systems in
+  // `status`: one row of blocks per system, or per pair of systems when p
+  // is paired
+  static const void* k3_ptr() {
+    if constexpr (is_paired<VF>::value) return (const void*)cg_k3_pair<VR, VF, NC>;
+    else return (const void*)cg_k3<TF, VR, VF, NC>;
+  }
+  static int k3_rows(int nsys) { return is_paired<VF>::value ? (nsys + 1) / 2 : nsys; }
+  void launch_k3(int gx, int status, int mode, cudaStream_t s, int* nact) const {
+    if constexpr (is_paired<VF>::value)
+      cg_k3_pair<VR, VF, NC><<<dim3(gx, k3_rows(cap_)), 256, 0, s>>>(g_.V, fr_, fp_, fx_, runits_, vunits_, ws_.S,
+                                                                     cap_, status, mode, nact);
+    else
+      cg_k3<TF, VR, VF, NC><<<dim3(gx, cap_), 256, 0, s>>>(g_.V, fr_, fp_, fx_, runits_, vunits_, ws_.S, status,
+                                                           mode, nact);
+  }
   int grid_of(const void* kernel, int block, int nsys) const {
     return grid_for(kernel, block, g_.V, nsys < 1 ? 1 : (nsys > cap_ ? cap_ : nsys), ntiles_);
   }
@@ -968,7 +993,8 @@ inline int fill_info(const SysState& s, const double* hh, int precision, double 
     inf->reliable_updates = s.n_ru;
     inf->status = code;
     inf->precision = precision;
-    inf->true_rel_resid = s.b2 > 0 ? sqrt(s.rr_true / s.b2) : 0.0;
+    const double b2 = s.cb2 > 0.0 ? s.cb2 : s.b2;
+    inf->true_rel_resid = b2 > 0 ? sqrt(s.rr_true / b2) : 0.0;
     inf->seconds = secs;
     ritz_extremes(hh, s.iter < kHist ? s.iter : kHist, &inf->lambda_min, &inf->lambda_max);
   }
@@ -991,7 +1017,8 @@ int run_cgne_ws(const Geom& g, const OpD& opd, const OpF& opf, const SolveArgs& 
   const auto t0 = steady_clock::now();
   Engine<OpD, OpF, MIXED> e(g, opd, opf, a.r, a.nsys, const_cast<double2*>(a.chi), a.x, ws, hs, hs + a.nsys,
                             a.stream, nullptr, use_graphs);
-  for (int i = 0; i < a.nsys; ++i) e.stage(i, a.masses[i], a.tols ? a.tols[i] : a.tol, a.max_iter);
+  for (int i = 0; i < a.nsys; ++i)
+    e.stage(i, a.masses[i], a.tols ? a.tols[i] : a.tol, a.max_iter, a.conv_b2 ? a.conv_b2[i] : 0.0);
   const long long max_rounds = 4LL * (a.max_iter / param_chunk() + 2) + 1000;
   int rc = SW_OK;
   bool host_rounds = true;
@@ -1089,7 +1116,8 @@ int run_inner_apply(const Geom& g, const OpF& opf, const double2* in, double2* o
   const GeomBlk gb = make_blocked(g, g.shape);
   const size_t vunits = VF::sys_units(g.V), n = (size_t)g.V * NC;
   const int ntiles = (g.V + kTile - 1) / kTile, pstride = kWarps * ntiles;
-  const size_t bytes = 2 * align_up(sizeof(PU) * vunits * nsys) + align_up(sizeof(float2) * n * nsys) +
+  const int nsp = pt_systems<VF>(nsys);
+  const size_t bytes = 2 * align_up(sizeof(PU) * vunits * nsp) + align_up(sizeof(float2) * n * nsys) +
                        align_up(sizeof(SysState) * nsys) + align_up(sizeof(double) * pstride * nsys) +
                        align_up(sizeof(unsigned) * nsys);
   DevMem mem;
@@ -1100,8 +1128,8 @@ int run_inner_apply(const Geom& g, const OpF& opf, const double2* in, double2* o
     c += align_up(b);
     return p;
   };
-  const VF fp{static_cast<PU*>(take(sizeof(PU) * vunits * nsys)), g.V};
-  const VF ft{static_cast<PU*>(take(sizeof(PU) * vunits * nsys)), g.V};
+  const VF fp{static_cast<PU*>(take(sizeof(PU) * vunits * nsp)), g.V};
+  const VF ft{static_cast<PU*>(take(sizeof(PU) * vunits * nsp)), g.V};
   const VR fr{static_cast<typename VR::unit*>(take(sizeof(float2) * n * nsys)), g.V};
   const size_t runits = VR::sys_units(g.V);
   SysState* S = static_cast<SysState*>(take(sizeof(SysState) * nsys));

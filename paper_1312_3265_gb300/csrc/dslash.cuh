@@ -293,6 +293,13 @@ template <typename Vec> __device__ __forceinline__ Vec sys_at(Vec v, int s, size
   v.p += s * stride;
   return v;
 }
+// paired storage: s systems further on, the pair and the lane move together
+template <int NC> __device__ __forceinline__ VecP32x2<NC> sys_at(VecP32x2<NC> v, int s, size_t stride) {
+  const int t = v.lane + s;
+  v.p += (size_t)(t >> 1) * 2 * stride;
+  v.lane = t & 1;
+  return v;
+}
 
 template <typename T> __device__ __forceinline__ void axpy3(V3<T>& acc, T a, const V3<T>& v) {
 #pragma unroll
@@ -387,11 +394,21 @@ __device__ __forceinline__ void sw_site_multi_pair(const GG& g, int n, const G& 
     for (int i = 0; i < 3; ++i) are[q][i] = aim[q][i] = make_float2(0.f, 0.f);
   // packed vector of pair q at site y: lanes (first, second system)
   auto ldp = [&](int q, int y, float2 vre[3], float2 vim[3]) {
-    const V3<float> a = ld3<In, float>(lane0[q], y), b = ld3<In, float>(lane1[q], y);
+    if constexpr (is_paired<In>::value) {  // the pair's storage holds the lanes already
+      const In b = sys_at(in, 2 * q, stride);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      vre[j] = make_float2(a.c[j].re, b.c[j].re);
-      vim[j] = make_float2(a.c[j].im, b.c[j].im);
+      for (int j = 0; j < 3; ++j) {
+        const float4 w = __ldg(b.p + pk(y, 3, j));
+        vre[j] = make_float2(w.x, w.y);
+        vim[j] = make_float2(w.z, w.w);
+      }
+    } else {
+      const V3<float> a = ld3<In, float>(lane0[q], y), b = ld3<In, float>(lane1[q], y);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        vre[j] = make_float2(a.c[j].re, b.c[j].re);
+        vim[j] = make_float2(a.c[j].im, b.c[j].im);
+      }
     }
   };
   const float half = dagger ? -0.5f : 0.5f;

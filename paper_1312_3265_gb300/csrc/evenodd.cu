@@ -26,21 +26,27 @@
 //
 // The engine runs on a one-dimensional layout geometry of V/2 sites (the
 // packed inner-precision fields are then in half-index order); the operators
-// carry the full lattice geometry for their neighbours.  Convergence: the
-// engine stops on the FP64 normal-equation residual of the Schur system; the
-// solution is then rebuilt on the full lattice and the FP64 normal-equation
-// residual of the full system, |b - A psi| / |b| with b = (D+m)^+ chi, is
-// recomputed and reported.  A system whose full residual is above the
-// tolerance resumes the Schur solve from its solution with a proportionally
-// tighter tolerance (at most four passes); the others stop at admission with
-// their solution unchanged, so each system's result does not depend on the
-// batch (its reliable-update count includes those admission residuals).
+// carry the full lattice geometry for their neighbours.  Convergence is
+// decided on the full system: every FP64 reliable update of the Schur solve
+// also yields the full system's normal-equation residual |b - A psi| / |b|
+// (b = (D+m)^+ chi, A = (D+m)^+(D+m)) of psi = (psi_e, psi_o(psi_e)) -- see
+// WEOOp::conv_site -- and that residual, in FP64, stops the solve and is
+// reported.  The iterated Schur residual only triggers the checks: first at
+// the Schur system's own tolerance, then at the level that the ratio of the
+// two residuals seen at the last check predicts.
 #include <cmath>
 #include <vector>
 
 #include "driver.cuh"
 
 namespace swc {
+
+template <typename T> __device__ __forceinline__ Sp<T> zero_sp() {
+  Sp<T> a;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) a.s[s] = zero3<T>();
+  return a;
+}
 
 // Full index and coordinates of half-lattice site h of parity `par`.
 __device__ __forceinline__ int half_site(const Geom& g, int h, int par, int x[4]) {
@@ -50,15 +56,12 @@ __device__ __forceinline__ int half_site(const Geom& g, int h, int par, int x[4]
   return 2 * h + b;
 }
 
-// sum_mu [(r - c g_mu) U_mu(x) psi(x+mu) + (r + c g_mu) U_mu(x-mu)^+ psi(x-mu)]
+// acc + sum_mu [(r - c g_mu) U_mu(x) psi(x+mu) + (r + c g_mu) U_mu(x-mu)^+ psi(x-mu)]
 // at full site n; psi is read at the neighbours' half index (HALF) or full
 // index from `in`.  c = -1 for the adjoint.
 template <typename T, bool R1, bool HALF, typename G, typename In>
 __device__ __forceinline__ Sp<T> wilson_hops(const Geom& g, int n, const int x[4], const G& U, const In& in, T r,
-                                            bool dagger) {
-  Sp<T> acc;
-#pragma unroll
-  for (int s = 0; s < 4; ++s) acc.s[s] = zero3<T>();
+                                            bool dagger, Sp<T> acc) {
   const T sg = dagger ? T(-1) : T(1);
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
@@ -125,11 +128,35 @@ struct WEOOp {
   static constexpr bool kHalf = false;
   static constexpr bool kTwoPass = true;
   static constexpr int kNS = 1;
+  // FP32 stencil blocks per SM: 7 (72 registers) with the spin-projected
+  // hops, as the unpreconditioned operator; the full 4-spinor hops (r != 1)
+  // need 96 registers not to spill
+  static constexpr int kMinBlocks = R1 ? 7 : 5;
   using Vec = VA<12>;
   Geom full;         // the lattice
   G U;               // links of the full lattice
   size_t half_units;  // storage units of one half-lattice field (the offset of a system's scratch)
   double r;           // Wilson parameter (the pre-pass's hops)
+
+  // Convergence on the full system: with psi_o rebuilt from psi_e the full
+  // defect chi - (D+m) psi is (t, 0) with t = chi^_e - D^ psi_e, the Schur
+  // defect, so the full normal-equation residual is
+  //   |(D+m)^+ (t, 0)|^2 = M^2 |t|^2 (even sites) + |(D^+)_oe t|^2 (odd sites),
+  // and (D^+)_oe t is what the adjoint pre-pass has left in t's scratch.
+  static constexpr bool kFullConv = true;
+  __device__ __forceinline__ double conv_site(int h, const Vec& t, double m, double r) const {
+    const double M = 4.0 * r + m;
+    const Sp<T> a = ld_sp<Vec, T>(t, h), u = ld_sp<Vec, T>(scratch(t), h);
+    double e = 0.0, o = 0.0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        e += norm2(a.s[s].c[i]);
+        o += norm2(u.s[s].c[i]);
+      }
+    return M * M * e + o;
+  }
 
   __device__ __forceinline__ Vec scratch(const Vec& in) const {
     Vec u = in;
@@ -140,14 +167,20 @@ struct WEOOp {
   __device__ __forceinline__ CV<T, 12> apply(const Geom&, int h, const Vec& in, T m, T r, bool dag) const {
     int x[4];
     const int n = half_site(full, h, 0, x);
-    const Sp<T> hops = wilson_hops<T, R1, true>(full, n, x, U, scratch(in), r, dag);
-    const Sp<T> self = ld_sp<Vec, T>(in, h);
-    const T M = T(4) * r + m, c = T(0.5) / M;  // D_eo u = -1/2 hops(u)
+    // M in + c hops(u) = c (2 M^2 in + hops(u)), c = 1 / (2M), with D_eo u =
+    // -1/2 hops(u): one spinor accumulator, started from the site's own term
+    const T M = T(4) * r + m, c = T(0.5) / M, M2 = T(2) * M * M;
+    Sp<T> acc = ld_sp<Vec, T>(in, h);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) acc.s[s].c[i] = M2 * acc.s[s].c[i];
+    acc = wilson_hops<T, R1, true>(full, n, x, U, scratch(in), r, dag, acc);
     CV<T, 12> v;
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) v.c[3 * s + i] = M * self.s[s].c[i] + c * hops.s[s].c[i];
+      for (int i = 0; i < 3; ++i) v.c[3 * s + i] = c * acc.s[s].c[i];
     return v;
   }
   template <int NS, typename GG>
@@ -167,7 +200,7 @@ struct WEOOp {
   __device__ __forceinline__ void prepass_site(const Vec& in, int h, T r, bool dag) const {
     int x[4];
     const int n = half_site(full, h, 1, x);
-    const Sp<T> hops = wilson_hops<T, R1, true>(full, n, x, U, in, r, dag);
+    const Sp<T> hops = wilson_hops<T, R1, true>(full, n, x, U, in, r, dag, zero_sp<T>());
     CV<T, 12> v;
 #pragma unroll
     for (int s = 0; s < 4; ++s)
@@ -206,7 +239,7 @@ __global__ void eo_prepare(Geom g, const double2* U, const double2* chi, const d
   for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.V / 2; h += gridDim.x * blockDim.x) {
     int xc[4];
     const int n = half_site(g, h, 0, xc);
-    const Sp<double> hops = wilson_hops<double, R1, false>(g, n, xc, Ug, in, r, false);
+    const Sp<double> hops = wilson_hops<double, R1, false>(g, n, xc, Ug, in, r, false, zero_sp<double>());
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -237,7 +270,7 @@ __global__ void eo_rebuild(Geom g, const double2* U, const double2* chi, const d
 #pragma unroll
     for (int k = 0; k < 12; ++k) x[(size_t)ne * 12 + k] = x_e[(size_t)h * 12 + k];
     const int no = half_site(g, h, 1, xc);
-    const Sp<double> hops = wilson_hops<double, R1, true>(g, no, xc, Ug, in, r, false);
+    const Sp<double> hops = wilson_hops<double, R1, true>(g, no, xc, Ug, in, r, false, zero_sp<double>());
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -250,19 +283,25 @@ __global__ void eo_rebuild(Geom g, const double2* U, const double2* chi, const d
   }
 }
 
-// |v|^2 per system in a fixed order: tile sums, then one block per system.
-static __global__ void __launch_bounds__(kTile) tile_norms(const double2* v, size_t n, size_t stride, double* part,
-                                                         int ntiles) {
+// |(D+m)^+ v|^2 per tile of kTile sites, one system per blockIdx.y, into
+// part[sys * ntiles + tile] (a fixed summation order: tiles, then sum_tiles)
+template <typename W>
+__global__ void __launch_bounds__(kTile) eo_normal_norm(Geom g, W op, const double2* v, const double* mass,
+                                                      double r, double* part, int ntiles) {
   __shared__ double sm[32];
   const int sys = blockIdx.y;
-  v += sys * stride;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  const VecC64<12> in{const_cast<double2*>(v + sys * (size_t)g.V * 12)};
+  const double m = mass[sys];
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int n = tile * kTile + threadIdx.x;
     double a = 0.0;
-    for (size_t i = (size_t)t * kTile * 12 + threadIdx.x; i < std::min(n, (size_t)(t + 1) * kTile * 12);
-         i += blockDim.x)
-      a += v[i].x * v[i].x + v[i].y * v[i].y;
+    if (n < g.V) {
+      const CV<double, 12> w = op.apply(g, n, in, m, r, true);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) a += norm2(w.c[c]);
+    }
     a = block_sum(a, sm);
-    if (threadIdx.x == 0) part[(size_t)sys * ntiles + t] = a;
+    if (threadIdx.x == 0) part[(size_t)sys * ntiles + tile] = a;
   }
 }
 static __global__ void __launch_bounds__(kTile) sum_tiles(const double* part, int ntiles, double* out) {
@@ -272,48 +311,33 @@ static __global__ void __launch_bounds__(kTile) sum_tiles(const double* part, in
   a = block_sum(a, sm);
   if (threadIdx.x == 0) out[blockIdx.x] = a;
 }
-// out = a - b
-static __global__ void sub_fields(const double2* a, const double2* b, double2* out, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
-}
 
 using WEO64R1 = WEOOp<double, GaugeC64, VecC64, true>;
 using WEO64R = WEOOp<double, GaugeC64, VecC64, false>;
 using WEO32R1 = WEOOp<float, GaugeP32, VecP32q, true>;
 using WEO32R = WEOOp<float, GaugeP32, VecP32q, false>;
 
-// FP64 normal-equation residual |b - A psi| / |b| of the full system for every
-// system of the batch (b = (D+m)^+ chi, A = (D+m)^+(D+m)).
-static int full_residuals(const Geom& g, const SolveArgs& a, std::vector<double>& out) {
-  const size_t n = (size_t)g.V * 12;
+// |b|^2 = |(D+m)^+ chi|^2 of the full system for every system of the batch
+// (FP64), into host h[nsys].
+template <bool R1>
+static int full_b2(const Geom& g, const SolveArgs& a, const double* dmass, std::vector<double>& h) {
+  using W64 = WOp<double, GaugeC64, VecC64, R1>;
   const int ntiles = (g.V + kTile - 1) / kTile;
   DevMem m;
-  if (!m.alloc(sizeof(double2) * n * 4 + sizeof(double) * (size_t)ntiles * 2 + 2 * sizeof(double), a.stream))
-    return SW_ERR_OOM;
-  double2 *t = m.as<double2>(), *u = t + n, *b = u + n, *rr = b + n;
-  double* part = reinterpret_cast<double*>(rr + n);
-  double* nrm = part + 2 * (size_t)ntiles;
-  out.assign(a.nsys, 0.0);
-  for (int i = 0; i < a.nsys; ++i) {
-    const double2* chi = a.chi + (size_t)i * n;
-    const double2* x = a.x + (size_t)i * n;
-    int e;
-    if ((e = wilson_apply_f64(g, a.U, x, t, a.masses[i], a.r, 0, a.stream))) return e;  // (D+m) psi
-    sub_fields<<<sm_count() * 4, 256, 0, a.stream>>>(chi, t, u, n);                     // chi - (D+m) psi
-    if ((e = wilson_apply_f64(g, a.U, u, rr, a.masses[i], a.r, 1, a.stream))) return e;  // b - A psi
-    if ((e = wilson_apply_f64(g, a.U, chi, b, a.masses[i], a.r, 1, a.stream))) return e;  // b
-    tile_norms<<<dim3(std::min(ntiles, sm_count() * 8), 1), kTile, 0, a.stream>>>(rr, n, 0, part, ntiles);
-    tile_norms<<<dim3(std::min(ntiles, sm_count() * 8), 1), kTile, 0, a.stream>>>(b, n, 0, part + ntiles, ntiles);
-    sum_tiles<<<2, kTile, 0, a.stream>>>(part, ntiles, nrm);
-    note_launches(5);
-    double h[2] = {0.0, 0.0};
-    if (const cudaError_t ce = cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, a.stream);
-        ce != cudaSuccess)
-      return cuda_fail(ce);
-    if (const cudaError_t ce = cudaStreamSynchronize(a.stream); ce != cudaSuccess) return cuda_fail(ce);
-    out[i] = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : 0.0;
-  }
+  if (!m.alloc(sizeof(double) * ((size_t)ntiles + 1) * a.nsys, a.stream)) return SW_ERR_OOM;
+  double* part = m.as<double>();
+  double* nrm = part + (size_t)ntiles * a.nsys;
+  const int gx = std::max(1, std::min(ntiles, sm_count() * 8 / std::max(1, a.nsys)));
+  eo_normal_norm<W64><<<dim3(gx, a.nsys), kTile, 0, a.stream>>>(g, W64{GaugeC64{a.U}}, a.chi, dmass, a.r, part,
+                                                                ntiles);
+  sum_tiles<<<a.nsys, kTile, 0, a.stream>>>(part, ntiles, nrm);
+  note_launches(2);
+  h.assign(a.nsys, 0.0);
+  if (const cudaError_t ce = cudaMemcpyAsync(h.data(), nrm, sizeof(double) * a.nsys, cudaMemcpyDeviceToHost,
+                                             a.stream);
+      ce != cudaSuccess)
+    return cuda_fail(ce);
+  if (const cudaError_t ce = cudaStreamSynchronize(a.stream); ce != cudaSuccess) return cuda_fail(ce);
   return SW_OK;
 }
 
@@ -351,51 +375,19 @@ static int eo_solve(const Geom& g, const SolveArgs& a) {
     note_launches(1);
     opf = D32{g, GaugeP32{u32.as<float2>()}, VecP32q<12>::sys_units(Vh), a.r};
   }
+  std::vector<double> b2;
+  if (int e = full_b2<R1>(g, a, dmass.as<double>(), b2)) return e;
   SolveArgs ae = a;
   ae.chi = chi_e;
   ae.x = x_e;
-  std::vector<sw_solve_info> infos(a.nsys), total(a.nsys);
-  ae.infos = infos.data();
-  std::vector<double> res, tols(a.nsys, a.tol);
-  ae.tols = tols.data();
-  int rc = SW_OK;
-  for (int pass = 0; pass < 4; ++pass) {
-    rc = (a.precision == SW_PREC_F32_RELIABLE) ? run_cgne<D64, D32, true>(gh, opd, opf, ae)
-                                               : run_cgne<D64, D64, false>(gh, opd, opd, ae);
-    if (rc < 0) return rc;
-    for (int i = 0; i < a.nsys; ++i) {
-      total[i].iters += infos[i].iters;
-      total[i].reliable_updates += infos[i].reliable_updates;
-      if (pass == 0 || total[i].lambda_max == 0.0) {  // the Ritz values of the main pass
-        total[i].lambda_min = infos[i].lambda_min;
-        total[i].lambda_max = infos[i].lambda_max;
-      }
-    }
-    eo_rebuild<R1><<<dim3(gx, a.nsys), 128, 0, a.stream>>>(g, a.U, a.chi, x_e, a.x, dmass.as<double>(), a.r, s64);
-    note_launches(1);
-    if (int e = full_residuals(g, a, res)) return e;
-    bool again = false;
-    for (int i = 0; i < a.nsys; ++i)
-      if (res[i] > a.tol) {  // this system resumes from its psi_e with a tighter Schur tolerance
-        tols[i] = std::max(1e-15, tols[i] * 0.5 * a.tol / res[i]);
-        again = true;
-      }
-    // (a system already within tol is re-admitted with its own tolerance and
-    // stops at admission, x unchanged: its result does not depend on the batch)
-    if (rc != SW_OK || !again) break;
-  }
-  int worst_rc = rc;
-  for (int i = 0; i < a.nsys; ++i) {
-    if (rc == SW_OK && !(res[i] <= a.tol)) worst_rc = worst_code(worst_rc, SW_NOT_CONVERGED);
-    if (a.infos) {
-      sw_solve_info& o = a.infos[i];
-      o = total[i];
-      o.status = rc != SW_OK ? infos[i].status : (res[i] <= a.tol ? SW_OK : SW_NOT_CONVERGED);
-      o.precision = a.precision;
-      o.true_rel_resid = res[i];
-    }
-  }
-  return worst_rc;
+  ae.conv_b2 = b2.data();
+  const int rc = (a.precision == SW_PREC_F32_RELIABLE) ? run_cgne<D64, D32, true>(gh, opd, opf, ae)
+                                                      : run_cgne<D64, D64, false>(gh, opd, opd, ae);
+  if (rc < 0) return rc;
+  eo_rebuild<R1><<<dim3(gx, a.nsys), 128, 0, a.stream>>>(g, a.U, a.chi, x_e, a.x, dmass.as<double>(), a.r, s64);
+  note_launches(1);
+  if (const cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(e);
+  return rc;
 }
 
 int wilson_cgne_eo(const Geom& g, const SolveArgs& a) {

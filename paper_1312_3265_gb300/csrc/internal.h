@@ -23,6 +23,7 @@ struct SolveArgs {
   sw_solve_info* infos;
   cudaStream_t stream;
   const double* tols = nullptr;  // host [nsys]: per-system tolerances (nullptr: tol for every system)
+  const double* conv_b2 = nullptr;  // host [nsys]: |b|^2 of an operator's own convergence criterion
 };
 
 int hypercube_build_f64(const Geom& g, const double2* U, double2* W, cudaStream_t st);

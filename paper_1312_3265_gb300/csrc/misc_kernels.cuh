@@ -122,17 +122,22 @@ __global__ void demote_r(GeomBlk gb, const double2* r64, RV r32, size_t s64, siz
 }
 
 // Admission, step 1 (systems in ST_ADMIT): clear the search direction (and the
-// FP32 correction), which may hold a previous system's values.  units: the
-// storage units of one system's p (FP16 vectors include their scales).
-template <typename TP>
-__global__ void admit_clear(size_t units, TP* p, size_t pstride, float2* x32, size_t xunits, const SysState* S) {
+// FP32 correction), which may hold a previous system's values: every site of
+// p through its accessor (paired layouts hold two systems in one unit), and
+// xunits float2 of the correction.
+template <typename PVec, int NC>
+__global__ void admit_clear(int V, PVec p, size_t pstride, float2* x32, size_t xunits, const SysState* S) {
   const int sys = blockIdx.y;
   if (S[sys].status != ST_ADMIT) return;
-  p += sys * pstride;
+  p = sys_view(p, sys, pstride);
   if (x32) x32 += sys * xunits;
-  const size_t n = units > xunits ? units : xunits;
+  using T = typename std::conditional<std::is_same<typename PVec::unit, double2>::value, double, float>::type;
+  CV<T, NC> zero;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) zero.c[c] = {T(0), T(0)};
+  const size_t n = (size_t)V > xunits ? (size_t)V : xunits;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    if (i < units) p[i] = TP{};
+    if (i < (size_t)V) st_site(p, (int)i, zero);
     if (x32 && i < xunits) x32[i] = make_float2(0.f, 0.f);
   }
 }
@@ -159,7 +164,8 @@ __global__ void demote_chi(GeomBlk gb, const double2* chi, PVec out, size_t s64,
 
 // Admission, step 3: |x0|^2 of each admitted system -> S.x02, and |b|^2 ->
 // S.b2 from b (FP64 mode; b == nullptr: S.b2 already holds it, from rhs_lo);
-// S.tol2 <- S.tol2 * |b|^2 (S.tol2 holds tol^2 on entry), and the system's
+// S.tol2 <- S.tol2 * |b|^2 (S.tol2 holds tol^2 on entry; |b|^2: S.cb2 when
+// the criterion is another system's), S.trig2 <- tol^2 |b|^2, and the system's
 // next state: b = 0 -> ST_ZERO_B, x0 = 0 -> ST_ZERO_GUESS, else ST_NEED_RU
 // (non-finite b -> ST_FAILED).
 template <int NC>
@@ -200,7 +206,8 @@ __global__ void __launch_bounds__(kTile) norm_b(int V, const double2* b, const d
       if (b) st.b2 = s;
       const double b2 = st.b2;
       st.x02 = sx;
-      st.tol2 *= b2;
+      st.trig2 = st.tol2 * b2;
+      st.tol2 *= st.cb2 > 0.0 ? st.cb2 : b2;
       if (!isfinite(b2) || !isfinite(sx)) st.status = ST_FAILED;
       else if (b2 == 0.0) st.status = ST_ZERO_B;
       else if (sx == 0.0) st.status = ST_ZERO_GUESS;

@@ -99,7 +99,7 @@ struct EngineImpl : EngineBase {
 };
 
 using SW64 = SWOp<double, GaugeC64, TransC64, VecC64>;
-using SW32 = SWOp<float, GaugeP32, TransP32, VecP32>;
+using SW32 = SWOp<float, GaugeP32, TransP32, VecP32x2>;
 using SW16 = SWOp<float, GaugeP16, TransP16, VecP16>;
 template <bool R1> using W64 = WOp<double, GaugeC64, VecC64, R1>;
 template <bool R1> using W32 = WOp<float, GaugeP32, VecP32q, R1>;

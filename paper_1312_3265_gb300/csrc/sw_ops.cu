@@ -4,7 +4,7 @@
 namespace swc {
 
 using SW64 = SWOp<double, GaugeC64, TransC64, VecC64>;
-using SW32 = SWOp<float, GaugeP32, TransP32, VecP32>;
+using SW32 = SWOp<float, GaugeP32, TransP32, VecP32x2>;
 using SW16 = SWOp<float, GaugeP16, TransP16, VecP16>;
 
 int sw_apply_f64(const Geom& g, const double2* U, const double2* W, const double2* in, double2* out,

@@ -554,9 +554,11 @@ def test_persistent_graph_is_bitwise_host_rounds(sw, op, prec):
 def test_even_odd_wilson_matches_the_oracle(sw, prec, case):
     """Wilson CGNE on the even-odd Schur complement (SW_OP_WILSON_EVEN_ODD):
     the same solution as the oracle's unpreconditioned CG (1e-6 relative), the
-    full system's FP64 true residual <= tol checked by the oracle's operator,
-    and fewer CG iterations than the unpreconditioned solve of the same system;
-    a batch of three masses gives each system's result bit for bit as alone."""
+    full system's FP64 true residual <= tol checked by the oracle's operator
+    (and reported as the oracle computes it), fewer CG iterations than the
+    unpreconditioned solve of the same system, initial guesses (exact: no
+    iteration; perturbed: converges again); a batch of three masses gives each
+    system's result bit for bit as alone."""
     import torch
     if case == "r1":
         P = Problem(sw, (6, 4, 4, 6), sw.SW_OP_WILSON, 16, ls.PLAQ_EPS, 0.1, apbc=True)
@@ -572,6 +574,14 @@ def test_even_odd_wilson_matches_the_oracle(sw, prec, case):
     assert abs(info.true_rel_resid - P.true_resid(chi, x)) <= 1e-13 + 1e-3 * info.true_rel_resid
     assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-6
     assert info.iters < info_un.iters, (info.iters, info_un.iters)
+    # an initial guess: the oracle's solution stops at admission; a perturbed
+    # one converges again to the full system's tolerance
+    x0, info0 = P.solve(sw, chi, 1e-9, prec, x0=ref)
+    assert info0.status == sw.SW_OK and info0.iters == 0 and P.true_resid(chi, x0) <= 1.01e-9
+    noise = 1e-3 * np.linalg.norm(ref) / np.sqrt(ref.size) * ls.gaussian_source(P.dims, 12, 141).reshape(-1)
+    x1, info1 = P.solve(sw, chi, 1e-9, prec, x0=ref + noise)
+    assert info1.status == sw.SW_OK and 0 < info1.iters and P.true_resid(chi, x1) <= 1.01e-9
+    assert abs(info1.true_rel_resid - P.true_resid(chi, x1)) <= 1e-13 + 1e-3 * info1.true_rel_resid
     # batch of three masses = each alone
     masses = [0.05, 0.1, 0.2]
     chis = np.stack([ls.gaussian_source(P.dims, 12, 150 + i).reshape(-1, 4, 3) for i in range(3)])
