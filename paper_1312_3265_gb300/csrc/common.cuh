@@ -442,6 +442,23 @@ __device__ __forceinline__ cx<float> h2c(__half2 h) {
   return {f.x, f.y};
 }
 
+// row 2 of an SU(3) matrix from rows 0 and 1: conj(row0 x row1)
+__device__ __forceinline__ void su3_third_row(M3<float>& M) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int a = (j + 1) % 3, b = (j + 2) % 3;
+    // c = row0_a row1_b - row0_b row1_a, as fused multiply-adds
+    float re = M.e[0][a].re * M.e[1][b].re, im = M.e[0][a].re * M.e[1][b].im;
+    re = fma(-M.e[0][a].im, M.e[1][b].im, re);
+    im = fma(M.e[0][a].im, M.e[1][b].re, im);
+    re = fma(-M.e[0][b].re, M.e[1][a].re, re);
+    re = fma(M.e[0][b].im, M.e[1][a].im, re);
+    im = fma(-M.e[0][b].re, M.e[1][a].im, im);
+    im = fma(-M.e[0][b].im, M.e[1][a].re, im);
+    M.e[2][j] = {re, -im};
+  }
+}
+
 struct GaugeP16 {
   static constexpr int kBytes = 4 * 6 * 4;
   static constexpr const char* kPrec = "f16";
@@ -453,20 +470,7 @@ struct GaugeP16 {
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) M.e[i][j] = h2c(__ldg(q + (i * 3 + j) * 16));
-    // row 2 = conj(row0 x row1)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int a = (j + 1) % 3, b = (j + 2) % 3;
-      // c = row0_a row1_b - row0_b row1_a, as fused multiply-adds
-      float re = M.e[0][a].re * M.e[1][b].re, im = M.e[0][a].re * M.e[1][b].im;
-      re = fma(-M.e[0][a].im, M.e[1][b].im, re);
-      im = fma(M.e[0][a].im, M.e[1][b].re, im);
-      re = fma(-M.e[0][b].re, M.e[1][a].re, re);
-      re = fma(M.e[0][b].im, M.e[1][a].im, re);
-      im = fma(-M.e[0][b].re, M.e[1][a].im, im);
-      im = fma(-M.e[0][b].im, M.e[1][a].re, im);
-      M.e[2][j] = {re, -im};
-    }
+    su3_third_row(M);
     return M;
   }
 };
