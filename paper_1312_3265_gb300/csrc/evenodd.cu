@@ -283,20 +283,30 @@ __global__ void eo_rebuild(Geom g, const double2* U, const double2* chi, const d
   }
 }
 
+// Canonical FP64 vectors read as FP32 (the inner precision's view of chi).
+template <int NC> struct VecC64as32 {
+  double2* p;
+  __device__ __forceinline__ cx<float> ld(int n, int c) const {
+    const double2 v = __ldg(p + (size_t)n * NC + c);
+    return {(float)v.x, (float)v.y};
+  }
+};
+
 // |(D+m)^+ v|^2 per tile of kTile sites, one system per blockIdx.y, into
-// part[sys * ntiles + tile] (a fixed summation order: tiles, then sum_tiles)
+// part[sys * ntiles + tile] (a fixed summation order: tiles, then sum_tiles);
+// v canonical FP64, the operator FP64 or the inner precision's
 template <typename W>
 __global__ void __launch_bounds__(kTile) eo_normal_norm(Geom g, W op, const double2* v, const double* mass,
                                                       double r, double* part, int ntiles) {
   __shared__ double sm[32];
   const int sys = blockIdx.y;
-  const VecC64<12> in{const_cast<double2*>(v + sys * (size_t)g.V * 12)};
+  const typename W::Vec in{const_cast<double2*>(v + sys * (size_t)g.V * 12)};
   const double m = mass[sys];
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int n = tile * kTile + threadIdx.x;
     double a = 0.0;
     if (n < g.V) {
-      const CV<double, 12> w = op.apply(g, n, in, m, r, true);
+      const auto w = op.apply(g, n, in, m, r, true);
 #pragma unroll
       for (int c = 0; c < 12; ++c) a += norm2(w.c[c]);
     }
@@ -317,19 +327,27 @@ using WEO64R = WEOOp<double, GaugeC64, VecC64, false>;
 using WEO32R1 = WEOOp<float, GaugeP32, VecP32q, true>;
 using WEO32R = WEOOp<float, GaugeP32, VecP32q, false>;
 
-// |b|^2 = |(D+m)^+ chi|^2 of the full system for every system of the batch
-// (FP64), into host h[nsys].
+// |b|^2 = |(D+m)^+ chi|^2 of the full system for every system of the batch,
+// into host h[nsys]: with the FP64 operator, or (u32: the packed FP32 links,
+// lexicographic order) with the FP32 one -- the precision in which the
+// mixed modes take every other system's |b|^2 (the tolerance's scale).
 template <bool R1>
-static int full_b2(const Geom& g, const SolveArgs& a, const double* dmass, std::vector<double>& h) {
+static int full_b2(const Geom& g, const SolveArgs& a, const double* dmass, const float2* u32,
+                   std::vector<double>& h) {
   using W64 = WOp<double, GaugeC64, VecC64, R1>;
+  using W32 = WOp<float, GaugeP32, VecC64as32, R1>;
   const int ntiles = (g.V + kTile - 1) / kTile;
   DevMem m;
   if (!m.alloc(sizeof(double) * ((size_t)ntiles + 1) * a.nsys, a.stream)) return SW_ERR_OOM;
   double* part = m.as<double>();
   double* nrm = part + (size_t)ntiles * a.nsys;
   const int gx = std::max(1, std::min(ntiles, sm_count() * 8 / std::max(1, a.nsys)));
-  eo_normal_norm<W64><<<dim3(gx, a.nsys), kTile, 0, a.stream>>>(g, W64{GaugeC64{a.U}}, a.chi, dmass, a.r, part,
-                                                                ntiles);
+  if (u32)
+    eo_normal_norm<W32><<<dim3(gx, a.nsys), kTile, 0, a.stream>>>(g, W32{GaugeP32{u32}}, a.chi, dmass, a.r, part,
+                                                                  ntiles);
+  else
+    eo_normal_norm<W64><<<dim3(gx, a.nsys), kTile, 0, a.stream>>>(g, W64{GaugeC64{a.U}}, a.chi, dmass, a.r, part,
+                                                                  ntiles);
   sum_tiles<<<a.nsys, kTile, 0, a.stream>>>(part, ntiles, nrm);
   note_launches(2);
   h.assign(a.nsys, 0.0);
@@ -376,7 +394,9 @@ static int eo_solve(const Geom& g, const SolveArgs& a) {
     opf = D32{g, GaugeP32{u32.as<float2>()}, VecP32q<12>::sys_units(Vh), a.r};
   }
   std::vector<double> b2;
-  if (int e = full_b2<R1>(g, a, dmass.as<double>(), b2)) return e;
+  if (int e = full_b2<R1>(g, a, dmass.as<double>(), a.precision == SW_PREC_F32_RELIABLE ? u32.as<float2>() : nullptr,
+                         b2))
+    return e;
   SolveArgs ae = a;
   ae.chi = chi_e;
   ae.x = x_e;

@@ -201,3 +201,53 @@ def test_transport_of_a_pure_gauge_is_path_independent(dims):
     for k, s in enumerate(hypercube_vectors(False)):
         want = Om @ np.conj(np.swapaxes(lat.shift_links(Om, list(s)), -1, -2))
         assert np.abs(W16[k] - want).max() < 1e-13, s
+
+
+@pytest.mark.parametrize("apbc", [False, True])
+def test_wilson_even_odd_schur_reading(apbc):
+    """The even-odd Schur reading of the Wilson operator (the basis of
+    SW_OP_WILSON_EVEN_ODD), from the oracle's operator alone: hops join
+    opposite parities only, so the even part of D (v_e, 0) is M v_e (M = 4r +
+    m); psi_e from D^ psi_e = chi^_e (chi^_e = chi_e - D_eo chi_o / M, D^ = M -
+    D_eo D_oe / M, dense solve) and psi_o = (chi_o - D_oe psi_e) / M solve
+    D psi = chi; for any psi_e the defect of (psi_e, psi_o(psi_e)) is (chi^_e -
+    D^ psi_e, 0), and |D^+(defect)|^2 = M^2 |t|^2 + |(D^+)_oe t|^2."""
+    lat, U = setup((4, 2, 2, 4), apbc, seed=21)
+    even = ((sum(lat.x) % 2) == 0)[..., None, None]
+    for r in (1.0, 0.7):
+        m = 0.15
+        M = 4 * r + m
+        D = lambda v, dag=False: ops.wilson_dslash(lat, U, v, m, r, dagger=dag)
+        ev = lambda v: np.where(even, v, 0)
+        od = lambda v: np.where(even, 0, v)
+        v = ev(rand_field(lat, (4, 3), 30))
+        assert np.abs(ev(D(v)) - M * v).max() < 1e-13
+        assert np.abs(ev(D(v, True)) - M * v).max() < 1e-13
+        # D_eo u = even part of D (0, u_o); D_oe v = odd part of D (v_e, 0)
+        Deo = lambda u: ev(D(od(u)))
+        Doe = lambda w: od(D(ev(w)))
+        Dhat = lambda w: M * ev(w) - Deo(Doe(w)) / M
+        chi = rand_field(lat, (4, 3), 31)
+        chih = ev(chi) - Deo(chi) / M
+        # dense D^ on the even sites
+        idx = np.flatnonzero(np.broadcast_to(even, lat.shape + (4, 3)).reshape(-1))
+        n = idx.size
+        A = np.zeros((n, n), dtype=complex)
+        for k in range(n):
+            e = np.zeros(lat.shape + (4, 3), dtype=complex).reshape(-1)
+            e[idx[k]] = 1.0
+            A[:, k] = Dhat(e.reshape(lat.shape + (4, 3))).reshape(-1)[idx]
+        psie = np.zeros(lat.shape + (4, 3), dtype=complex).reshape(-1)
+        psie[idx] = np.linalg.solve(A, chih.reshape(-1)[idx])
+        psie = psie.reshape(lat.shape + (4, 3))
+        psi = psie + (od(chi) - Doe(psie)) / M
+        assert np.abs(D(psi) - chi).max() < 1e-11
+        # defect of an arbitrary psi_e with its psi_o rebuilt
+        w = ev(rand_field(lat, (4, 3), 32))
+        psi = w + (od(chi) - Doe(w)) / M
+        t = chih - Dhat(w)
+        defect = chi - D(psi)
+        assert np.abs(defect - t).max() < 1e-12
+        lhs = np.vdot(D(defect, True), D(defect, True)).real
+        rhs = M * M * np.vdot(t, t).real + np.vdot(od(D(t, True)), od(D(t, True))).real
+        assert abs(lhs - rhs) <= 1e-12 * lhs
