@@ -59,9 +59,10 @@ NCU_TRAFFIC = {
     # profiles/ncu_sw_k1k2k3_fp32_16x16x16x32_12sys.md
     "sw.k1.f32": {"bytes": 186.1e6, "algorithmic": 188.7e6, "systems": 12},
     "sw.k2.f32": {"bytes": 224.3e6, "algorithmic": 226.5e6, "systems": 12},
-    # profiles/ncu_wilson_k1k2k3_fp32_16x16x16x32_12sys.md
-    "wilson.k1.f32": {"bytes": 323.6e6, "algorithmic": 339.7e6, "systems": 12},
-    "wilson.k2.f32": {"bytes": 477.4e6, "algorithmic": 490.7e6, "systems": 12},
+    # profiles/ncu_wilson_k1k2k3_fp32_16x16x16x32_12sys.md (the 48-system section:
+    # the headline's batch, every system running)
+    "wilson.k1.f32": {"bytes": 1628.7e6, "algorithmic": 1245.7e6, "systems": 48},
+    "wilson.k2.f32": {"bytes": 2329.6e6, "algorithmic": 1849.7e6, "systems": 48},
 }
 
 # FP64 peak of a GB300 when no measurement is given (nominal 1.25 TFLOP/s; the
