@@ -88,8 +88,7 @@ enum { SW_OP_STAGGERED_WILSON = 0, SW_OP_WILSON = 1, SW_OP_WILSON_EVEN_ODD = 2 }
  * residual b - A x in FP64; dot products accumulate in FP64, and convergence
  * is always decided on an FP64 residual.  (The scale |b| of the relative
  * residual is taken from the inner precision's b = (D+m)^+ chi with FP64
- * accumulation, so it carries the inner precision's relative rounding,
- * about 1e-7 in FP32.)
+ * accumulation, so it is exact only to the inner precision's rounding.)
  * SW_PREC_F16_RELIABLE: as F32, with FP16 storage of the links (first two
  * rows, the third rebuilt as conj(row0 x row1): U must be SU(3) to 1e-5, else
  * SW_ERR_ARG), of the hypercube transports, and of the stencil vectors p and
