@@ -148,7 +148,12 @@ struct SWOp {
   }
 };
 
-template <typename T, typename G, template <int> class VA, bool R1>
+// LEAN: the spin-projected FP32 stencil in its lean form (wilson_site_lean) at
+// 8 blocks per SM (64 registers), for lattices whose FP32 links stay in L2;
+// beyond that the default form at 7 blocks, whose longer-lived loads keep
+// more memory requests in flight per thread, is faster.  Both compute the
+// same operations in the same order: their results are bit-identical.
+template <typename T, typename G, template <int> class VA, bool R1, bool LEAN = false>
 struct WOp {
   static constexpr int NC = 12;
   static constexpr int kMats = 4;   // 4 links per site
@@ -158,6 +163,9 @@ struct WOp {
   static constexpr double kFlops = 1392.0;  // per site and application (Eq. 4)
   static constexpr bool kHalf = std::is_same<G, GaugeP16>::value;  // FP16 storage
   static constexpr int kNS = 1;
+  static constexpr bool kLean =
+      LEAN && R1 && std::is_same<G, GaugeP32>::value && std::is_same<VA<12>, VecP32q<12>>::value;
+  static constexpr int kMinBlocks = kLean ? 8 : 0;
   using Vec = VA<12>;
 
   G U;
@@ -174,7 +182,10 @@ struct WOp {
   __device__ __forceinline__ void apply_multi(const GG& g, int n, const Vec& in, size_t stride, unsigned act,
                                               const T* m, T r, bool dag, CV<T, 12>* out) const {
     Sp<T> o[NS];
-    wilson_site_multi<T, R1, NS>(g, n, U, in, stride, act, m, r, dag, o);
+    if constexpr (NS == 1 && kLean)
+      wilson_site_lean(g, n, U, in, m[0], dag, o[0]);
+    else
+      wilson_site_multi<T, R1, NS>(g, n, U, in, stride, act, m, r, dag, o);
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -364,8 +375,9 @@ __device__ __forceinline__ unsigned running_mask(const SysState* S, int sys0, in
 // Minimum resident blocks per SM requested from the compiler for the
 // inner-precision stencil kernels (caps their registers): they are
 // latency-bound, so more resident warps hide more of the L2 latency
-// (FP32 storage: staggered Wilson 8 blocks = 64 registers, Wilson 7 = 72,
-// chosen from the spill counts of ptxas and GB300 timings).  The FP16-storage
+// (FP32 storage: staggered Wilson 9 blocks = 56 registers, Wilson 7 = 72 --
+// 8 = 64 for its lean form on lattices whose links stay in L2 -- chosen from
+// the spill counts of ptxas and GB300 timings).  The FP16-storage
 // stencils also convert and scale every value they load: at 7 blocks they
 // spill about 0.5 KB per thread (Wilson) and take 5 blocks (96 registers,
 // no spills), staggered Wilson 7.  FP64 kernels are ALU-bound: no cap.
@@ -376,7 +388,7 @@ template <typename T, typename Op> constexpr int stencil_min_blocks() {
   if (sizeof(T) != 4) return 1;
   if (op_min_blocks<Op>::value > 0) return op_min_blocks<Op>::value;  // the operator's own occupancy target
   if (Op::kHalf) return Op::NC == 3 ? 7 : 5;
-  return Op::NC == 3 ? 8 : 7;
+  return Op::NC == 3 ? 9 : 7;
 }
 
 template <typename T, typename Op, int NS, typename GG>

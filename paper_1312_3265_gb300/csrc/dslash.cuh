@@ -509,6 +509,134 @@ __device__ __forceinline__ void sw_site_multi_pair(const GG& g, int n, const G& 
   }
 }
 
+// ---- lean form of the spin-projected FP32 Wilson site (one system per thread)
+// The same arithmetic as wilson_site_multi at r = 1, in an order that keeps
+// fewer values live: each projected row h0, h1 is formed from the two spins
+// it needs (the float4 units that hold them; a unit's other half is kept for
+// the second row), and the transported rows are formed one colour at a time,
+// from one row (or column) of the link, and reconstructed into the
+// accumulator at once.
+__device__ __forceinline__ cx<float> lo2(float4 v) { return {v.x, v.y}; }
+__device__ __forceinline__ cx<float> hi2(float4 v) { return {v.z, v.w}; }
+
+template <int MU>
+__device__ __forceinline__ void wproject_rows(const float4* b, float c, V3<float>& h0, V3<float>& h1) {
+  // component k = 3 spin + colour sits in unit k/2, half k%2
+  if constexpr (MU < 2) {  // rows from spins (0, 3) and (1, 2)
+    const float4 u0 = __ldg(b), u1 = __ldg(b + 16), u4 = __ldg(b + 64), u5 = __ldg(b + 80);
+    const cx<float> s0[3] = {lo2(u0), hi2(u0), lo2(u1)}, s3[3] = {hi2(u4), lo2(u5), hi2(u5)};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) h0.c[i] = MU == 0 ? s0[i] - c * times_i(s3[i]) : s0[i] + c * s3[i];
+    const cx<float> c3 = hi2(u1), c8 = lo2(u4);
+    const float4 u2 = __ldg(b + 32), u3 = __ldg(b + 48);
+    const cx<float> s1[3] = {c3, lo2(u2), hi2(u2)}, s2[3] = {lo2(u3), hi2(u3), c8};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) h1.c[i] = MU == 0 ? s1[i] - c * times_i(s2[i]) : s1[i] - c * s2[i];
+  } else {  // rows from spins (0, 2) and (1, 3)
+    const float4 u0 = __ldg(b), u1 = __ldg(b + 16), u3 = __ldg(b + 48), u4 = __ldg(b + 64);
+    const cx<float> s0[3] = {lo2(u0), hi2(u0), lo2(u1)}, s2[3] = {lo2(u3), hi2(u3), lo2(u4)};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) h0.c[i] = MU == 2 ? s0[i] - c * times_i(s2[i]) : s0[i] - c * s2[i];
+    const cx<float> c3 = hi2(u1), c9 = hi2(u4);
+    const float4 u2 = __ldg(b + 32), u5 = __ldg(b + 80);
+    const cx<float> s1[3] = {c3, lo2(u2), hi2(u2)}, s3[3] = {c9, lo2(u5), hi2(u5)};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) h1.c[i] = MU == 2 ? s1[i] + c * times_i(s3[i]) : s1[i] - c * s3[i];
+  }
+}
+
+// acc += (1 - c g_mu) reconstructed from row i of the transported rows: one
+// link row (fwd) or column (bwd, the adjoint) at a time
+template <int MU, bool BWD>
+__device__ __forceinline__ void whop_rows(const float2* q, float c, bool flip, const V3<float>& h0,
+                                          const V3<float>& h1, Sp<float>& acc) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cx<float> m[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float2 e = __ldg(q + (BWD ? (j * 3 + i) : (i * 3 + j)) * 16);
+      m[j] = {e.x, e.y};
+    }
+    float r0, i0, r1, i1;
+    if constexpr (!BWD) {  // the products of mv
+      r0 = m[0].re * h0.c[0].re, i0 = m[0].re * h0.c[0].im;
+      r0 = fma(-m[0].im, h0.c[0].im, r0);
+      i0 = fma(m[0].im, h0.c[0].re, i0);
+      cmac(r0, i0, m[1], h0.c[1]);
+      cmac(r0, i0, m[2], h0.c[2]);
+      r1 = m[0].re * h1.c[0].re, i1 = m[0].re * h1.c[0].im;
+      r1 = fma(-m[0].im, h1.c[0].im, r1);
+      i1 = fma(m[0].im, h1.c[0].re, i1);
+      cmac(r1, i1, m[1], h1.c[1]);
+      cmac(r1, i1, m[2], h1.c[2]);
+    } else {  // the products of mdv
+      r0 = m[0].re * h0.c[0].re, i0 = m[0].re * h0.c[0].im;
+      r0 = fma(m[0].im, h0.c[0].im, r0);
+      i0 = fma(-m[0].im, h0.c[0].re, i0);
+      cjmac(r0, i0, m[1], h0.c[1]);
+      cjmac(r0, i0, m[2], h0.c[2]);
+      r1 = m[0].re * h1.c[0].re, i1 = m[0].re * h1.c[0].im;
+      r1 = fma(m[0].im, h1.c[0].im, r1);
+      i1 = fma(-m[0].im, h1.c[0].re, i1);
+      cjmac(r1, i1, m[1], h1.c[1]);
+      cjmac(r1, i1, m[2], h1.c[2]);
+    }
+    cx<float> b0 = {r0, i0}, b1 = {r1, i1};
+    if (flip) {
+      b0 = {-b0.re, -b0.im};
+      b1 = {-b1.re, -b1.im};
+    }
+    acc.s[0].c[i] = acc.s[0].c[i] + b0;
+    acc.s[1].c[i] = acc.s[1].c[i] + b1;
+    if constexpr (MU == 0) {
+      acc.s[2].c[i] = acc.s[2].c[i] + c * times_i(b1);
+      acc.s[3].c[i] = acc.s[3].c[i] + c * times_i(b0);
+    } else if constexpr (MU == 1) {
+      acc.s[2].c[i] = acc.s[2].c[i] - c * b1;
+      acc.s[3].c[i] = acc.s[3].c[i] + c * b0;
+    } else if constexpr (MU == 2) {
+      acc.s[2].c[i] = acc.s[2].c[i] + c * times_i(b0);
+      acc.s[3].c[i] = acc.s[3].c[i] - c * times_i(b1);
+    } else {
+      acc.s[2].c[i] = acc.s[2].c[i] - c * b0;
+      acc.s[3].c[i] = acc.s[3].c[i] - c * b1;
+    }
+  }
+}
+
+template <int MU, typename GG>
+__device__ __forceinline__ void whop_lean(const GG& g, int n, const int x[4], const GaugeP32& U,
+                                          const VecP32q<12>& in, float sg, Sp<float>& acc) {
+  const int nf = hop(g, n, x, MU, +1), nb = hop(g, n, x, MU, -1);
+  V3<float> h0, h1;
+  wproject_rows<MU>(in.p + pk(nf, 6, 0), sg, h0, h1);
+  whop_rows<MU, false>(U.p + pk(n, 36, MU * 9), sg, MU == 3 && bc_flip(g, x, +1), h0, h1, acc);
+  wproject_rows<MU>(in.p + pk(nb, 6, 0), -sg, h0, h1);
+  whop_rows<MU, true>(U.p + pk(nb, 36, MU * 9), -sg, MU == 3 && bc_flip(g, x, -1), h0, h1, acc);
+}
+
+template <typename GG>
+__device__ __forceinline__ void wilson_site_lean(const GG& g, int n, const GaugeP32& U, const VecP32q<12>& in,
+                                                 float mass, bool dagger, Sp<float>& out) {
+  int x[4];
+  coords(g, n, x);
+  Sp<float> acc;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) acc.s[s] = zero3<float>();
+  const float sg = dagger ? -1.f : 1.f;
+  whop_lean<0>(g, n, x, U, in, sg, acc);
+  whop_lean<1>(g, n, x, U, in, sg, acc);
+  whop_lean<2>(g, n, x, U, in, sg, acc);
+  whop_lean<3>(g, n, x, U, in, sg, acc);
+  const Sp<float> self = ld_sp<VecP32q<12>, float>(in, n);
+  const float diag = 4.f + mass;  // 4r + m at r = 1
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out.s[k].c[i] = diag * self.s[k].c[i] - 0.5f * acc.s[k].c[i];
+}
+
 template <typename T, bool R1, int NS, typename G, typename In, typename GG>
 __device__ __forceinline__ void wilson_site_multi(const GG& g, int n, const G& U, const In& in, size_t stride,
                                                   unsigned act, const T* mass, T r, bool dagger, Sp<T>* out) {

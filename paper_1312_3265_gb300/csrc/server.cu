@@ -103,6 +103,7 @@ using SW32 = SWOp<float, GaugeP32, TransP32, VecP32x2>;
 using SW16 = SWOp<float, GaugeP16, TransP16, VecP16>;
 template <bool R1> using W64 = WOp<double, GaugeC64, VecC64, R1>;
 template <bool R1> using W32 = WOp<float, GaugeP32, VecP32q, R1>;
+using W32L = WOp<float, GaugeP32, VecP32q, true, true>;  // the lean r = 1 form (wilson_lean lattices)
 template <bool R1> using W16 = WOp<float, GaugeP16, VecP16, R1>;
 
 // Allocate on `st`, remembering the block for the engine's destructor.
@@ -240,18 +241,23 @@ static int make_engine(const Geom& g, int op, const double2* U, double r, int pr
         *f = W16<R1>{GaugeP16{u16}};
         return (int)SW_OK;
       }, out);
-    return build_engine<W64<R1>, W32<R1>, true>(g, cap, r, prec,
-                                                [&](auto& owned, cudaStream_t st, W64<R1>* d, W32<R1>* f) {
-      double2* Ur;
-      if (int e = copy_links(owned, st, &Ur)) return e;
-      float2* u32 = (float2*)own(owned, V * 288, st);
-      if (!u32) return (int)SW_ERR_OOM;
-      pack_mats_p32<<<gp, 256, 0, st>>>(make_blocked(g, g.shape), 4, Ur, u32);
-      note_launches(1);
-      *d = W64<R1>{GaugeC64{Ur}};
-      *f = W32<R1>{GaugeP32{u32}};
-      return (int)SW_OK;
-    }, out);
+    auto f32 = [&](auto tag) -> int {  // tag: the FP32 operator type
+      using OF = typename decltype(tag)::type;
+      return build_engine<W64<R1>, OF, true>(g, cap, r, prec, [&](auto& owned, cudaStream_t st, W64<R1>* d, OF* f) {
+        double2* Ur;
+        if (int e = copy_links(owned, st, &Ur)) return e;
+        float2* u32 = (float2*)own(owned, V * 288, st);
+        if (!u32) return (int)SW_ERR_OOM;
+        pack_mats_p32<<<gp, 256, 0, st>>>(make_blocked(g, g.shape), 4, Ur, u32);
+        note_launches(1);
+        *d = W64<R1>{GaugeC64{Ur}};
+        *f = OF{GaugeP32{u32}};
+        return (int)SW_OK;
+      }, out);
+    };
+    if constexpr (R1)
+      if (wilson_lean(g)) return f32(std::common_type<W32L>{});
+    return f32(std::common_type<W32<R1>>{});
   };
   return r == 1.0 ? wilson(std::true_type{}) : wilson(std::false_type{});
 }

@@ -6,6 +6,7 @@ namespace swc {
 
 template <bool R1> using W64 = WOp<double, GaugeC64, VecC64, R1>;
 template <bool R1> using W32 = WOp<float, GaugeP32, VecP32q, R1>;
+using W32L = WOp<float, GaugeP32, VecP32q, true, true>;  // the lean r = 1 form
 template <bool R1> using W16 = WOp<float, GaugeP16, VecP16, R1>;
 
 template <bool R1>
@@ -36,6 +37,8 @@ static int cgne_impl(const Geom& g, const SolveArgs& a) {
     if (!mu.alloc(sizeof(float2) * 36 * (size_t)g.V, a.stream)) return SW_ERR_OOM;
     pack_mats_p32<<<sm_count() * 8, 256, 0, a.stream>>>(make_blocked(g, g.shape), 4, a.U, mu.as<float2>());
     note_launches(1);
+    if constexpr (R1)
+      if (wilson_lean(g)) return run_cgne<W64<R1>, W32L, true>(g, opd, W32L{GaugeP32{mu.as<float2>()}}, a);
     const W32<R1> opf{GaugeP32{mu.as<float2>()}};
     return run_cgne<W64<R1>, W32<R1>, true>(g, opd, opf, a);
   }
@@ -64,6 +67,8 @@ static int inner_impl(const Geom& g, const double2* U, const double2* in, double
     if (!mu.alloc(sizeof(float2) * 36 * (size_t)g.V, st)) return SW_ERR_OOM;
     pack_mats_p32<<<sm_count() * 8, 256, 0, st>>>(make_blocked(g, g.shape), 4, U, mu.as<float2>());
     note_launches(1);
+    if constexpr (R1)
+      if (wilson_lean(g)) return run_inner_apply(g, W32L{GaugeP32{mu.as<float2>()}}, in, out, nsys, masses, r, dagger, st);
     return run_inner_apply(g, W32<R1>{GaugeP32{mu.as<float2>()}}, in, out, nsys, masses, r, dagger, st);
   }
   if (precision == SW_PREC_F16_RELIABLE) {
