@@ -57,12 +57,12 @@ ITERS_TABLE = {"sw": {0.02: 41.0, 0.05: 39.0, 0.1: 36.9, 0.2: 32.0},
 # with the systems computed).  Entries are removed when the kernel changes.
 NCU_TRAFFIC = {
     # profiles/ncu_sw_k1k2k3_fp32_16x16x16x32_12sys.md
-    "sw.k1.f32": {"bytes": 186.1e6, "algorithmic": 188.7e6, "systems": 12},
-    "sw.k2.f32": {"bytes": 224.3e6, "algorithmic": 226.5e6, "systems": 12},
+    "sw.k1.f32": {"bytes": 195.3e6, "algorithmic": 188.7e6, "systems": 12},
+    "sw.k2.f32": {"bytes": 236.8e6, "algorithmic": 226.5e6, "systems": 12},
     # profiles/ncu_wilson_k1k2k3_fp32_16x16x16x32_12sys.md (the 48-system section:
     # the headline's batch, every system running)
-    "wilson.k1.f32": {"bytes": 1628.7e6, "algorithmic": 1245.7e6, "systems": 48},
-    "wilson.k2.f32": {"bytes": 2329.6e6, "algorithmic": 1849.7e6, "systems": 48},
+    "wilson.k1.f32": {"bytes": 1582.8e6, "algorithmic": 1245.7e6, "systems": 48},
+    "wilson.k2.f32": {"bytes": 2206.5e6, "algorithmic": 1849.7e6, "systems": 48},
 }
 
 # FP64 peak of a GB300 when no measurement is given (nominal 1.25 TFLOP/s; the
