@@ -245,12 +245,19 @@ int cgne_solve_noalloc(const sw_lattice* lat, int op, const void* U, const void*
  *   reads the status words on the host after every round.  Solves taken while
  *   kernel timing is enabled (sw_profile_enable), the server's engines and
  *   cgne_solve_noalloc always use the host-driven rounds.
+ * SW_PARAM_WILSON_LEAN: form of the spin-projected (r = 1) FP32 Wilson
+ *   stencil: -1 (default) chooses by lattice size -- the lean form (fewer
+ *   live registers, 8 blocks per SM) when the packed FP32 links take at most
+ *   64 MB, else the default form (7 blocks per SM); 1 always the lean form, 0
+ *   always the default form.  The two forms perform the same operations in
+ *   the same order: results are bit-identical, only the speed differs.  Read
+ *   when a solve starts or a server engine is created.
  * None of these changes what a solve converges to: convergence is always
  * decided on an FP64 residual.  Returns SW_ERR_ARG for an unknown key or a
  * value out of range. */
 enum { SW_PARAM_CHUNK = 0, SW_PARAM_RELIABLE_DELTA = 1, SW_PARAM_NS_SW = 2, SW_PARAM_NS_WILSON = 3,
        SW_PARAM_GRAPHS = 4, SW_PARAM_SITE_BLOCKING = 5, SW_PARAM_GROUP_FAST = 6,
-       SW_PARAM_RELIABLE_DELTA_F16 = 9, SW_PARAM_PERSISTENT = 10 };
+       SW_PARAM_RELIABLE_DELTA_F16 = 9, SW_PARAM_PERSISTENT = 10, SW_PARAM_WILSON_LEAN = 11 };
 enum { SW_SITE_SHAPES = 6 };
 int sw_set_param(int key, double value);
 int sw_get_param(int key, double* value);

@@ -19,5 +19,5 @@ from ._binding import (  # noqa: F401
     sw_kernel_launches, sw_measure_fp64_peak, sw_workspace_reserved, sw_trim_workspace, cgne_solve_noalloc, sw_set_param, sw_get_param,
     sw_autotune, sw_autotune_layout, SW_PARAM_CHUNK, SW_PARAM_RELIABLE_DELTA, SW_PARAM_NS_SW, SW_PARAM_NS_WILSON, SW_PARAM_GRAPHS,
     SW_PARAM_SITE_BLOCKING, SW_PARAM_GROUP_FAST,
-    SW_PARAM_RELIABLE_DELTA_F16, SW_PARAM_PERSISTENT, SW_SITE_SHAPES,
+    SW_PARAM_RELIABLE_DELTA_F16, SW_PARAM_PERSISTENT, SW_PARAM_WILSON_LEAN, SW_SITE_SHAPES,
 )

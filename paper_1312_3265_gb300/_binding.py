@@ -24,6 +24,7 @@ SW_PARAM_SITE_BLOCKING = 5
 SW_PARAM_GROUP_FAST = 6
 SW_PARAM_RELIABLE_DELTA_F16 = 9
 SW_PARAM_PERSISTENT = 10
+SW_PARAM_WILSON_LEAN = 11
 SW_SITE_SHAPES = 6  # SW_PARAM_SITE_BLOCKING values: 0 lexicographic, 1..5 site-block shapes
 
 

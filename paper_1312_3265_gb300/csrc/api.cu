@@ -79,6 +79,7 @@ std::atomic<int> g_param_ns_sw{2};
 std::atomic<int> g_param_ns_wilson{1};
 std::atomic<int> g_param_graphs{1};
 std::atomic<int> g_param_persistent{0};
+std::atomic<int> g_param_wilson_lean{-1};
 std::atomic<int> g_param_site_block{0};
 std::atomic<int> g_param_group_fast{0};
 thread_local std::vector<cudaEvent_t> t_used;
@@ -130,6 +131,7 @@ double param_delta(bool half) { return half ? g_param_delta16.load() : g_param_d
 int param_ns(int nc) { return nc == 3 ? g_param_ns_sw.load() : g_param_ns_wilson.load(); }
 bool param_graphs() { return g_param_graphs.load() != 0; }
 bool param_persistent() { return g_param_persistent.load() != 0; }
+int param_wilson_lean() { return g_param_wilson_lean.load(); }
 int param_site_shape() { return g_param_site_block.load(); }
 bool param_group_fast() { return g_param_group_fast.load() != 0; }
 
@@ -260,6 +262,10 @@ int sw_set_param(int key, double value) {
                                                                                : g_param_persistent)
           .store((int)value);
       return SW_OK;
+    case SW_PARAM_WILSON_LEAN:
+      if (!(value == -1 || value == 0 || value == 1)) return SW_ERR_ARG;
+      g_param_wilson_lean.store((int)value);
+      return SW_OK;
     case SW_PARAM_SITE_BLOCKING:
       if (!(value >= 0 && value < SW_SITE_SHAPES && value == (int)value)) return SW_ERR_ARG;
       g_param_site_block.store((int)value);
@@ -286,6 +292,7 @@ int sw_get_param(int key, double* value) {
     case SW_PARAM_SITE_BLOCKING: *value = g_param_site_block.load(); return SW_OK;
     case SW_PARAM_GROUP_FAST: *value = g_param_group_fast.load(); return SW_OK;
     case SW_PARAM_PERSISTENT: *value = g_param_persistent.load(); return SW_OK;
+    case SW_PARAM_WILSON_LEAN: *value = g_param_wilson_lean.load(); return SW_OK;
     default: return SW_ERR_ARG;
   }
 }

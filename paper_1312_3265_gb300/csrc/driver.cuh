@@ -40,6 +40,7 @@ int param_ns(int nc);  // systems per thread of the FP32 stencils (1, 2 or 4) fo
 bool param_group_fast();     // system groups as the fastest grid dimension of the stencils
 bool param_graphs();   // replay chunks of iterations as captured CUDA graphs
 bool param_persistent();  // whole solve as one CUDA graph with a device-driven loop of rounds
+int param_wilson_lean();  // -1 by lattice size, 0 the default form, 1 the lean form (FP32 Wilson, r = 1)
 
 // Operators applied in two passes (the even-odd Schur complement): before
 // every application the engine launches the operator's pre-pass, which
@@ -96,7 +97,10 @@ struct DevMem {
 // The lean FP32 Wilson stencil (WOp's LEAN form) for lattices whose packed
 // FP32 links (288 B per site) take at most 64 MB, half the L2 -- measured on
 // GB300: 3% faster at 16^3x32, 4-8% slower at 24^3x48 and 32^3x64.
-inline bool wilson_lean(const Geom& g) { return (size_t)g.V * 288 <= (size_t(64) << 20); }
+inline bool wilson_lean(const Geom& g) {
+  const int f = param_wilson_lean();
+  return f < 0 ? (size_t)g.V * 288 <= (size_t(64) << 20) : f == 1;
+}
 
 inline int check_su3(const Geom& g, const double2* U, cudaStream_t st) {
   DevMem m;

@@ -81,7 +81,7 @@ def test_binding_constants_match_the_header():
             assert getattr(bd, name) == val, name
     for name in ("SW_PARAM_CHUNK", "SW_PARAM_RELIABLE_DELTA", "SW_PARAM_RELIABLE_DELTA_F16", "SW_PARAM_NS_SW",
                  "SW_PARAM_NS_WILSON", "SW_PARAM_GRAPHS", "SW_PARAM_SITE_BLOCKING", "SW_PARAM_GROUP_FAST",
-                 "SW_PARAM_PERSISTENT", "SW_SITE_SHAPES", "SW_PREC_F64", "SW_PREC_F32_RELIABLE", "SW_PREC_F16_RELIABLE"):
+                 "SW_PARAM_PERSISTENT", "SW_PARAM_WILSON_LEAN", "SW_SITE_SHAPES", "SW_PREC_F64", "SW_PREC_F32_RELIABLE", "SW_PREC_F16_RELIABLE"):
         assert getattr(bd, name) == consts[name], name
 
 
@@ -100,6 +100,7 @@ def test_tunable_ranges(lib):
         bd.SW_PARAM_GRAPHS: ([0, 1], [2, -1]),
         bd.SW_PARAM_GROUP_FAST: ([0, 1], [2]),
         bd.SW_PARAM_PERSISTENT: ([0, 1], [2, 0.5]),
+        bd.SW_PARAM_WILSON_LEAN: ([-1, 0, 1], [2, -2, 0.5]),
         bd.SW_PARAM_SITE_BLOCKING: (list(range(bd.SW_SITE_SHAPES)), [-1, bd.SW_SITE_SHAPES, 1.5]),
     }
     v = ctypes.c_double()

@@ -596,3 +596,36 @@ def test_even_odd_wilson_matches_the_oracle(sw, prec, case):
         assert np.array_equal(xi.cpu().numpy(), xb[i].cpu().numpy())
         P.mass = m
         assert P.true_resid(chis[i].reshape(-1), xb[i].cpu().numpy().reshape(-1)) <= 1.01e-9
+
+
+def test_wilson_lean_form_is_bitwise_default_form(sw):
+    """The two forms of the spin-projected FP32 Wilson stencil
+    (SW_PARAM_WILSON_LEAN: the lean one at 8 blocks per SM, the default one at
+    7) perform the same operations in the same order: a mixed-precision batch
+    (ragged masses, antiperiodic) and the inner operator itself, both ways,
+    give bit-identical results."""
+    import torch
+    P = Problem(sw, (6, 4, 4, 6), sw.SW_OP_WILSON, 23, ls.PLAQ_EPS, 0.1, apbc=True)
+    masses = [0.05, 0.1, 0.2, 0.07, 0.3]
+    chis = np.stack([ls.gaussian_source(P.dims, 12, 60 + i).reshape(-1, 4, 3) for i in range(5)])
+    chi = dev(chis)
+    old = sw.sw_get_param(sw.SW_PARAM_WILSON_LEAN)
+    out = {}
+    try:
+        for form in (1, 0):
+            sw.sw_set_param(sw.SW_PARAM_WILSON_LEAN, form)
+            x = torch.zeros_like(chi)
+            rc, infos = sw.cgne_solve_batch(P.dims, P.op, P.U, None, chi, x, masses, 1.0, 1e-9, 10000,
+                                            sw.SW_PREC_F32_RELIABLE, True)
+            assert rc == sw.SW_OK
+            y = torch.zeros_like(chi)
+            for dag in (False, True):
+                sw.dslash_apply_inner(P.dims, P.op, P.U, None, chi, y, masses, 1.0, dag, sw.SW_PREC_F32_RELIABLE, True)
+                out[(form, dag)] = y.cpu().numpy()
+            out[form] = (x.cpu().numpy(), [(i.iters, i.reliable_updates) for i in infos])
+    finally:
+        sw.sw_set_param(sw.SW_PARAM_WILSON_LEAN, old)
+    assert out[1][1] == out[0][1]
+    assert np.array_equal(out[1][0], out[0][0])
+    for dag in (False, True):
+        assert np.array_equal(out[(1, dag)], out[(0, dag)])
